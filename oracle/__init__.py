@@ -1,0 +1,268 @@
+"""FP64 CPU oracle for the GaussianImage accumulated-summation rasterizer.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke``
+and by the CPU-baseline leg of ``bench.py``. The product path (the
+``paper_2403_08551_gb300`` package and its CUDA library) never imports, links
+or runs anything here, and nothing here imports the product.
+
+The heavy loops (support rule, binning, render, backward) are plain C in
+``gi_oracle.c`` (FP64 arithmetic, FP32 only for the support rule); the
+per-Gaussian steps with no loops worth compiling (Adam, vector-quantisation
+decode/encode, PSNR) are numpy in FP64 here. Every function cites the passage
+of the paper it follows.
+
+Parity status per function (pins live in ``tests/test_oracle_*.py``):
+  rect_rule ... pinned (3-sigma ellipse extents, brute-force tile test)
+  bin ......... pinned (numpy brute force per tile)
+  render ...... pinned (isotropic closed form, linearity, permutation,
+                union additivity, brute force bit-exact)
+  backward .... pinned (central finite differences, isotropic closed form)
+  adam ........ pinned (closed-form first step, torch.optim.Adam)
+  vq_decode ... pinned (IEEE float32 addition, zero residual codebook)
+  rvq_encode .. pinned (exhaustive per-stage argmin)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import sys
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "gi_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+LOG2E = 1.4426950408889634
+
+
+def build(force: bool = False) -> str:
+    """Compile gi_oracle.c with gcc (OpenMP when available)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    base = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+            "-fPIC", "-shared", _SRC, "-lm"]
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    r = subprocess.run(base[:1] + ["-fopenmp"] + base[1:] + ["-o", tmp],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        r = subprocess.run(base + ["-o", tmp], capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError("oracle build failed:\n" + r.stderr)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            P = ctypes.c_void_p
+            i64, i32 = ctypes.c_int64, ctypes.c_int32
+            lib.gio_rect_rule.argtypes = [P, P, P, i64, i32, i32, i32, P, P]
+            lib.gio_rect_rule.restype = None
+            lib.gio_bin.argtypes = [P, P, i64, i32, i32, i64, P, P, P]
+            lib.gio_bin.restype = i64
+            lib.gio_conic.argtypes = [P, i64, P]
+            lib.gio_conic.restype = None
+            lib.gio_render.argtypes = [P, P, P, P, P, i32, i32, i32, P]
+            lib.gio_render.restype = None
+            lib.gio_render_brute.argtypes = [P, P, P, P, P, i64, i32, i32, i32, i32, P]
+            lib.gio_render_brute.restype = None
+            lib.gio_loss.argtypes = [P, P, i32, i32, P]
+            lib.gio_loss.restype = ctypes.c_double
+            lib.gio_backward.argtypes = [P, P, P, P, P, i64, i32, i32, i32, P, P, P, P, P]
+            lib.gio_backward.restype = None
+            lib.gio_num_threads.restype = ctypes.c_int
+            lib.gio_set_num_threads.argtypes = [ctypes.c_int]
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def num_threads() -> int:
+    return _load().gio_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    _load().gio_set_num_threads(int(n))
+
+
+def tiles(W: int, H: int, T: int):
+    return (W + T - 1) // T, (H + T - 1) // T
+
+
+def rect_rule(means, chol, color, W, H, T):
+    """Tile rectangles [n,4] (tx0, ty0, tx1, ty1) and counts [n] by the FP32
+    3-sigma support rule (reading of Sec. 3.2; see gi_oracle.c)."""
+    means, chol, color = _f32(means), _f32(chol), _f32(color)
+    n = means.shape[0]
+    rect = np.zeros((n, 4), np.int32)
+    cnt = np.zeros(n, np.int32)
+    _load().gio_rect_rule(_p(means), _p(chol), _p(color), n, W, H, T, _p(rect), _p(cnt))
+    return rect, cnt
+
+
+def bin_tiles(rect, cnt, W, H, T):
+    """Per-tile Gaussian lists by definition (ascending g within a tile).
+    Returns ids [K] uint32, ranges [T_img,2] int32, pair_off [n+1] int64."""
+    rect = np.ascontiguousarray(rect, np.int32)
+    cnt = np.ascontiguousarray(cnt, np.int32)
+    n = cnt.shape[0]
+    tw, th = tiles(W, H, T)
+    K = int(cnt.astype(np.int64).sum())
+    ids = np.zeros(max(K, 1), np.uint32)
+    ranges = np.zeros((tw * th, 2), np.int32)
+    pair_off = np.zeros(n + 1, np.int64)
+    k = _load().gio_bin(_p(rect), _p(cnt), n, tw, th, ids.shape[0], _p(ids), _p(ranges), _p(pair_off))
+    assert k == K
+    return ids[:K], ranges, pair_off
+
+
+def conic(chol):
+    """Sigma^-1 = [[A, B], [B, C]] of Sigma = L L^T (Eq. 1), FP64 [n,3]."""
+    chol = _f32(chol)
+    q = np.zeros((chol.shape[0], 3), np.float64)
+    _load().gio_conic(_p(chol), chol.shape[0], _p(q))
+    return q
+
+
+def render(means, chol, color, ids, ranges, W, H, T):
+    """Binned accumulated-summation render (Eq. 7), FP64 [H,W,3]."""
+    means, chol, color = _f32(means), _f32(chol), _f32(color)
+    ids = np.ascontiguousarray(ids, np.uint32)
+    if ids.size == 0:
+        ids = np.zeros(1, np.uint32)
+    ranges = np.ascontiguousarray(ranges, np.int32)
+    out = np.zeros((H, W, 3), np.float64)
+    _load().gio_render(_p(means), _p(chol), _p(color), _p(ids), _p(ranges), W, H, T, _p(out))
+    return out
+
+
+def render_brute(means, chol, color, rect, cnt, W, H, T, use_support=True):
+    """Every Gaussian at every pixel (Eq. 7); with ``use_support`` the same
+    tile-granular support as the binned form, else untruncated."""
+    means, chol, color = _f32(means), _f32(chol), _f32(color)
+    rect = np.ascontiguousarray(rect, np.int32)
+    cnt = np.ascontiguousarray(cnt, np.int32)
+    out = np.zeros((H, W, 3), np.float64)
+    _load().gio_render_brute(_p(means), _p(chol), _p(color), _p(rect), _p(cnt),
+                             means.shape[0], W, H, T, int(bool(use_support)), _p(out))
+    return out
+
+
+def loss(out, target):
+    """L2 loss read as the mean over 3HW (Sec. 3.4); returns (L, dL/dC)."""
+    out = np.ascontiguousarray(out, np.float64)
+    target = _f32(target)
+    H, W, _ = out.shape
+    d = np.zeros_like(out)
+    L = _load().gio_loss(_p(out), _p(target), W, H, _p(d))
+    return L, d
+
+
+def backward(means, chol, color, rect, cnt, W, H, T, dldc):
+    """Analytic gradients (App. A.1, A.2 with the errata noted in
+    gi_oracle.c). Returns dict of FP64 arrays: means [n,2], chol [n,3],
+    color [n,3], conic [n,3]."""
+    means, chol, color = _f32(means), _f32(chol), _f32(color)
+    rect = np.ascontiguousarray(rect, np.int32)
+    cnt = np.ascontiguousarray(cnt, np.int32)
+    dldc = np.ascontiguousarray(dldc, np.float64)
+    n = means.shape[0]
+    gm = np.zeros((n, 2)); gl = np.zeros((n, 3)); gc = np.zeros((n, 3)); gq = np.zeros((n, 3))
+    _load().gio_backward(_p(means), _p(chol), _p(color), _p(rect), _p(cnt), n, W, H, T,
+                         _p(dldc), _p(gm), _p(gl), _p(gc), _p(gq))
+    return {"means": gm, "chol": gl, "color": gc, "conic": gq}
+
+
+def forward_backward(means, chol, color, target, T):
+    """One full pass: support rule, binning, render, L2 loss, gradients."""
+    H, W, _ = target.shape
+    rect, cnt = rect_rule(means, chol, color, W, H, T)
+    ids, ranges, pair_off = bin_tiles(rect, cnt, W, H, T)
+    out = render(means, chol, color, ids, ranges, W, H, T)
+    L, d = loss(out, target)
+    grads = backward(means, chol, color, rect, cnt, W, H, T, d)
+    return dict(rect=rect, cnt=cnt, ids=ids, ranges=ranges, pair_off=pair_off,
+                out=out, loss=L, dldc=d, grads=grads)
+
+
+ADAM_BETAS = (0.9, 0.999)
+ADAM_EPS = 1e-8
+
+
+def adam(param, grad, m, v, step, lr, betas=ADAM_BETAS, eps=ADAM_EPS):
+    """One Adam step (Kingma & Ba, bias-corrected), FP64. ``step`` is the
+    1-based step count after this update. Returns (param, m, v)."""
+    b1, b2 = betas
+    p = np.asarray(param, np.float64)
+    g = np.asarray(grad, np.float64)
+    m = b1 * np.asarray(m, np.float64) + (1.0 - b1) * g
+    v = b2 * np.asarray(v, np.float64) + (1.0 - b2) * g * g
+    mhat = m / (1.0 - b1 ** step)
+    vhat = v / (1.0 - b2 ** step)
+    return p - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
+def vq_decode(means16, idx, codebooks):
+    """Codec decode (Sec. 3.3): positions from FP16; Cholesky and colour as
+    the sum over RVQ stages of codebook rows (hat c^M = sum_k C^k[i^k]),
+    evaluated in FP64 in stage order and rounded once to FP32.
+
+    means16 [n,2] float16 (or its uint16 bits), idx [2][M][n] uint8,
+    codebooks [2][M][B][3] float32 (attr 0 = Cholesky, 1 = colour)."""
+    m16 = np.asarray(means16)
+    if m16.dtype == np.uint16:
+        m16 = m16.view(np.float16)
+    means = m16.astype(np.float64).astype(np.float32)
+    idx = np.asarray(idx)
+    cb = np.asarray(codebooks, np.float32)
+    outs = []
+    for a in range(2):
+        acc = np.zeros((idx.shape[2], 3), np.float64)
+        for s in range(idx.shape[1]):
+            acc = acc + cb[a, s][idx[a, s].astype(np.int64)].astype(np.float64)
+        outs.append(acc.astype(np.float32))
+    return means, outs[0], outs[1]
+
+
+def rvq_encode(x, codebooks_attr):
+    """Greedy residual VQ (Sec. 3.3): stage m picks
+    argmin_k || C^m[k] - (x - hat x^{m-1}) ||^2 (lowest k on ties), FP64.
+    x [n,3], codebooks_attr [M][B][3] -> idx [M][n] uint8."""
+    x = np.asarray(x, np.float64)
+    cb = np.asarray(codebooks_attr, np.float32).astype(np.float64)
+    M = cb.shape[0]
+    idx = np.zeros((M, x.shape[0]), np.uint8)
+    recon = np.zeros_like(x)
+    for m in range(M):
+        res = x - recon
+        d2 = ((res[:, None, :] - cb[m][None, :, :]) ** 2).sum(-1)
+        k = np.argmin(d2, axis=1)  # first minimum = lowest index
+        idx[m] = k.astype(np.uint8)
+        recon = recon + cb[m][k]
+    return idx
+
+
+def psnr(out, target):
+    """PSNR = 10 log10(1 / MSE) on the output clamped to [0, 1] (Sec. 4.1)."""
+    o = np.clip(np.asarray(out, np.float64), 0.0, 1.0)
+    mse = np.mean((o - np.asarray(target, np.float64)) ** 2)
+    return float(10.0 * np.log10(1.0 / mse)) if mse > 0 else float("inf")
