@@ -1,0 +1,361 @@
+"""Benchmark: GaussianImage image fitting on GB300.
+
+Workload (one GPU): a 768x512 synthetic RGB image (Kodak-shaped) fitted by
+70,000 2D Gaussians (560K parameters), FP32, tile 16; one step = formation,
+binning, render + L2 loss, backward and Adam, replayed from a CUDA graph.
+Metric: fit iterations per second (whole job; N GPUs fit N independent
+images, weak scaling, no collective). Also reported: render FPS
+(formation + binning + render), Gaussian-pixel evaluations per second, the
+roofline of the dominant kernel, a batched-vs-plain comparison on uneven
+image batches, and the FP64 CPU oracle timed on this host (cpu_baseline).
+
+Timing: W untimed warm-up steps, then K steps, each bracketed by CUDA events
+on the launching stream with an L2 flush (a 256 MB write) before it, outside
+the timed window; barrier + synchronize before and after; max over ranks.
+
+``--impl reference`` times the FP64 CPU oracle (the reference arm of this
+build) on the same workload and prints its own JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "fit iter/s + render FPS (768×512, 70k Gaussians); batched vs plain at equal PSNR"
+WORKLOAD = "c1_768x512_70k"
+LR = (1e-3, 1e-2, 1e-2)
+FWD_FLOP_PER_EVAL = 11   # 1 FADD + 2 FFMA (quadratic form) + 3 FFMA (accumulate); exp on the SFU
+BWD_FLOP_PER_EVAL = 22   # 1 FADD + 2 FFMA + 3 FFMA + FMUL + 2 FFMA + FMUL + FADD + FMUL + FADD + FFMA
+SMS, FP32_LANES, SFU_LANES, SM_MAX_MHZ = 152, 128, 16, 2070.0
+FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5 (FMA = 2 flops)
+
+
+def env_rank():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
+        os.environ.get("LOCAL_RANK", "0"))
+
+
+def pack(w):
+    return np.concatenate([w.means, w.chol, w.color], axis=1).astype(np.float32)
+
+
+def radix_passes(W, H, T):
+    """LSD passes the binning sort makes over the tile keys (8-bit digits)."""
+    tiles = ((W + T - 1) // T) * ((H + T - 1) // T)
+    bits = max(1, math.ceil(math.log2(max(tiles, 2))))
+    return (bits + 7) // 8
+
+
+def evals_per_render(ranges, W, H, T):
+    """Gaussian-pixel evaluations: sum over tiles of list length x in-image pixels."""
+    tw, th = (W + T - 1) // T, (H + T - 1) // T
+    ln = (ranges[:, 1] - ranges[:, 0]).astype(np.int64).reshape(th, tw)
+    pw = np.minimum(T, W - np.arange(tw) * T)
+    ph = np.minimum(T, H - np.arange(th) * T)
+    return int((ln * ph[:, None] * pw[None, :]).sum()), int((ln * T * T).sum())
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int, path: str | None):
+        self.index, self.path, self.p = index, path, None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.p is None:
+            return
+        time.sleep(0.3)
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        for line in out.splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+        if self.path:
+            with open(self.path, "w") as f:
+                f.write(self.Q + "\n" + out)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        mhz = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if "Active" in r[5 + i]
+                          and "Not" not in r[5 + i]})
+        return {"sm_mhz": statistics.median(mhz) if mhz else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def cpu_baseline(w, T, budget_s=20.0):
+    """The FP64 oracle as it stands: full fit steps on this workload."""
+    import oracle
+    p = pack(w).astype(np.float64)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    lr = np.tile(np.array([LR[0]] * 2 + [LR[1]] * 3 + [LR[2]] * 3), (p.shape[0], 1))
+    steps, t0 = 0, time.perf_counter()
+    while True:
+        r = oracle.forward_backward(p[:, 0:2].astype(np.float32), p[:, 2:5].astype(np.float32),
+                                    p[:, 5:8].astype(np.float32), w.target, T)
+        g = np.concatenate([r["grads"]["means"], r["grads"]["chol"], r["grads"]["color"]], axis=1)
+        p, m, v = oracle.adam(p, g, m, v, steps + 1, lr)
+        steps += 1
+        el = time.perf_counter() - t0
+        if el > budget_s or steps >= 50:
+            break
+    return {"value": steps / el, "unit": "iter/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{steps} full fit steps of {WORKLOAD} (FP64 C oracle, OpenMP) in {el:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = env_rank()
+    if rank != 0:
+        return 0
+    import oracle
+    w = synth.workload(WORKLOAD)
+    T = args.tile
+    p = pack(w).astype(np.float64)
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    lr = np.tile(np.array([LR[0]] * 2 + [LR[1]] * 3 + [LR[2]] * 3), (p.shape[0], 1))
+    times = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = oracle.forward_backward(p[:, 0:2].astype(np.float32), p[:, 2:5].astype(np.float32),
+                                    p[:, 5:8].astype(np.float32), w.target, T)
+        g = np.concatenate([r["grads"]["means"], r["grads"]["chol"], r["grads"]["color"]], axis=1)
+        p, m, v = oracle.adam(p, g, m, v, s + 1, lr)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    val = args.steps / tot
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "iter/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": f"{WORKLOAD} (768x512 RGB, 70,000 Gaussians, tile {T})"},
+            "cpu_baseline": {"value": val, "unit": "iter/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{args.steps} full fit steps of {WORKLOAD} per timed run"},
+            "e2e": {"value": val, "unit": "iter/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def batched_vs_plain(gi, torch, n_images, steps, T, stream):
+    """Images of uneven sizes fitted in one launch per stage vs one at a time."""
+    ws = synth.batch_workload(n_images)
+    tg = [torch.from_numpy(w.target).cuda() for w in ws]
+    pr = [torch.from_numpy(pack(w)).cuda() for w in ws]
+    fit = gi.Fit(tg, pr, tile=T, lr=LR)
+    fit.step(2)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fit.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    t_b = e0.elapsed_time(e1) / 1e3
+    mse_b = fit.mse()
+    fit.close()
+    plain = [gi.Fit([t], [p], tile=T, lr=LR) for t, p in zip(tg, pr)]
+    for f in plain:
+        f.step(2)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for f in plain:
+        f.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    t_p = e0.elapsed_time(e1) / 1e3
+    mse_p = [f.mse()[0] for f in plain]
+    for f in plain:
+        f.close()
+    psnr = lambda e: 10 * math.log10(1.0 / e) if e > 0 else float("inf")  # noqa: E731
+    dpsnr = max(abs(psnr(a) - psnr(b)) for a, b in zip(mse_b, mse_p))
+    return {"images": n_images, "steps": steps, "sizes": "uniform over 256x256, 512x384, 768x512, 1024x768",
+            "gaussians": int(sum(w.n for w in ws)),
+            "batched_image_steps_per_s": n_images * steps / t_b, "plain_image_steps_per_s": n_images * steps / t_p,
+            "speedup": t_p / t_b, "max_abs_dpsnr_db": dpsnr}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--tile", type=int, default=16)
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--batch-images", type=int, default=64)
+    ap.add_argument("--out", default=os.path.join(ROOT, "gpurun_out"))
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = env_rank()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2403_08551_gb300 as gi
+    gi.load()
+    T = args.tile
+    stream = torch.cuda.current_stream()
+
+    w = synth.workload(WORKLOAD, index=rank)
+    target = torch.from_numpy(w.target).cuda()
+    params = torch.from_numpy(pack(w)).cuda()
+    fit = gi.Fit([target], [params], tile=T, lr=LR, stage_events=True)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    for _ in range(args.warmup):
+        fit.step(1)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stage = np.zeros(5)
+    os.makedirs(args.out, exist_ok=True)
+    with Clocks(local, os.path.join(args.out, f"clocks_rank{rank}.csv") if rank == 0 else None) as clk:
+        barrier()
+        for i in range(args.steps):
+            flush.zero_()
+            ev[i][0].record(stream)
+            fit.step(1)
+            ev[i][1].record(stream)
+            stage += np.array(fit.stage_times())  # waits for this step; the next flush hides launch latency
+        barrier()
+    step_ms = sum(a.elapsed_time(b) for a, b in ev)
+    t_local = step_ms / 1e3
+    if world > 1:
+        t = torch.tensor([t_local], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    else:
+        t_max = t_local
+    value = world * args.steps / t_max
+    stage_ms = stage / args.steps
+
+    # Render FPS: formation + binning + render (no backward), flushed L2.
+    n_r = max(20, args.steps // 2)
+    evr = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_r)]
+    for i in range(n_r):
+        flush.zero_()
+        evr[i][0].record(stream)
+        fit.render()
+        evr[i][1].record(stream)
+    torch.cuda.synchronize()
+    render_ms = sum(a.elapsed_time(b) for a, b in evr) / n_r
+
+    # Evaluations per render for the current parameters.
+    p_now = fit.params.clone()
+    rec, rect, cnt = gi.project(p_now[:, 0:2].contiguous(), p_now[:, 2:5].contiguous(), p_now[:, 5:8].contiguous(),
+                                w.W, w.H, T)
+    bins = gi.bin_tiles(rect, cnt, None, w.W, w.H, T)
+    ev_in, ev_all = evals_per_render(bins.ranges.cpu().numpy(), w.W, w.H, T)
+    K = bins.K
+
+    # End to end through the public API with host buffers: per step the
+    # target image is copied from pinned host memory and the loss read back.
+    host_tgt = torch.from_numpy(w.target.reshape(-1)).pin_memory()
+    host_loss = torch.empty(fit.loss_sum.shape, dtype=torch.float64).pin_memory()
+    n_e = max(20, args.steps // 2)
+    eve = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_e)]
+    for i in range(n_e):
+        flush.zero_()
+        eve[i][0].record(stream)
+        fit.targets.copy_(host_tgt, non_blocking=True)
+        fit.step(1)
+        host_loss.copy_(fit.loss_sum, non_blocking=True)
+        eve[i][1].record(stream)
+    torch.cuda.synchronize()
+    e2e_s = sum(a.elapsed_time(b) for a, b in eve) / 1e3
+    e2e = {"value": world * n_e / e2e_s if world == 1 else None, "unit": "iter/s",
+           "h2d_bytes_per_step": int(host_tgt.numel() * 4), "d2h_bytes_per_step": int(host_loss.numel() * 8)}
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e["value"] = world * n_e / float(t.item())
+
+    # Roofline of the dominant kernel (backward or render), FP32-pipe bound.
+    names = ["formation", "binning", "render", "backward", "update"]
+    bwd_tflops = BWD_FLOP_PER_EVAL * ev_all / (stage_ms[3] * 1e-3) / 1e12
+    fwd_tflops = FWD_FLOP_PER_EVAL * ev_all / (stage_ms[2] * 1e-3) / 1e12
+    dom = "backward" if stage_ms[3] >= stage_ms[2] else "render"
+    ach = bwd_tflops if dom == "backward" else fwd_tflops
+    roof = {"kernel": "k_backward" if dom == "backward" else "k_render", "bound": "alu", "achieved": ach,
+            "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz",
+            "sfu_frac": (ev_all / (stage_ms[3 if dom == 'backward' else 2] * 1e-3))
+            / (SMS * SFU_LANES * SM_MAX_MHZ * 1e6)}
+
+    out = {"metric": METRIC, "value": value, "unit": "iter/s", "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": f"{WORKLOAD}: 768x512 RGB synthetic image, 70,000 Gaussians, tile {T}, "
+                                  f"FP32 Adam (lr 1e-3 means, 1e-2 others)", "global_batch": world,
+                      "parallelism": f"replica x{world} (independent images)",
+                      "l2": "flushed (256 MB write) before every timed step"},
+           "render_fps": 1e3 / render_ms, "render_ms": render_ms,
+           "stage_ms": dict(zip(names, [float(x) for x in stage_ms])),
+           "pairs": K, "evals_per_render": ev_in, "evals_per_render_padded": ev_all,
+           "fwd_evals_per_s": ev_all / (stage_ms[2] * 1e-3), "bwd_evals_per_s": ev_all / (stage_ms[3] * 1e-3),
+           "gpu_launches": args.steps * (6 + radix_passes(w.W, w.H, T)), "roofline": roof, "e2e": e2e,
+           "paper_context": {"render_fps": 2092.17, "fit_iter_s": 469.1, "hw": "V100 (Table 1a, Kodak)"}}
+    out["fit_psnr_db_after"] = 10 * math.log10(1.0 / max(fit.mse()[0], 1e-30))
+    if rank == 0:
+        out["clocks"] = clk.summary()
+    if not args.no_batched and rank == 0:
+        out["batched"] = batched_vs_plain(gi, torch, args.batch_images, 20, T, stream)
+    if not args.no_cpu and rank == 0:
+        out["cpu_baseline"] = cpu_baseline(w, T)
+    fit.close()
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

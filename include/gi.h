@@ -1,0 +1,250 @@
+/*
+ * gi.h -- C ABI of libgi, a GB300 (sm_103a) implementation of the
+ * differentiable accumulated-summation rasterizer of GaussianImage
+ * (arXiv 2403.08551): 2D Gaussians with 8 parameters each (mean mu, Cholesky
+ * vector l = (l1, l2, l3), weighted colour c'), rendered as
+ *     C_i = sum_n c'_n exp(-sigma_n),  sigma_n = 1/2 d^T Sigma_n^-1 d,
+ * with Sigma = L L^T, d = pixel centre - mu, no alpha blending, no depth
+ * order (Sec. 3.1 Eq. 1, Sec. 3.2 Eqs. 5 and 7).
+ *
+ * Conventions for every entry point:
+ *  - Pointers named *_dev or documented "device" are CUDA device pointers
+ *    owned by the caller; the library never frees them. Unless stated, a
+ *    call allocates nothing (gi_fit_create and gi_alu_peaks are the
+ *    exceptions).
+ *  - Arrays are dense, row-major and 16-byte aligned; a misaligned or NULL
+ *    required pointer returns GI_ERR_INVALID_ARG without launching.
+ *  - Images are HWC float32 ([height][width][3]); pixel (x, y) has centre
+ *    (x + 0.5, y + 0.5); means are in the same pixel frame.
+ *  - Parameters are pixel-space values (no activation functions applied).
+ *  - Every call is stream-ordered on `stream` (NULL = legacy default
+ *    stream), does not synchronise the host and can be captured in a CUDA
+ *    graph. Launch failures return GI_ERR_CUDA; faults during execution
+ *    surface at a later synchronisation. Conditions detected on the device
+ *    (pair capacity exceeded, a bounded wait that gave up) set bits in a
+ *    per-device error word read by gi_device_errors().
+ *  - On failure gi_last_error() returns a thread-local message.
+ *
+ * Support of a Gaussian (the paper leaves it unspecified): the tile-granular
+ * rectangle of its 3-sigma ellipse, evaluated in FP32 with correctly rounded
+ * operations only:
+ *     rx = 3|l1|, ry = 3 sqrt(l2^2 + l3^2)
+ *     tx0 = clamp(floor((mx - rx)/T), 0, tw), tx1 = clamp(floor((mx + rx)/T) + 1, 0, tw)
+ * (y likewise), tw = ceil(W/T), th = ceil(H/T). A Gaussian whose parameters
+ * are non-finite, whose det = (l1 l3)^2 is 0, whose FP32 conic is not finite
+ * or whose rectangle is empty is culled (count 0). Pixel i receives Gaussian
+ * n iff i's tile lies in n's rectangle.
+ */
+#ifndef GI_H_
+#define GI_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define GI_API __attribute__((visibility("default")))
+#else
+#define GI_API
+#endif
+
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st* gi_stream;
+
+typedef enum {
+    GI_OK = 0,
+    GI_ERR_INVALID_ARG = 1, /* bad pointer, size, alignment or tile edge */
+    GI_ERR_CUDA = 2,        /* a CUDA runtime call or launch failed */
+    GI_ERR_CAPACITY = 3,    /* more (tile, Gaussian) pairs than capacity */
+    GI_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    GI_ERR_UNSUPPORTED = 5, /* configuration not supported */
+    GI_ERR_NO_MEMORY = 6    /* allocation failed (gi_fit_create only) */
+} gi_status;
+
+/* Device error bits reported by gi_device_errors(). */
+#define GI_DEVERR_CAPACITY 1u /* K exceeded capacity: binned outputs incomplete */
+#define GI_DEVERR_TIMEOUT 2u  /* a bounded spin/mbarrier wait gave up */
+#define GI_DEVERR_BOUNDS 4u   /* an index check failed; the access was skipped */
+
+/* An image and its tile edge T (8, 16 or 32). */
+typedef struct {
+    int32_t width, height, tile;
+} gi_image;
+
+/* Floats per projected record: (mx, my, A', B', C', c'r, c'g, c'b) where
+ * Sigma^-1 = [[A, B], [B, C]] and A' = A log2(e)/2, B' = B log2(e),
+ * C' = C log2(e)/2, so exp(-sigma) = exp2(-(A'dx^2 + B'dx dy + C'dy^2)). */
+#define GI_REC_FLOATS 8
+
+GI_API int32_t gi_abi_version(void);
+GI_API const char* gi_last_error(void);
+GI_API const char* gi_status_string(int32_t status);
+
+/* Synchronises `stream`, returns the OR of GI_DEVERR_* bits raised on the
+ * current device since the last clear, clearing them if `clear` != 0. */
+GI_API gi_status gi_device_errors(uint32_t* bits, int32_t clear, gi_stream stream);
+
+/* ------------------------------------------------------------------------
+ * gi_project -- 2D Gaussian formation (Sec. 3.1, Eq. 1; Sec. 3.2, Eq. 5):
+ * Sigma = L L^T, its inverse (the conic) and the support rectangle.
+ *   means [n][2], chol [n][3] = (l1, l2, l3), color [n][3]: device, f32.
+ *   rec [n][8] f32 (GI_REC_FLOATS), rect [n][4] i32 (tx0, ty0, tx1, ty1),
+ *   cnt [n] i32 = (tx1 - tx0)(ty1 - ty0), 0 when culled (rect = 0).
+ * n = 0 is allowed (nothing is written).
+ * ---------------------------------------------------------------------- */
+GI_API gi_status gi_project(const float* means, const float* chol, const float* color, int32_t n, gi_image img,
+                     float* rec, int32_t* rect, int32_t* cnt, gi_stream stream);
+
+/* ------------------------------------------------------------------------
+ * gi_bin_tiles -- tile binning for the tile-based rasterization the paper
+ * builds on (Sec. 4.1, implementation details) without any depth sort
+ * (Sec. 3.2): for every tile t (row-major, t = ty*tw + tx) the list of
+ * Gaussians n whose rect contains t, in ascending n.
+ *   rect, cnt    from gi_project (device).
+ *   rec          nullable; if given with rec_binned, rec_binned[k] = rec[ids[k]].
+ *   capacity     number of pairs the outputs can hold (1 .. 2^30 - 1).
+ *   ws, ws_bytes scratch of gi_bin_workspace_size() bytes (device, 256-byte
+ *                aligned); contents are overwritten.
+ *   keys [capacity] u32  sorted tile id of each pair;
+ *   ids  [capacity] u32  Gaussian id of each pair (ascending within a tile);
+ *   ranges [tw*th][2] i32  [begin, end) of each tile in keys/ids, [0,0) empty;
+ *   rec_binned [capacity][8] f32, nullable;
+ *   pair_off [n+1] i64  exclusive prefix sum of cnt (pair index of n's first
+ *                tile in emission order); pair_off[n] = K;
+ *   k_dev [1] i64        K, the total number of pairs.
+ * If K > capacity only the first `capacity` emitted pairs are binned, the
+ * outputs are incomplete, k_dev still holds K and GI_DEVERR_CAPACITY is
+ * raised on the device (the call itself returns GI_OK: it does not wait).
+ * Bit-exact: identical inputs give identical outputs on every run.
+ * ---------------------------------------------------------------------- */
+GI_API gi_status gi_bin_workspace_size(int32_t n, gi_image img, int64_t capacity, size_t* bytes);
+GI_API gi_status gi_bin_tiles(const int32_t* rect, const int32_t* cnt, const float* rec, int32_t n, gi_image img,
+                       int64_t capacity, void* ws, size_t ws_bytes, uint32_t* keys, uint32_t* ids,
+                       int32_t* ranges, float* rec_binned, int64_t* pair_off, int64_t* k_dev,
+                       gi_stream stream);
+
+/* ------------------------------------------------------------------------
+ * gi_render -- accumulated-summation render (Sec. 3.2, Eq. 7) with an
+ * optional fused L2 reconstruction loss (Sec. 3.4, read as the mean over the
+ * 3*H*W values).
+ *   rec_binned, ranges: from gi_bin_tiles (device).
+ *   target [H][W][3] f32, nullable. out [H][W][3] f32 (written).
+ *   dl_dout [H][W][3] f32, nullable: dL/dC = 2 (C - target) / (3HW).
+ *   loss_sum [1] f64, nullable: sum of (C - target)^2 is ADDED to it
+ *   (zero it first; the loss is loss_sum / (3HW)).
+ * Summation per pixel runs over the tile's list in a fixed split order, so
+ * the result is the same on every run. c' is not clamped (Sec. 3.2).
+ * ---------------------------------------------------------------------- */
+GI_API gi_status gi_render(const float* rec_binned, const int32_t* ranges, gi_image img, const float* target,
+                    float* out, float* dl_dout, double* loss_sum, gi_stream stream);
+
+/* ------------------------------------------------------------------------
+ * gi_render_backward -- gradients of the render (App. A.1) chained through
+ * Sigma = L L^T to the Cholesky vector (App. A.2; the printed dL/dl2 has a
+ * typo: it is 2 g2 l1 + 2 g3 l2), recomputing exp(-sigma) per tile instead
+ * of storing per-pixel state.
+ *   rec_binned, keys, ids, ranges, pair_off, k_dev: from gi_bin_tiles;
+ *   rect, cnt: from gi_project; chol [n][3]: the parameters.
+ *   dl_dout [H][W][3] f32: upstream dL/dC.
+ *   capacity: the value given to gi_bin_tiles.
+ *   ws, ws_bytes: scratch of gi_backward_workspace_size() bytes.
+ *   g_means [n][2], g_chol [n][3], g_color [n][3]: written (not added).
+ *   g_conic [n][3], nullable: dL/dA, dL/dB, dL/dC of Sigma^-1 = [[A,B],[B,C]]
+ *   (B counted once).
+ * Deterministic: per-pair partial sums are reduced per Gaussian in emission
+ * order; no floating-point atomics.
+ * ---------------------------------------------------------------------- */
+GI_API gi_status gi_backward_workspace_size(int32_t n, gi_image img, int64_t capacity, size_t* bytes);
+GI_API gi_status gi_render_backward(const float* rec_binned, const uint32_t* keys, const uint32_t* ids,
+                             const int32_t* ranges, const int32_t* rect, const int32_t* cnt,
+                             const int64_t* pair_off, const int64_t* k_dev, const float* chol, int32_t n,
+                             gi_image img, int64_t capacity, const float* dl_dout, void* ws, size_t ws_bytes,
+                             float* g_means, float* g_chol, float* g_color, float* g_conic, gi_stream stream);
+
+/* ------------------------------------------------------------------------
+ * gi_vq_decode -- codec decode (Sec. 3.3): FP16 positions and residual
+ * vector quantisation, hat c^M = sum_{k=1..M} C^k[i^k], for the Cholesky
+ * vector (attribute 0) and the weighted colour (attribute 1).
+ *   means16 [n][2] IEEE binary16 bits; idx [2][stages][n] u8;
+ *   codebooks [2][stages][cb_size][3] f32 (cb_size <= 256);
+ *   means [n][2], chol [n][3], color [n][3] f32 (written).
+ * Bit-exact: each output is the exact stage sum rounded once to FP32.
+ * ---------------------------------------------------------------------- */
+GI_API gi_status gi_vq_decode(const uint16_t* means16, const uint8_t* idx, const float* codebooks, int32_t n,
+                       int32_t stages, int32_t cb_size, float* means, float* chol, float* color,
+                       gi_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Fitting (Sec. 3.4: L2 loss, no adaptive density control, Gaussian count
+ * fixed): one step = formation, binning, render + loss, backward and an
+ * Adam update (the paper uses Adan; Adam with bias correction here) of all
+ * 8 parameters. Several images of different sizes and Gaussian counts are
+ * fitted together: their tiles share one launch per stage. The step can be
+ * captured once into a CUDA graph and replayed.
+ * ---------------------------------------------------------------------- */
+typedef struct gi_fit gi_fit;
+
+typedef struct {
+    int32_t n_images;
+    const int32_t* widths;  /* host [n_images] */
+    const int32_t* heights; /* host [n_images] */
+    const int32_t* counts;  /* host [n_images] Gaussians per image */
+    const float* targets;   /* device, images concatenated, sum W*H*3 f32 */
+    const float* params;    /* device [sum counts][8] f32 initial (mx,my,l1,l2,l3,c'r,c'g,c'b) */
+    int32_t tile;           /* 8, 16 or 32 */
+    float lr_means, lr_chol, lr_color;
+    float beta1, beta2, eps;
+    int64_t capacity; /* pair capacity (>= 1), fixed for the context */
+    int32_t use_graph; /* 1: capture the step once and replay it */
+    int32_t stage_events; /* 1: record CUDA events between the five stages */
+} gi_fit_desc;
+
+/* Allocates the context and copies targets and params (the caller's buffers
+ * are not referenced afterwards). */
+GI_API gi_status gi_fit_create(const gi_fit_desc* desc, gi_stream stream, gi_fit** out);
+/* Runs `steps` fit steps (graph replays when use_graph). Asynchronous. */
+GI_API gi_status gi_fit_step(gi_fit* fit, int32_t steps, gi_stream stream);
+/* Renders the current parameters into the context's output buffer. */
+GI_API gi_status gi_fit_render(gi_fit* fit, gi_stream stream);
+
+/* Device pointers into the context (valid until gi_fit_destroy):
+ *   GI_FIT_PARAMS [N][8], GI_FIT_ADAM_M [N][8], GI_FIT_ADAM_V [N][8],
+ *   GI_FIT_GRADS [N][8] (gradients of the last step),
+ *   GI_FIT_OUT (images concatenated, HWC f32, the last step's render),
+ *   GI_FIT_LOSS [n_images] f64 sums of squared error of the last step,
+ *   GI_FIT_STEP [1] i32 completed steps, GI_FIT_K [1] i64 pairs of the last
+ *   step, GI_FIT_TARGET (images concatenated, HWC f32; may be overwritten
+ *   between steps to change the targets). */
+enum {
+    GI_FIT_PARAMS = 0,
+    GI_FIT_ADAM_M = 1,
+    GI_FIT_ADAM_V = 2,
+    GI_FIT_GRADS = 3,
+    GI_FIT_OUT = 4,
+    GI_FIT_LOSS = 5,
+    GI_FIT_STEP = 6,
+    GI_FIT_K = 7,
+    GI_FIT_TARGET = 8
+};
+GI_API gi_status gi_fit_pointer(gi_fit* fit, int32_t what, void** ptr);
+GI_API gi_status gi_fit_destroy(gi_fit* fit);
+
+/* With stage_events set: waits for the last step and writes the device time
+ * in milliseconds of its five stages: ms[0] formation, ms[1] binning,
+ * ms[2] render + loss, ms[3] backward, ms[4] reduction + Adam update. */
+GI_API gi_status gi_fit_stage_times(gi_fit* fit, float* ms);
+
+/* Measures FP32 FMA, packed f32x2 FMA and MUFU.EX2 throughput on the current
+ * device (synchronous; allocates a few bytes). result[0..5] = FFMA lane-ops/s,
+ * f32x2 FMA lane-ops/s, EX2/s, render-mix elements/s (6 FP32 + 1 EX2),
+ * SM MHz during the FFMA run, SM count. */
+GI_API gi_status gi_alu_peaks(double* result, gi_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GI_H_ */

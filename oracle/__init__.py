@@ -80,7 +80,7 @@ def _load():
             lib.gio_render_brute.restype = None
             lib.gio_loss.argtypes = [P, P, i32, i32, P]
             lib.gio_loss.restype = ctypes.c_double
-            lib.gio_backward.argtypes = [P, P, P, P, P, i64, i32, i32, i32, P, P, P, P, P]
+            lib.gio_backward.argtypes = [P, P, P, P, P, i64, i32, i32, i32, P, P, P, P, P, P]
             lib.gio_backward.restype = None
             lib.gio_num_threads.restype = ctypes.c_int
             lib.gio_set_num_threads.argtypes = [ctypes.c_int]
@@ -180,16 +180,19 @@ def loss(out, target):
 def backward(means, chol, color, rect, cnt, W, H, T, dldc):
     """Analytic gradients (App. A.1, A.2 with the errata noted in
     gi_oracle.c). Returns dict of FP64 arrays: means [n,2], chol [n,3],
-    color [n,3], conic [n,3]."""
+    color [n,3], conic [n,3], and "abs": per parameter the sum over pixels of
+    |that pixel's contribution| (the condition magnitude of the sum)."""
     means, chol, color = _f32(means), _f32(chol), _f32(color)
     rect = np.ascontiguousarray(rect, np.int32)
     cnt = np.ascontiguousarray(cnt, np.int32)
     dldc = np.ascontiguousarray(dldc, np.float64)
     n = means.shape[0]
     gm = np.zeros((n, 2)); gl = np.zeros((n, 3)); gc = np.zeros((n, 3)); gq = np.zeros((n, 3))
+    ga = np.zeros((n, 8))
     _load().gio_backward(_p(means), _p(chol), _p(color), _p(rect), _p(cnt), n, W, H, T,
-                         _p(dldc), _p(gm), _p(gl), _p(gc), _p(gq))
-    return {"means": gm, "chol": gl, "color": gc, "conic": gq}
+                         _p(dldc), _p(gm), _p(gl), _p(gc), _p(gq), _p(ga))
+    return {"means": gm, "chol": gl, "color": gc, "conic": gq,
+            "abs": {"means": ga[:, 0:2], "chol": ga[:, 2:5], "color": ga[:, 5:8]}}
 
 
 def forward_backward(means, chol, color, target, T):

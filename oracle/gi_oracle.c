@@ -278,20 +278,30 @@ double gio_loss(const double* out, const float* target, int32_t W, int32_t H, do
  * in-image pixels (row-major); Gaussians are independent, so the loop over
  * g is parallel.  Outputs (FP64): g_means [n][2], g_chol [n][3],
  * g_color [n][3], g_conic [n][3] = dL/dA, dL/dB, dL/dC of the symmetric
- * conic (B counted once, i.e. dL/dQ12 + dL/dQ21).
+ * conic (B counted once, i.e. dL/dQ12 + dL/dQ21), and, when g_abs is not
+ * NULL, g_abs [n][8] = the condition magnitude of each of the 8 parameter
+ * gradients as App. A computes them (sums over pixels first, then the
+ * per-Gaussian chain): the same formulas with every per-pixel term and every
+ * chain coefficient replaced by its absolute value. It bounds |gradient|
+ * and scales the rounding error of any floating-point evaluation of those
+ * sums; it equals |gradient| when nothing cancels.
  */
 void gio_backward(const float* means, const float* chol, const float* color,
                   const int32_t* rect, const int32_t* cnt, int64_t n, int32_t W,
                   int32_t H, int32_t T, const double* dldc, double* g_means,
-                  double* g_chol, double* g_color, double* g_conic) {
+                  double* g_chol, double* g_color, double* g_conic, double* g_abs) {
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t g = 0; g < n; ++g) {
         double gm[2] = {0, 0}, gc[3] = {0, 0, 0}, gq11 = 0, gq12 = 0, gq22 = 0;
+        /* sum over pixels of |per-pixel contribution| to each parameter's
+         * gradient (the condition magnitude of each gradient sum) */
+        double ab[8] = {0, 0, 0, 0, 0, 0, 0, 0}, am[5] = {0, 0, 0, 0, 0};
         if (cnt[g] > 0) {
             double A, B, C;
             conic64(chol, g, &A, &B, &C);
             const double mx = means[2 * g], my = means[2 * g + 1];
             const double cr = color[3 * g], cg = color[3 * g + 1], cbl = color[3 * g + 2];
+            const double l1 = chol[3 * g], l2 = chol[3 * g + 1], l3 = chol[3 * g + 2];
             const int32_t* r = rect + 4 * g;
             for (int32_t ty = r[1]; ty < r[3]; ++ty)
                 for (int32_t tx = r[0]; tx < r[2]; ++tx)
@@ -310,6 +320,19 @@ void gio_backward(const float* means, const float* chol, const float* color,
                             gq11 += e * 0.5 * dx * dx;
                             gq12 += e * 0.5 * dx * dy;
                             gq22 += e * 0.5 * dy * dy;
+                            if (g_abs) {
+                                /* absolute per-pixel terms of the sums App. A
+                                 * accumulates: e d (for mu), e/2 d d^T (for
+                                 * dL/dSigma, chained afterwards), G w (for c') */
+                                am[0] += fabs(e * dx);
+                                am[1] += fabs(e * dy);
+                                am[2] += fabs(0.5 * e * dx * dx);
+                                am[3] += fabs(0.5 * e * dx * dy);
+                                am[4] += fabs(0.5 * e * dy * dy);
+                                ab[5] += fabs(G[0] * w);
+                                ab[6] += fabs(G[1] * w);
+                                ab[7] += fabs(G[2] * w);
+                            }
                         }
             /* dL/dSigma = -Q G_Q Q, G_Q = [[gq11, gq12], [gq12, gq22]] */
             const double QG11 = A * gq11 + B * gq12, QG12 = A * gq12 + B * gq22;
@@ -317,10 +340,22 @@ void gio_backward(const float* means, const float* chol, const float* color,
             const double g1 = -(QG11 * A + QG12 * B);
             const double g2 = -(QG11 * B + QG12 * C);
             const double g3 = -(QG21 * B + QG22 * C);
-            const double l1 = chol[3 * g], l2 = chol[3 * g + 1], l3 = chol[3 * g + 2];
             g_chol[3 * g] = 2.0 * g1 * l1 + 2.0 * g2 * l2;
             g_chol[3 * g + 1] = 2.0 * g2 * l1 + 2.0 * g3 * l2;
             g_chol[3 * g + 2] = 2.0 * g3 * l3;
+            if (g_abs) {
+                /* the same linear maps with every coefficient and every sum
+                 * replaced by its absolute value */
+                ab[0] = fabs(A) * am[0] + fabs(B) * am[1];
+                ab[1] = fabs(B) * am[0] + fabs(C) * am[1];
+                const double k11a = A * A * l1 + A * B * l2, k12a = 2.0 * A * B * l1 + (A * C + B * B) * l2,
+                             k22a = B * B * l1 + B * C * l2;
+                const double k11b = A * B * l1 + B * B * l2, k12b = (A * C + B * B) * l1 + 2.0 * B * C * l2,
+                             k22b = B * C * l1 + C * C * l2;
+                ab[2] = 2.0 * (fabs(k11a) * am[2] + fabs(k12a) * am[3] + fabs(k22a) * am[4]);
+                ab[3] = 2.0 * (fabs(k11b) * am[2] + fabs(k12b) * am[3] + fabs(k22b) * am[4]);
+                ab[4] = 2.0 * fabs(l3) * (B * B * am[2] + 2.0 * fabs(B * C) * am[3] + C * C * am[4]);
+            }
         } else {
             g_chol[3 * g] = g_chol[3 * g + 1] = g_chol[3 * g + 2] = 0.0;
         }
@@ -329,6 +364,8 @@ void gio_backward(const float* means, const float* chol, const float* color,
         g_color[3 * g] = gc[0];
         g_color[3 * g + 1] = gc[1];
         g_color[3 * g + 2] = gc[2];
+        if (g_abs)
+            for (int j = 0; j < 8; ++j) g_abs[8 * g + j] = ab[j];
         if (g_conic) {
             g_conic[3 * g] = gq11;
             g_conic[3 * g + 1] = 2.0 * gq12;

@@ -1,0 +1,298 @@
+"""Python API over libgi: per-stage calls, an autograd Function and fitting
+contexts. Torch supplies device memory and the current CUDA stream; every
+step of the rasterizer runs in libgi's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+from typing import List, Optional, Sequence
+
+import torch
+
+from . import _lib as L
+
+__all__ = ["project", "bin_tiles", "render", "render_backward", "vq_decode", "device_errors",
+           "GIRender", "rasterize", "Fit", "Bins", "alu_peaks", "tiles"]
+
+
+def tiles(W: int, H: int, T: int):
+    return (W + T - 1) // T, (H + T - 1) // T
+
+
+def _dev(t: torch.Tensor, dtype, name: str) -> torch.Tensor:
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    return t.contiguous()
+
+
+def _img(W, H, T):
+    return L.GIImage(int(W), int(H), int(T))
+
+
+def device_errors(clear: bool = True) -> int:
+    bits = ctypes.c_uint32(0)
+    L.check(L.load().gi_device_errors(ctypes.byref(bits), int(clear), L.stream_handle()), "gi_device_errors")
+    return bits.value
+
+
+def project(means, chol, color, W: int, H: int, tile: int = 16):
+    """Formation (Eq. 1): returns rec [n,8], rect [n,4] int32, cnt [n] int32."""
+    means = _dev(means, torch.float32, "means")
+    chol = _dev(chol, torch.float32, "chol")
+    color = _dev(color, torch.float32, "color")
+    n = means.shape[0]
+    rec = torch.empty((n, 8), dtype=torch.float32, device=means.device)
+    rect = torch.empty((n, 4), dtype=torch.int32, device=means.device)
+    cnt = torch.empty((n,), dtype=torch.int32, device=means.device)
+    L.check(L.load().gi_project(L.ptr(means), L.ptr(chol), L.ptr(color), n, _img(W, H, tile), L.ptr(rec),
+                                L.ptr(rect), L.ptr(cnt), L.stream_handle()), "gi_project")
+    return rec, rect, cnt
+
+
+@dataclass
+class Bins:
+    keys: torch.Tensor
+    ids: torch.Tensor
+    ranges: torch.Tensor
+    rec_binned: Optional[torch.Tensor]
+    pair_off: torch.Tensor
+    k_dev: torch.Tensor
+    K: int
+    capacity: int
+
+
+def bin_tiles(rect, cnt, rec, W: int, H: int, tile: int = 16, capacity: Optional[int] = None) -> Bins:
+    """Tile binning. With ``capacity=None`` the pair count is read back and
+    the call is repeated once with an exact capacity if the guess was short
+    (one host synchronisation)."""
+    lib = L.load()
+    n = cnt.shape[0]
+    dev = cnt.device
+    rect = _dev(rect, torch.int32, "rect")
+    cnt = _dev(cnt, torch.int32, "cnt")
+    rec = None if rec is None else _dev(rec, torch.float32, "rec")
+    tw, th = tiles(W, H, tile)
+    auto = capacity is None
+    cap = int(capacity) if capacity else max(4096, 8 * n)
+    for _ in range(2):
+        ws_bytes = ctypes.c_size_t(0)
+        L.check(lib.gi_bin_workspace_size(n, _img(W, H, tile), cap, ctypes.byref(ws_bytes)), "gi_bin_workspace_size")
+        ws = torch.empty((ws_bytes.value + 256,), dtype=torch.uint8, device=dev)
+        keys = torch.empty((cap,), dtype=torch.int32, device=dev)
+        ids = torch.empty((cap,), dtype=torch.int32, device=dev)
+        ranges = torch.empty((tw * th, 2), dtype=torch.int32, device=dev)
+        rec_binned = torch.empty((cap, 8), dtype=torch.float32, device=dev) if rec is not None else None
+        pair_off = torch.empty((n + 1,), dtype=torch.int64, device=dev)
+        k_dev = torch.empty((1,), dtype=torch.int64, device=dev)
+        L.check(lib.gi_bin_tiles(L.ptr(rect) if n else None, L.ptr(cnt) if n else None, L.ptr(rec) if n else None,
+                                 n, _img(W, H, tile), cap, L.ptr(ws), ws_bytes.value, L.ptr(keys), L.ptr(ids),
+                                 L.ptr(ranges), L.ptr(rec_binned) if rec is not None else None, L.ptr(pair_off),
+                                 L.ptr(k_dev), L.stream_handle()), "gi_bin_tiles")
+        K = int(k_dev.item())
+        if K <= cap:
+            return Bins(keys, ids, ranges, rec_binned, pair_off, k_dev, K, cap)
+        if not auto:
+            raise L.GIError(f"gi_bin_tiles: {K} pairs exceed capacity {cap}")
+        device_errors(clear=True)  # drop the capacity bit raised by the short guess
+        cap = K
+    raise L.GIError("gi_bin_tiles: capacity retry failed")
+
+
+def render(bins: Bins, W: int, H: int, tile: int = 16, target=None, want_dl: bool = False):
+    """Accumulated-summation render (Eq. 7); with a target also the L2 loss
+    (mean over 3HW) and optionally dL/dC. Returns (out, dl or None, loss or None)."""
+    dev = bins.ranges.device
+    out = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+    dl = loss = None
+    if target is not None:
+        target = _dev(target, torch.float32, "target")
+        loss = torch.zeros((1,), dtype=torch.float64, device=dev)
+        if want_dl:
+            dl = torch.empty((H, W, 3), dtype=torch.float32, device=dev)
+    L.check(L.load().gi_render(L.ptr(bins.rec_binned), L.ptr(bins.ranges), _img(W, H, tile), L.ptr(target),
+                               L.ptr(out), L.ptr(dl), L.ptr(loss), L.stream_handle()), "gi_render")
+    if loss is not None:
+        loss = loss / (3.0 * W * H)
+    return out, dl, loss
+
+
+def render_backward(bins: Bins, rect, cnt, chol, dl_dout, W: int, H: int, tile: int = 16, want_conic=False):
+    """Gradients (App. A.1, A.2): returns g_means [n,2], g_chol [n,3],
+    g_color [n,3] and g_conic [n,3] (or None)."""
+    lib = L.load()
+    n = cnt.shape[0]
+    dev = cnt.device
+    chol = _dev(chol, torch.float32, "chol")
+    dl_dout = _dev(dl_dout, torch.float32, "dl_dout")
+    ws_bytes = ctypes.c_size_t(0)
+    L.check(lib.gi_backward_workspace_size(n, _img(W, H, tile), bins.capacity, ctypes.byref(ws_bytes)),
+            "gi_backward_workspace_size")
+    ws = torch.empty((ws_bytes.value + 256,), dtype=torch.uint8, device=dev)
+    gm = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    gl = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    gc = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    gq = torch.empty((n, 3), dtype=torch.float32, device=dev) if want_conic else None
+    L.check(lib.gi_render_backward(L.ptr(bins.rec_binned), L.ptr(bins.keys), L.ptr(bins.ids), L.ptr(bins.ranges),
+                                   L.ptr(rect), L.ptr(cnt), L.ptr(bins.pair_off), L.ptr(bins.k_dev), L.ptr(chol), n,
+                                   _img(W, H, tile), bins.capacity, L.ptr(dl_dout), L.ptr(ws), ws_bytes.value,
+                                   L.ptr(gm), L.ptr(gl), L.ptr(gc), L.ptr(gq), L.stream_handle()),
+            "gi_render_backward")
+    return gm, gl, gc, gq
+
+
+def vq_decode(means16, idx, codebooks):
+    """Codec decode (Sec. 3.3). means16 [n,2] float16 or int16/uint16 bits,
+    idx [2,M,n] uint8, codebooks [2,M,B,3] float32."""
+    lib = L.load()
+    if means16.dtype == torch.float16:
+        means16 = means16.view(torch.int16)
+    means16 = means16.contiguous()
+    idx = _dev(idx, torch.uint8, "idx")
+    cb = _dev(codebooks, torch.float32, "codebooks")
+    n = means16.shape[0]
+    M, B = cb.shape[1], cb.shape[2]
+    dev = means16.device
+    means = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    chol = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    color = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    L.check(lib.gi_vq_decode(L.ptr(means16), L.ptr(idx), L.ptr(cb), n, M, B, L.ptr(means), L.ptr(chol),
+                             L.ptr(color), L.stream_handle()), "gi_vq_decode")
+    return means, chol, color
+
+
+class GIRender(torch.autograd.Function):
+    """Differentiable render: forward runs formation, binning and Eq. 7;
+    backward recomputes the weights per tile (no per-pixel state saved)."""
+
+    @staticmethod
+    def forward(ctx, means, chol, color, W: int, H: int, tile: int = 16):
+        rec, rect, cnt = project(means, chol, color, W, H, tile)
+        bins = bin_tiles(rect, cnt, rec, W, H, tile)
+        out, _, _ = render(bins, W, H, tile)
+        ctx.save_for_backward(chol.detach().contiguous(), rect, cnt)
+        ctx.bins = bins
+        ctx.meta = (W, H, tile)
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        chol, rect, cnt = ctx.saved_tensors
+        W, H, tile = ctx.meta
+        gm, gl, gc, _ = render_backward(ctx.bins, rect, cnt, chol, grad_out.contiguous(), W, H, tile)
+        return gm, gl, gc, None, None, None
+
+
+def rasterize(means, chol, color, W: int, H: int, tile: int = 16):
+    return GIRender.apply(means, chol, color, W, H, tile)
+
+
+class _DevArray:
+    """Zero-copy view of device memory owned by a Fit context."""
+
+    def __init__(self, addr: int, shape, typestr: str):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": typestr, "data": (addr, False),
+                                         "version": 3, "strides": None}
+
+
+class Fit:
+    """Fitting context over one or more images (Sec. 3.4): each step is
+    formation, binning, render + L2 loss, backward and Adam, replayed from a
+    CUDA graph when ``use_graph``.
+
+    targets: list of [H,W,3] float32 CUDA tensors; params: list of [n,8]
+    float32 tensors (mx, my, l1, l2, l3, c'r, c'g, c'b) per image."""
+
+    def __init__(self, targets: Sequence[torch.Tensor], params: Sequence[torch.Tensor], tile: int = 16,
+                 lr=(1e-3, 1e-2, 1e-2), betas=(0.9, 0.999), eps=1e-8, capacity: Optional[int] = None,
+                 capacity_factor: float = 1.5, use_graph: bool = True, stage_events: bool = False):
+        lib = L.load()
+        assert len(targets) == len(params) and len(targets) >= 1
+        self.shapes = [(int(t.shape[1]), int(t.shape[0])) for t in targets]
+        self.counts = [int(p.shape[0]) for p in params]
+        self.tile = tile
+        dev = targets[0].device
+        tgt = torch.cat([_dev(t, torch.float32, "target").reshape(-1) for t in targets])
+        prm = torch.cat([_dev(p, torch.float32, "params").reshape(-1, 8) for p in params]).contiguous()
+        if capacity is None:
+            K = 0
+            for (W, H), p in zip(self.shapes, params):
+                p = p.contiguous()
+                rec, rect, cnt = project(p[:, 0:2].contiguous(), p[:, 2:5].contiguous(), p[:, 5:8].contiguous(),
+                                         W, H, tile)
+                K += bin_tiles(rect, cnt, None, W, H, tile).K
+            capacity = max(4096, int(K * capacity_factor) + 1024)
+        self.capacity = int(capacity)
+        n_img = len(targets)
+        self._w = (ctypes.c_int32 * n_img)(*[s[0] for s in self.shapes])
+        self._h = (ctypes.c_int32 * n_img)(*[s[1] for s in self.shapes])
+        self._n = (ctypes.c_int32 * n_img)(*self.counts)
+        desc = L.GIFitDesc(n_img, ctypes.cast(self._w, ctypes.c_void_p), ctypes.cast(self._h, ctypes.c_void_p),
+                           ctypes.cast(self._n, ctypes.c_void_p), tgt.data_ptr(), prm.data_ptr(), tile,
+                           lr[0], lr[1], lr[2], betas[0], betas[1], eps, self.capacity, int(use_graph),
+                           int(stage_events))
+        h = ctypes.c_void_p()
+        L.check(lib.gi_fit_create(ctypes.byref(desc), L.stream_handle(), ctypes.byref(h)), "gi_fit_create")
+        self._h_fit = h
+        self.device = dev
+        N = sum(self.counts)
+        npix = sum(W * H for W, H in self.shapes)
+        self.params = self._view(L.FIT_PARAMS, (N, 8), "<f4")
+        self.adam_m = self._view(L.FIT_ADAM_M, (N, 8), "<f4")
+        self.adam_v = self._view(L.FIT_ADAM_V, (N, 8), "<f4")
+        self.grads = self._view(L.FIT_GRADS, (N, 8), "<f4")
+        self.out = self._view(L.FIT_OUT, (npix * 3,), "<f4")
+        self.loss_sum = self._view(L.FIT_LOSS, (n_img,), "<f8")
+        self.step_count = self._view(L.FIT_STEP, (1,), "<i4")
+        self.k = self._view(L.FIT_K, (1,), "<i8")
+        self.targets = self._view(L.FIT_TARGET, (npix * 3,), "<f4")
+
+    def _view(self, what, shape, typestr):
+        p = ctypes.c_void_p()
+        L.check(L.load().gi_fit_pointer(self._h_fit, what, ctypes.byref(p)), "gi_fit_pointer")
+        return torch.as_tensor(_DevArray(p.value, shape, typestr), device=self.device)
+
+    def step(self, n: int = 1):
+        L.check(L.load().gi_fit_step(self._h_fit, int(n), L.stream_handle()), "gi_fit_step")
+
+    def stage_times(self):
+        """Device ms of the last step's stages: formation, binning, render,
+        backward, update (needs stage_events=True)."""
+        ms = (ctypes.c_float * 5)()
+        L.check(L.load().gi_fit_stage_times(self._h_fit, ms), "gi_fit_stage_times")
+        return list(ms)
+
+    def render(self):
+        L.check(L.load().gi_fit_render(self._h_fit, L.stream_handle()), "gi_fit_render")
+
+    def images(self) -> List[torch.Tensor]:
+        outs, o = [], 0
+        for W, H in self.shapes:
+            outs.append(self.out[o:o + W * H * 3].view(H, W, 3))
+            o += W * H * 3
+        return outs
+
+    def mse(self) -> List[float]:
+        """Per-image mean squared error of the last step's render."""
+        s = self.loss_sum.cpu().tolist()
+        return [v / (3.0 * W * H) for v, (W, H) in zip(s, self.shapes)]
+
+    def close(self):
+        if getattr(self, "_h_fit", None) is not None:
+            L.load().gi_fit_destroy(self._h_fit)
+            self._h_fit = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def alu_peaks():
+    r = (ctypes.c_double * 6)()
+    L.check(L.load().gi_alu_peaks(r, L.stream_handle()), "gi_alu_peaks")
+    return {"ffma_lane_ops_s": r[0], "ffma2_lane_ops_s": r[1], "ex2_s": r[2], "mix_elems_s": r[3],
+            "sm_mhz": r[4], "sms": int(r[5])}

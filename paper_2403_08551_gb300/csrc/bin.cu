@@ -1,0 +1,472 @@
+// bin.cu -- Gaussian formation (projection to conic + tile rect) and tile
+// binning: count scan, key emission, stable LSD radix sort (onesweep with a
+// bounded decoupled look-back) and per-tile ranges.
+//
+// Formation follows Sec. 3.1, Eq. 1 (Sigma = L L^T) and Sec. 3.2, Eq. 5
+// (sigma = 1/2 d^T Sigma^-1 d). The paper does not define the screen support
+// of a Gaussian; the reading implemented here is the tile-granular 3-sigma
+// rectangle, evaluated with correctly rounded FP32 operations only (no fused
+// multiply-add), so that tile lists are bit-identical to the CPU oracle.
+// Binning keeps ascending Gaussian index inside each tile (the sort is
+// stable over keys emitted in Gaussian order), which fixes the summation
+// order of Eq. 7 and makes the forward render reproducible.
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace gi {
+
+namespace {
+
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagPre = 2u << 30;
+constexpr uint32_t kValMask = (1u << 30) - 1;
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ float clampf_(float v, float lo, float hi) {
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+__device__ void zero_job(const ZeroJob& zj) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+        uint32_t* p = zj.p[r];
+        if (!p) continue;
+        const int64_t n = zj.n32[r], n4 = n >> 2;
+        uint4* p4 = reinterpret_cast<uint4*>(p);
+        for (int64_t i = tid; i < n4; i += nth) p4[i] = make_uint4(0, 0, 0, 0);
+        for (int64_t i = (n4 << 2) + tid; i < n; i += nth) p[i] = 0u;
+    }
+}
+
+template <typename Tv>
+__device__ __forceinline__ Tv warp_incl_scan(Tv v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        Tv u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+template <typename Tv>
+__device__ __forceinline__ Tv warp_sum(Tv v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Inclusive scan over the block (blockDim.x a multiple of 32, <= 1024).
+template <typename Tv>
+__device__ Tv block_incl_scan(Tv v, Tv* s_warp /*[32]*/) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_incl_scan(v);
+    if (lane == 31) s_warp[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        Tv w = lane < nw ? s_warp[lane] : Tv(0);
+        w = warp_incl_scan(w);
+        if (lane < nw) s_warp[lane] = w;
+    }
+    __syncthreads();
+    if (warp > 0) v += s_warp[warp - 1];
+    __syncthreads();
+    return v;
+}
+
+template <typename Tv>
+__device__ Tv block_sum(Tv v, Tv* s_warp /*[32]*/) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) s_warp[warp] = v;
+    __syncthreads();
+    Tv r = Tv(0);
+    if (warp == 0) {
+        r = lane < nw ? s_warp[lane] : Tv(0);
+        r = warp_sum(r);
+        if (lane == 0) s_warp[0] = r;
+    }
+    __syncthreads();
+    r = s_warp[0];
+    __syncthreads();
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Formation: conic + FP32 3-sigma tile rect (Eq. 1, Eq. 5).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kProjBlock) k_project(ParamsIn P, Batch B, float4* __restrict__ rec,
+                                                        int4* __restrict__ rect, int32_t* __restrict__ cnt,
+                                                        int64_t* __restrict__ blk_sum, ZeroJob zj) {
+    __shared__ int64_t s_warp[32];
+    zero_job(zj);
+    const int g = blockIdx.x * kProjBlock + threadIdx.x;
+    int c = 0;
+    if (g < B.total_gauss) {
+        const ImgDesc d = img_desc(B, image_of_gauss(B, g));
+        const float mx = P.means[(int64_t)g * P.ms], my = P.means[(int64_t)g * P.ms + 1];
+        const float l1 = P.chol[(int64_t)g * P.ls], l2 = P.chol[(int64_t)g * P.ls + 1],
+                    l3 = P.chol[(int64_t)g * P.ls + 2];
+        const float cr = P.color[(int64_t)g * P.cs], cg = P.color[(int64_t)g * P.cs + 1],
+                    cb = P.color[(int64_t)g * P.cs + 2];
+        int4 r = make_int4(0, 0, 0, 0);
+        float4 r0 = make_float4(mx, my, 0.f, 0.f), r1 = make_float4(0.f, cr, cg, cb);
+        bool ok = isfinite(mx) && isfinite(my) && isfinite(l1) && isfinite(l2) && isfinite(l3) &&
+                  isfinite(cr) && isfinite(cg) && isfinite(cb);
+        float ca = 0.f, cbb = 0.f, cc = 0.f;
+        if (ok) {
+            const float s11 = __fmul_rn(l1, l1);
+            const float s12 = __fmul_rn(l1, l2);
+            const float s22 = __fadd_rn(__fmul_rn(l2, l2), __fmul_rn(l3, l3));
+            const float dd = __fmul_rn(l1, l3);
+            const float det = __fmul_rn(dd, dd);
+            ok = det != 0.0f;
+            if (ok) {
+                ca = __fdiv_rn(s22, det);
+                cbb = __fdiv_rn(-s12, det);
+                cc = __fdiv_rn(s11, det);
+                ok = isfinite(det) && isfinite(ca) && isfinite(cbb) && isfinite(cc);
+            }
+            if (ok) {
+                const float rx = __fmul_rn(3.0f, fabsf(l1));
+                const float ry = __fmul_rn(3.0f, __fsqrt_rn(s22));
+                ok = isfinite(rx) && isfinite(ry);
+                if (ok) {
+                    const float inv_t = 1.0f / (float)B.tile;  // power of two: exact
+                    const float ftw = (float)d.tw, fth = (float)d.th;
+                    const float fx0 = clampf_(floorf(__fmul_rn(__fsub_rn(mx, rx), inv_t)), 0.0f, ftw);
+                    const float fx1 =
+                        clampf_(__fadd_rn(floorf(__fmul_rn(__fadd_rn(mx, rx), inv_t)), 1.0f), 0.0f, ftw);
+                    const float fy0 = clampf_(floorf(__fmul_rn(__fsub_rn(my, ry), inv_t)), 0.0f, fth);
+                    const float fy1 =
+                        clampf_(__fadd_rn(floorf(__fmul_rn(__fadd_rn(my, ry), inv_t)), 1.0f), 0.0f, fth);
+                    r = make_int4((int)fx0, (int)fy0, (int)fx1, (int)fy1);
+                    ok = r.x < r.z && r.y < r.w;
+                    if (!ok) r = make_int4(0, 0, 0, 0);
+                }
+            }
+        }
+        if (ok) {
+            c = (r.z - r.x) * (r.w - r.y);
+            const float h = 0.5f * kLog2e;
+            r0.z = ca * h;
+            r0.w = cbb * kLog2e;
+            r1.x = cc * h;
+        }
+        rec[2 * (int64_t)g] = r0;
+        rec[2 * (int64_t)g + 1] = r1;
+        rect[g] = r;
+        cnt[g] = c;
+    }
+    const int64_t tot = block_sum<int64_t>((int64_t)c, s_warp);
+    if (threadIdx.x == 0 && blk_sum) blk_sum[blockIdx.x] = tot;
+}
+
+// Block sums of an existing cnt[] (standalone binning), plus zeroing.
+__global__ void __launch_bounds__(kProjBlock) k_blocksum(const int32_t* __restrict__ cnt, int32_t n,
+                                                         int64_t* __restrict__ blk_sum, ZeroJob zj) {
+    __shared__ int64_t s_warp[32];
+    zero_job(zj);
+    const int g = blockIdx.x * kProjBlock + threadIdx.x;
+    const int c = g < n ? cnt[g] : 0;
+    const int64_t tot = block_sum<int64_t>((int64_t)c, s_warp);
+    if (threadIdx.x == 0) blk_sum[blockIdx.x] = tot;
+}
+
+// ---------------------------------------------------------------------------
+// Key emission: pair_off = exclusive scan of cnt; Gaussian g writes
+// (tile, g) for its rect in row-major order at pair_off[g] + j. Also builds
+// the per-pass digit histograms of the radix sort.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kProjBlock) k_emit(const int4* __restrict__ rect, const int32_t* __restrict__ cnt,
+                                                     const int64_t* __restrict__ blk_sum, Batch B, int64_t capacity,
+                                                     uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                     int64_t* __restrict__ pair_off, int64_t* __restrict__ k_dev,
+                                                     int64_t* __restrict__ k_max, uint32_t* __restrict__ hist,
+                                                     RadixPlan rp, uint32_t* __restrict__ status) {
+    __shared__ int64_t s_warp[32];
+    __shared__ uint32_t s_hist[4 * 256];
+    const int n = B.total_gauss;
+    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) s_hist[i] = 0;
+    int64_t pre = 0;
+    for (int i = threadIdx.x; i < (int)blockIdx.x; i += blockDim.x) pre += blk_sum[i];
+    pre = block_sum<int64_t>(pre, s_warp);
+    const int g = blockIdx.x * kProjBlock + threadIdx.x;
+    const int c = g < n ? cnt[g] : 0;
+    const int64_t incl = block_incl_scan<int64_t>((int64_t)c, s_warp);
+    const int64_t off = pre + incl - c;
+    if (g < n) pair_off[g] = off;
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) {
+        const int64_t K = off + c;
+        pair_off[n] = K;
+        *k_dev = K;
+        if (k_max) atomicMax(reinterpret_cast<unsigned long long*>(k_max), (unsigned long long)K);
+        if (K > capacity) flag_error(status, kErrCapacity);
+    }
+    const uint32_t dmask = (1u << rp.dbits) - 1;
+    if (c > 0) {
+        const int4 r = rect[g];
+        const ImgDesc d = img_desc(B, image_of_gauss(B, g));
+        int64_t p = off;
+        for (int ty = r.y; ty < r.w; ++ty) {
+            for (int tx = r.x; tx < r.z; ++tx, ++p) {
+                if (p >= capacity) break;
+                const uint32_t key = (uint32_t)(d.tile_base + ty * d.tw + tx);
+                keys[p] = key;
+                vals[p] = (uint32_t)g;
+                for (int ps = 0; ps < rp.passes; ++ps)
+                    atomicAdd(&s_hist[ps * 256 + ((key >> (ps * rp.dbits)) & dmask)], 1u);
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < rp.passes * 256; i += blockDim.x) {
+        const uint32_t v = s_hist[i];
+        if (v) atomicAdd(&hist[i], v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// One stable LSD radix pass (onesweep). Each block takes a ticket, ranks its
+// 4096 keys per digit with warp-level multi-split (items ordered by (warp,
+// round, lane) = input order, so the ranking is stable), resolves its
+// per-digit global offset with a decoupled look-back over lower tickets
+// (bounded spin), and scatters.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kSortThreads) k_onesweep(
+    const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
+    uint32_t* __restrict__ vals_out, const int64_t* __restrict__ k_dev, int64_t capacity, int shift, int dbits,
+    const uint32_t* __restrict__ hist, uint32_t* __restrict__ lookback, uint32_t* __restrict__ ticket,
+    const float4* __restrict__ rec, float4* __restrict__ rec_binned, int32_t n_gauss,
+    uint32_t* __restrict__ status) {
+    constexpr int NW = kSortThreads / 32;
+    __shared__ uint32_t s_wc[NW][256];
+    __shared__ uint32_t s_base[256];
+    __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_ticket;
+    const int K = (int)min(*k_dev, capacity);
+    if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1u);
+    for (int i = threadIdx.x; i < NW * 256; i += kSortThreads) (&s_wc[0][0])[i] = 0;
+    __syncthreads();
+    const int blk = (int)s_ticket;
+    const int64_t start = (int64_t)blk * kSortTile;
+    if (start >= K) return;
+    const int radix = 1 << dbits;
+    const uint32_t mask = (uint32_t)radix - 1;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    uint32_t key[kSortItems], val[kSortItems], lrank[kSortItems];
+    uint32_t dig[kSortItems];
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const int64_t idx = start + warp * 32 * kSortItems + r * 32 + lane;
+        if (idx < K) {
+            key[r] = keys_in[idx];
+            val[r] = vals_in[idx];
+            dig[r] = (key[r] >> shift) & mask;
+        } else {
+            key[r] = 0;
+            val[r] = 0;
+            dig[r] = 256;
+        }
+    }
+    uint32_t* wc = s_wc[warp];
+    const uint32_t ltmask = lanemask_lt();
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const uint32_t dg = dig[r];
+        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+        const int leader = __ffs(peers) - 1;
+        uint32_t base = 0;
+        if (lane == leader && dg < 256) {
+            base = wc[dg];
+            wc[dg] = base + __popc(peers);
+        }
+        base = __shfl_sync(0xffffffffu, base, leader);
+        lrank[r] = base + __popc(peers & ltmask);
+        __syncwarp();
+    }
+    __syncthreads();
+
+    const int d = threadIdx.x;  // kSortThreads == 256 >= radix
+    uint32_t tot = 0;
+    if (d < radix) {
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t v = s_wc[w][d];
+            s_wc[w][d] = tot;
+            tot += v;
+        }
+    }
+    // Global digit base: exclusive scan of this pass's histogram.
+    const uint32_t h = d < radix ? hist[d] : 0u;
+    const uint32_t hex = block_incl_scan<uint32_t>(h, s_warp) - h;
+    if (d < radix) {
+        uint32_t excl = 0;
+        uint32_t* mine = lookback + (size_t)blk * 256 + d;
+        if (blk == 0) {
+            st_release_u32(mine, kFlagPre | tot);
+        } else {
+            st_release_u32(mine, kFlagAgg | tot);
+            int j = blk - 1;
+            uint32_t spins = 0;
+            while (j >= 0) {
+                const uint32_t v = ld_relaxed_u32(lookback + (size_t)j * 256 + d);
+                const uint32_t f = v & (3u << 30);
+                if (f == 0) {
+                    if (++spins > kSpinLimit) {
+                        flag_error(status, kErrTimeout);
+                        break;
+                    }
+                    if (spins > 32) __nanosleep(100);
+                    continue;
+                }
+                excl += v & kValMask;
+                if (f == kFlagPre) break;
+                --j;
+            }
+            st_release_u32(mine, kFlagPre | ((excl + tot) & kValMask));
+        }
+        s_base[d] = hex + excl;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kSortItems; ++r) {
+        const uint32_t dg = dig[r];
+        if (dg < 256) {
+            const uint32_t pos = s_base[dg] + s_wc[warp][dg] + lrank[r];
+            if (pos >= (uint32_t)K) {
+                flag_error(status, kErrBounds);
+                continue;
+            }
+            keys_out[pos] = key[r];
+            vals_out[pos] = val[r];
+            if (rec_binned) {
+                if (val[r] < (uint32_t)n_gauss) {
+                    rec_binned[2 * (size_t)pos] = rec[2 * (size_t)val[r]];
+                    rec_binned[2 * (size_t)pos + 1] = rec[2 * (size_t)val[r] + 1];
+                } else {
+                    flag_error(status, kErrBounds);
+                }
+            }
+        }
+    }
+}
+
+// ranges[t] = [first, last + 1) of key t in the sorted keys.
+__global__ void k_ranges(const uint32_t* __restrict__ keys, const int64_t* __restrict__ k_dev, int64_t capacity,
+                         int2* __restrict__ ranges, int total_tiles) {
+    const int K = (int)min(*k_dev, capacity);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+        const uint32_t t = keys[k];
+        if (t >= (uint32_t)total_tiles) continue;
+        if (k == 0 || keys[k - 1] != t) ranges[t].x = k;
+        if (k == K - 1 || keys[k + 1] != t) ranges[t].y = k + 1;
+    }
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int sm_count() {
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 148;
+    if (!cached[dev]) {
+        int v = 0;
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+        cached[dev] = v;
+    }
+    return cached[dev];
+}
+
+}  // namespace
+
+RadixPlan radix_plan(int total_tiles) {
+    int bits = 1;
+    while (bits < 31 && (int64_t(1) << bits) < (int64_t)total_tiles) ++bits;
+    const int passes = (bits + 7) / 8;
+    const int dbits = (bits + passes - 1) / passes;
+    return {bits, passes, dbits};
+}
+
+BinWs bin_ws_layout(void* base, int64_t n, int64_t capacity, int total_tiles) {
+    const RadixPlan rp = radix_plan(total_tiles);
+    const int64_t nblk = std::max<int64_t>(1, (n + kProjBlock - 1) / kProjBlock);
+    const int64_t sblk = std::max<int64_t>(1, (capacity + kSortTile - 1) / kSortTile);
+    const int64_t cap = std::max<int64_t>(1, capacity);
+    char* b = static_cast<char*>(base);
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> void* {
+        const size_t o = off;
+        off = align_up(off + bytes, 256);
+        return b ? static_cast<void*>(b + o) : nullptr;
+    };
+    BinWs w;
+    w.blk_sum = static_cast<int64_t*>(take(nblk * sizeof(int64_t)));
+    w.keys_tmp = static_cast<uint32_t*>(take(cap * 4));
+    w.vals_tmp = static_cast<uint32_t*>(take(cap * 4));
+    w.hist = static_cast<uint32_t*>(take((size_t)rp.passes * 256 * 4));
+    w.lookback = static_cast<uint32_t*>(take((size_t)rp.passes * sblk * 256 * 4));
+    w.tickets = static_cast<uint32_t*>(take(16));
+    w.bytes = off;
+    return w;
+}
+
+cudaError_t launch_project(const ParamsIn& P, const Batch& B, float4* rec, int4* rect, int32_t* cnt,
+                           int64_t* blk_sum, const ZeroJob& zj, cudaStream_t s) {
+    const int nblk = std::max(1, (B.total_gauss + kProjBlock - 1) / kProjBlock);
+    k_project<<<nblk, kProjBlock, 0, s>>>(P, B, rec, rect, cnt, blk_sum, zj);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin(const int4* rect, const int32_t* cnt, const float4* rec, const Batch& B, int64_t capacity,
+                       const BinWs& ws, bool blk_sum_ready, uint32_t* keys, uint32_t* ids, int2* ranges,
+                       float4* rec_binned, int64_t* pair_off, int64_t* k_dev, int64_t* k_max, uint32_t* status,
+                       cudaStream_t s) {
+    const RadixPlan rp = radix_plan(B.total_tiles);
+    const int n = B.total_gauss;
+    const int nblk = std::max(1, (n + kProjBlock - 1) / kProjBlock);
+    const int64_t sblk = std::max<int64_t>(1, (capacity + kSortTile - 1) / kSortTile);
+    if (!blk_sum_ready) {
+        ZeroJob zj{};
+        zj.p[0] = ws.hist;
+        zj.n32[0] = (int64_t)rp.passes * 256;
+        zj.p[1] = ws.lookback;
+        zj.n32[1] = (int64_t)rp.passes * sblk * 256;
+        zj.p[2] = ws.tickets;
+        zj.n32[2] = 4;
+        zj.p[3] = reinterpret_cast<uint32_t*>(ranges);
+        zj.n32[3] = (int64_t)B.total_tiles * 2;
+        k_blocksum<<<nblk, kProjBlock, 0, s>>>(cnt, n, ws.blk_sum, zj);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    uint32_t* ka = (rp.passes & 1) ? ws.keys_tmp : keys;
+    uint32_t* va = (rp.passes & 1) ? ws.vals_tmp : ids;
+    uint32_t* kb = (rp.passes & 1) ? keys : ws.keys_tmp;
+    uint32_t* vb = (rp.passes & 1) ? ids : ws.vals_tmp;
+    k_emit<<<nblk, kProjBlock, 0, s>>>(rect, cnt, ws.blk_sum, B, capacity, ka, va, pair_off, k_dev, k_max, ws.hist,
+                                       rp, status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    for (int ps = 0; ps < rp.passes; ++ps) {
+        const bool last = ps == rp.passes - 1;
+        k_onesweep<<<(unsigned)sblk, kSortThreads, 0, s>>>(
+            ka, va, kb, vb, k_dev, capacity, ps * rp.dbits, rp.dbits, ws.hist + ps * 256,
+            ws.lookback + (size_t)ps * sblk * 256, ws.tickets + ps, last ? rec : nullptr,
+            last ? rec_binned : nullptr, n, status);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        std::swap(ka, kb);
+        std::swap(va, vb);
+    }
+    const int rblk = std::max(1, std::min<int>(sm_count() * 4, (int)((capacity + 255) / 256)));
+    k_ranges<<<rblk, 256, 0, s>>>(keys, k_dev, capacity, ranges, B.total_tiles);
+    return cudaGetLastError();
+}
+
+}  // namespace gi

@@ -1,0 +1,161 @@
+// common.cuh -- shared device/host helpers of libgi (sm_103a).
+//
+// Data layout (all device memory, caller-owned unless noted):
+//   rec[g]        8 x f32 = (mx, my, A', B', C', c'r, c'g, c'b); the conic
+//                 is pre-scaled so that exp(-sigma) = exp2(-(A'dx^2 +
+//                 B'dx dy + C'dy^2)), A' = A log2(e)/2, B' = B log2(e),
+//                 C' = C log2(e)/2 with Sigma^-1 = [[A, B], [B, C]].
+//   rect[g]       int4 (tx0, ty0, tx1, ty1), image-local tile coordinates.
+//   cnt[g]        int32 number of tiles in rect (0 = culled).
+//   pair_off[g]   int64 exclusive prefix of cnt: index of g's first pair in
+//                 emission order (row-major tiles of the rect).
+//   keys / ids    u32 global tile id / Gaussian id of each pair, sorted by
+//                 tile, ascending Gaussian id inside a tile.
+//   rec_binned[k] the record of ids[k] (tile lists contiguous in memory).
+//   ranges[t]     int2 [begin, end) of global tile t in the sorted pairs.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/gi.h"
+
+namespace gi {
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr int kMaxCapacityLog2 = 30;  // pair indices fit the 30-bit look-back field
+constexpr int64_t kMaxCapacity = (int64_t(1) << kMaxCapacityLog2) - 1;
+
+// Device-side error bits, OR-ed into a status word by kernels.
+enum : uint32_t {
+    kErrCapacity = 1u << 0,  // more pairs than capacity
+    kErrTimeout = 1u << 1,   // a bounded wait gave up
+    kErrBounds = 1u << 2,    // an index check failed
+};
+
+// Per-image descriptor. Pixels of image b live at pix_base + y*W + x.
+struct ImgDesc {
+    int32_t W, H, tw, th;
+    int32_t tile_base;   // first global tile id
+    int32_t gauss_base;  // first Gaussian index
+    int64_t pix_base;    // first pixel index
+};
+
+// Either a single image (by value) or nimg > 1 images in device memory.
+struct Batch {
+    ImgDesc one;
+    const ImgDesc* many;
+    int32_t nimg;
+    int32_t tile;         // tile edge T (8, 16 or 32)
+    int32_t total_tiles;  // sum of tw*th
+    int32_t total_gauss;  // sum of n
+};
+
+__device__ __forceinline__ ImgDesc img_desc(const Batch& b, int i) {
+    return b.nimg == 1 ? b.one : b.many[i];
+}
+
+// Image owning Gaussian g (binary search over gauss_base).
+__device__ __forceinline__ int image_of_gauss(const Batch& b, int g) {
+    if (b.nimg == 1) return 0;
+    int lo = 0, hi = b.nimg - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (b.many[mid].gauss_base <= g) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Image owning global tile t (binary search over tile_base).
+__device__ __forceinline__ int image_of_tile(const Batch& b, int t) {
+    if (b.nimg == 1) return 0;
+    int lo = 0, hi = b.nimg - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (b.many[mid].tile_base <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+// ---------------------------------------------------------------------------
+
+// 2^x on the SFU (MUFU.EX2), flush-to-zero of denormal results.
+__device__ __forceinline__ float ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bounded wait on an mbarrier phase; returns false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t max_iters = 1u << 24) {
+    uint32_t addr = smem_addr(bar);
+    for (uint32_t it = 0; it < max_iters; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// 1-D bulk copy global -> shared (TMA unit), completion counted on `bar`.
+// dst, src 16-byte aligned; bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void flag_error(uint32_t* status, uint32_t bits) {
+    if (status) atomicOr(status, bits);
+}
+
+}  // namespace gi
+
+// Host-side launch check: returns GI_ERR_CUDA from the enclosing function.
+#define GI_CUDA_TRY(expr)                                      \
+    do {                                                       \
+        cudaError_t e_ = (expr);                               \
+        if (e_ != cudaSuccess) return gi::set_cuda_error(e_, #expr); \
+    } while (0)

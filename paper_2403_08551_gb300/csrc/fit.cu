@@ -1,0 +1,308 @@
+// fit.cu -- image fitting contexts (Sec. 3.4): one step = formation,
+// binning, render + L2 loss, backward and an Adam update, for one image or a
+// batch of images of different sizes whose tiles share every launch. The
+// step is five stream-ordered stages with no host round trip (pair counts
+// stay on the device), captured once into a CUDA graph and replayed.
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kernels.cuh"
+
+using namespace gi;
+
+struct gi_fit {
+    int dev = 0;
+    int nimg = 0;
+    int64_t N = 0;
+    int64_t npix = 0;
+    int64_t capacity = 0;
+    Batch B{};
+    AdamCfg adam{};
+    bool use_graph = false;
+    bool stage_events = false;
+    cudaEvent_t ev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    void* arena = nullptr;
+    // carved from arena
+    ImgDesc* d_desc = nullptr;
+    float *params = nullptr, *m = nullptr, *v = nullptr, *grads = nullptr;
+    float *targets = nullptr, *out = nullptr;
+    float4 *rec = nullptr, *rec_binned = nullptr, *dl_tiled = nullptr, *partial = nullptr;
+    int4* rect = nullptr;
+    int32_t* cnt = nullptr;
+    int64_t *pair_off = nullptr, *k_dev = nullptr, *k_max = nullptr;
+    uint32_t *keys = nullptr, *ids = nullptr, *done = nullptr;
+    int2* ranges = nullptr;
+    double* loss = nullptr;
+    int32_t* step = nullptr;
+    BinWs bws{};
+};
+
+namespace {
+
+size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+
+cudaError_t mark(gi_fit* f, int i, cudaStream_t s) {
+    if (!f->stage_events) return cudaSuccess;
+    // Inside a stream capture an external record becomes an event-record node
+    // of the graph, so every replay re-records the event.
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cs);
+    if (e != cudaSuccess) return e;
+    return cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(f->ev[i], s, cudaEventRecordExternal)
+                                               : cudaEventRecord(f->ev[i], s);
+}
+
+cudaError_t enqueue_forward(gi_fit* f, cudaStream_t s) {
+    const RadixPlan rp = radix_plan(f->B.total_tiles);
+    const int64_t sblk = std::max<int64_t>(1, (f->capacity + kSortTile - 1) / kSortTile);
+    ZeroJob zj{};
+    zj.p[0] = f->bws.hist;
+    zj.n32[0] = (int64_t)rp.passes * 256;
+    zj.p[1] = f->bws.lookback;
+    zj.n32[1] = (int64_t)rp.passes * sblk * 256;
+    zj.p[2] = f->bws.tickets;
+    zj.n32[2] = 4;
+    zj.p[3] = reinterpret_cast<uint32_t*>(f->ranges);
+    zj.n32[3] = (int64_t)f->B.total_tiles * 2;
+    zj.p[4] = reinterpret_cast<uint32_t*>(f->loss);
+    zj.n32[4] = (int64_t)f->nimg * 2;
+    cudaError_t e = mark(f, 0, s);
+    if (e == cudaSuccess)
+        e = launch_project(params_aos(f->params), f->B, f->rec, f->rect, f->cnt, f->bws.blk_sum, zj, s);
+    if (e == cudaSuccess) e = mark(f, 1, s);
+    if (e == cudaSuccess)
+        e = launch_bin(f->rect, f->cnt, f->rec, f->B, f->capacity, f->bws, true, f->keys, f->ids, f->ranges,
+                       f->rec_binned, f->pair_off, f->k_dev, f->k_max, device_status(), s);
+    if (e == cudaSuccess) e = mark(f, 2, s);
+    if (e == cudaSuccess)
+        e = launch_render(f->rec_binned, f->ranges, f->B, f->targets, f->out, nullptr, f->dl_tiled, f->loss,
+                          device_status(), s);
+    if (e == cudaSuccess) e = mark(f, 3, s);
+    return e;
+}
+
+cudaError_t enqueue_step(gi_fit* f, cudaStream_t s) {
+    cudaError_t e = enqueue_forward(f, s);
+    if (e != cudaSuccess) return e;
+    e = launch_backward(f->rec_binned, f->keys, f->ids, f->rect, f->pair_off, f->dl_tiled, f->B, f->k_dev,
+                        f->capacity, f->partial, s);
+    if (e == cudaSuccess) e = mark(f, 4, s);
+    if (e == cudaSuccess)
+        e = launch_reduce(f->partial, f->pair_off, f->cnt, f->capacity, (int32_t)f->N, params_aos(f->params),
+                          nullptr, nullptr, nullptr, nullptr, &f->adam, f->params, f->m, f->v, f->grads, s);
+    if (e == cudaSuccess) e = mark(f, 5, s);
+    return e;
+}
+
+void release(gi_fit* f) {
+    if (!f) return;
+    if (f->exec) cudaGraphExecDestroy(f->exec);
+    if (f->graph) cudaGraphDestroy(f->graph);
+    if (f->cap_stream) cudaStreamDestroy(f->cap_stream);
+    for (cudaEvent_t e : f->ev)
+        if (e) cudaEventDestroy(e);
+    if (f->arena) cudaFree(f->arena);
+    delete f;
+}
+
+}  // namespace
+
+extern "C" {
+
+gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
+    if (!d || !out) return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: NULL argument");
+    *out = nullptr;
+    if (d->n_images < 1 || !d->widths || !d->heights || !d->counts || !d->targets || !d->params)
+        return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: bad image list or NULL buffer");
+    if (d->tile != 8 && d->tile != 16 && d->tile != 32)
+        return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: tile must be 8, 16 or 32");
+    if (d->capacity < 1 || d->capacity > kMaxCapacity)
+        return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: capacity outside [1, 2^30)");
+    if ((reinterpret_cast<uintptr_t>(d->params) & 15) != 0)
+        return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: params must be 16-byte aligned");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+
+    std::vector<ImgDesc> desc(d->n_images);
+    int64_t tiles = 0, gauss = 0, pix = 0;
+    for (int i = 0; i < d->n_images; ++i) {
+        const int W = d->widths[i], H = d->heights[i], n = d->counts[i];
+        if (W <= 0 || H <= 0 || n < 0) return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: bad image %d", i);
+        const int tw = (W + d->tile - 1) / d->tile, th = (H + d->tile - 1) / d->tile;
+        desc[i] = ImgDesc{W, H, tw, th, (int32_t)tiles, (int32_t)gauss, pix};
+        tiles += (int64_t)tw * th;
+        gauss += n;
+        pix += (int64_t)W * H;
+    }
+    if (tiles >= (int64_t(1) << 30) || gauss >= (int64_t(1) << 31) - 1)
+        return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: batch too large");
+
+    gi_fit* f = new (std::nothrow) gi_fit();
+    if (!f) return set_error(GI_ERR_NO_MEMORY, "gi_fit_create: host allocation failed");
+    cudaGetDevice(&f->dev);
+    f->nimg = d->n_images;
+    f->N = gauss;
+    f->npix = pix;
+    f->capacity = d->capacity;
+    f->use_graph = d->use_graph != 0;
+    f->stage_events = d->stage_events != 0;
+    f->B.one = desc[0];
+    f->B.nimg = d->n_images;
+    f->B.tile = d->tile;
+    f->B.total_tiles = (int32_t)tiles;
+    f->B.total_gauss = (int32_t)gauss;
+
+    const int64_t N = std::max<int64_t>(1, gauss), P = std::max<int64_t>(1, pix);
+    const int npx = d->tile * d->tile;
+    const BinWs probe = bin_ws_layout(nullptr, N, f->capacity, (int)tiles);
+    size_t sz[] = {
+        up256(sizeof(ImgDesc) * d->n_images),   // 0 desc
+        up256((size_t)N * 32), up256((size_t)N * 32), up256((size_t)N * 32), up256((size_t)N * 32),  // 1-4
+        up256((size_t)P * 12), up256((size_t)P * 12),                                                // 5-6
+        up256((size_t)N * 32),                                  // 7 rec
+        up256((size_t)f->capacity * 32),                        // 8 rec_binned
+        up256((size_t)tiles * npx * 16),                        // 9 dl_tiled
+        up256((size_t)f->capacity * 32),                        // 10 partial
+        up256((size_t)N * 16),                                  // 11 rect
+        up256((size_t)N * 4),                                   // 12 cnt
+        up256((size_t)(N + 1) * 8),                             // 13 pair_off
+        256,                                                    // 14 k_dev, k_max
+        up256((size_t)f->capacity * 4), up256((size_t)f->capacity * 4),  // 15-16 keys ids
+        up256((size_t)tiles * 8),                               // 17 ranges
+        up256((size_t)d->n_images * 8),                         // 18 loss
+        256,                                                    // 19 step, done
+        up256(probe.bytes),                                     // 20 bin ws
+    };
+    size_t total = 0;
+    for (size_t x : sz) total += x;
+    cudaError_t e = cudaMalloc(&f->arena, total);
+    if (e != cudaSuccess) {
+        release(f);
+        return set_error(GI_ERR_NO_MEMORY, "gi_fit_create: cudaMalloc(%zu) failed: %s", total, cudaGetErrorString(e));
+    }
+    char* p = static_cast<char*>(f->arena);
+    auto at = [&](int i) {
+        size_t off = 0;
+        for (int j = 0; j < i; ++j) off += sz[j];
+        return p + off;
+    };
+    f->d_desc = reinterpret_cast<ImgDesc*>(at(0));
+    f->params = reinterpret_cast<float*>(at(1));
+    f->m = reinterpret_cast<float*>(at(2));
+    f->v = reinterpret_cast<float*>(at(3));
+    f->grads = reinterpret_cast<float*>(at(4));
+    f->targets = reinterpret_cast<float*>(at(5));
+    f->out = reinterpret_cast<float*>(at(6));
+    f->rec = reinterpret_cast<float4*>(at(7));
+    f->rec_binned = reinterpret_cast<float4*>(at(8));
+    f->dl_tiled = reinterpret_cast<float4*>(at(9));
+    f->partial = reinterpret_cast<float4*>(at(10));
+    f->rect = reinterpret_cast<int4*>(at(11));
+    f->cnt = reinterpret_cast<int32_t*>(at(12));
+    f->pair_off = reinterpret_cast<int64_t*>(at(13));
+    f->k_dev = reinterpret_cast<int64_t*>(at(14));
+    f->k_max = f->k_dev + 1;
+    f->keys = reinterpret_cast<uint32_t*>(at(15));
+    f->ids = reinterpret_cast<uint32_t*>(at(16));
+    f->ranges = reinterpret_cast<int2*>(at(17));
+    f->loss = reinterpret_cast<double*>(at(18));
+    f->step = reinterpret_cast<int32_t*>(at(19));
+    f->done = reinterpret_cast<uint32_t*>(at(19) + 16);
+    f->bws = bin_ws_layout(at(20), N, f->capacity, (int)tiles);
+    f->B.many = d->n_images > 1 ? f->d_desc : nullptr;
+
+    f->adam.lr[0] = d->lr_means;
+    f->adam.lr[1] = d->lr_chol;
+    f->adam.lr[2] = d->lr_color;
+    f->adam.beta1 = d->beta1;
+    f->adam.beta2 = d->beta2;
+    f->adam.eps = d->eps;
+    f->adam.step = f->step;
+    f->adam.done = f->done;
+
+#define FIT_TRY(x)                                      \
+    do {                                                \
+        cudaError_t e_ = (x);                           \
+        if (e_ != cudaSuccess) {                        \
+            release(f);                                 \
+            return set_cuda_error(e_, "gi_fit_create: " #x); \
+        }                                               \
+    } while (0)
+    FIT_TRY(cudaMemsetAsync(f->arena, 0, total, s));
+    FIT_TRY(cudaMemcpyAsync(f->d_desc, desc.data(), sizeof(ImgDesc) * desc.size(), cudaMemcpyHostToDevice, s));
+    FIT_TRY(cudaMemcpyAsync(f->params, d->params, (size_t)gauss * 32, cudaMemcpyDeviceToDevice, s));
+    FIT_TRY(cudaMemcpyAsync(f->targets, d->targets, (size_t)pix * 12, cudaMemcpyDeviceToDevice, s));
+    FIT_TRY(cudaStreamSynchronize(s));
+    FIT_TRY(cudaStreamCreateWithFlags(&f->cap_stream, cudaStreamNonBlocking));
+    if (f->stage_events)
+        for (cudaEvent_t& ev : f->ev) FIT_TRY(cudaEventCreate(&ev));
+    if (f->use_graph) {
+        FIT_TRY(cudaStreamBeginCapture(f->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t ce = enqueue_step(f, f->cap_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t ee = cudaStreamEndCapture(f->cap_stream, &g);
+        f->graph = g;
+        FIT_TRY(ce);
+        FIT_TRY(ee);
+        FIT_TRY(cudaGraphInstantiate(&f->exec, f->graph, 0));
+    }
+#undef FIT_TRY
+    *out = f;
+    return GI_OK;
+}
+
+gi_status gi_fit_step(gi_fit* f, int32_t steps, gi_stream stream) {
+    if (!f || steps < 0) return set_error(GI_ERR_INVALID_ARG, "gi_fit_step: bad argument");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    for (int i = 0; i < steps; ++i) {
+        cudaError_t e = f->exec ? cudaGraphLaunch(f->exec, s) : enqueue_step(f, s);
+        if (e != cudaSuccess) return set_cuda_error(e, "gi_fit_step");
+    }
+    return GI_OK;
+}
+
+gi_status gi_fit_render(gi_fit* f, gi_stream stream) {
+    if (!f) return set_error(GI_ERR_INVALID_ARG, "gi_fit_render: NULL fit");
+    cudaError_t e = enqueue_forward(f, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return set_cuda_error(e, "gi_fit_render");
+    return GI_OK;
+}
+
+gi_status gi_fit_pointer(gi_fit* f, int32_t what, void** ptr) {
+    if (!f || !ptr) return set_error(GI_ERR_INVALID_ARG, "gi_fit_pointer: NULL argument");
+    switch (what) {
+        case GI_FIT_PARAMS: *ptr = f->params; break;
+        case GI_FIT_ADAM_M: *ptr = f->m; break;
+        case GI_FIT_ADAM_V: *ptr = f->v; break;
+        case GI_FIT_GRADS: *ptr = f->grads; break;
+        case GI_FIT_OUT: *ptr = f->out; break;
+        case GI_FIT_LOSS: *ptr = f->loss; break;
+        case GI_FIT_STEP: *ptr = f->step; break;
+        case GI_FIT_K: *ptr = f->k_dev; break;
+        case GI_FIT_TARGET: *ptr = f->targets; break;
+        default: return set_error(GI_ERR_INVALID_ARG, "gi_fit_pointer: unknown field %d", what);
+    }
+    return GI_OK;
+}
+
+gi_status gi_fit_stage_times(gi_fit* f, float* ms) {
+    if (!f || !ms) return set_error(GI_ERR_INVALID_ARG, "gi_fit_stage_times: NULL argument");
+    if (!f->stage_events) return set_error(GI_ERR_INVALID_ARG, "gi_fit_stage_times: created without stage_events");
+    GI_CUDA_TRY(cudaEventSynchronize(f->ev[5]));
+    for (int i = 0; i < 5; ++i) GI_CUDA_TRY(cudaEventElapsedTime(&ms[i], f->ev[i], f->ev[i + 1]));
+    return GI_OK;
+}
+
+gi_status gi_fit_destroy(gi_fit* f) {
+    if (f) {
+        cudaSetDevice(f->dev);
+        cudaDeviceSynchronize();
+        release(f);
+    }
+    return GI_OK;
+}
+
+}  // extern "C"

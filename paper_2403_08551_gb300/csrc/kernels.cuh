@@ -1,0 +1,96 @@
+// kernels.cuh -- internal launchers shared by the C-ABI (abi.cu) and the
+// fit context (fit.cu). Not part of the public ABI.
+#pragma once
+#include "common.cuh"
+
+namespace gi {
+
+// Parameter access: AoS [n][8] (mx,my,l1,l2,l3,cr,cg,cb) or SoA arrays.
+struct ParamsIn {
+    const float* means;  // stride ms floats per Gaussian
+    const float* chol;   // stride ls
+    const float* color;  // stride cs
+    int32_t ms, ls, cs;
+};
+
+inline ParamsIn params_soa(const float* m, const float* l, const float* c) { return {m, l, c, 2, 3, 3}; }
+inline ParamsIn params_aos(const float* p) { return {p, p + 2, p + 5, 8, 8, 8}; }
+
+// Regions zeroed by the projection kernel before binning: p[r] (16-byte
+// aligned) holds n32[r] 32-bit words.
+struct ZeroJob {
+    uint32_t* p[6];
+    int64_t n32[6];
+};
+
+// Radix plan for the tile keys.
+struct RadixPlan {
+    int bits;    // total key bits
+    int passes;  // LSD passes
+    int dbits;   // digit bits per pass (<= 8)
+};
+RadixPlan radix_plan(int total_tiles);
+
+constexpr int kProjBlock = 1024;       // Gaussians per projection / emit block
+constexpr int kSortThreads = 256;      // threads per onesweep block
+constexpr int kSortItems = 16;         // keys per thread
+constexpr int kSortTile = kSortThreads * kSortItems;  // keys per onesweep block
+
+// Binning workspace carve-up.
+struct BinWs {
+    int64_t* blk_sum;     // [ceil(n / kProjBlock)]
+    uint32_t* keys_tmp;   // [capacity]
+    uint32_t* vals_tmp;   // [capacity]
+    uint32_t* hist;       // [passes][256]
+    uint32_t* lookback;   // [passes][sort_blocks][256]
+    uint32_t* tickets;    // [4]
+    size_t bytes;
+};
+BinWs bin_ws_layout(void* base, int64_t n, int64_t capacity, int total_tiles);
+
+// Launchers (stream-ordered, no host synchronisation).
+cudaError_t launch_project(const ParamsIn& P, const Batch& B, float4* rec, int4* rect, int32_t* cnt,
+                           int64_t* blk_sum, const ZeroJob& zj, cudaStream_t s);
+cudaError_t launch_bin(const int4* rect, const int32_t* cnt, const float4* rec, const Batch& B,
+                       int64_t capacity, const BinWs& ws, bool blk_sum_ready, uint32_t* keys,
+                       uint32_t* ids, int2* ranges, float4* rec_binned, int64_t* pair_off,
+                       int64_t* k_dev, int64_t* k_max, uint32_t* status, cudaStream_t s);
+
+// Forward render: out (HWC), optional loss sum (double per image), dL/dC in
+// HWC (dl_hwc) and/or tiled float4 (dl_tiled).
+cudaError_t launch_render(const float4* rec_binned, const int2* ranges, const Batch& B,
+                          const float* target, float* out, float* dl_hwc, float4* dl_tiled,
+                          double* loss_sum, uint32_t* status, cudaStream_t s);
+
+// Backward: per-pair partial sums (8 floats per pair at its emission index).
+cudaError_t launch_backward(const float4* rec_binned, const uint32_t* keys, const uint32_t* ids,
+                            const int4* rect, const int64_t* pair_off, const float4* dl_tiled,
+                            const Batch& B, const int64_t* k_dev, int64_t capacity, float4* partial,
+                            cudaStream_t s);
+cudaError_t launch_pack_dl(const float* dl_hwc, const Batch& B, float4* dl_tiled, cudaStream_t s);
+
+struct AdamCfg {
+    float lr[3];  // means, chol, color
+    float beta1, beta2, eps;
+    int32_t* step;  // device counter (1-based step of the update being made = *step + 1)
+    uint32_t* done; // device counter for the last-block step increment
+};
+
+// Reduce partials per Gaussian, chain conic -> Cholesky; then either write
+// gradients (g_means/g_chol/g_color/g_conic, SoA, any may be null) or, when
+// adam != null, update AoS params/m/v in place (grads_aos optional).
+cudaError_t launch_reduce(const float4* partial, const int64_t* pair_off, const int32_t* cnt,
+                          int64_t capacity, int32_t n, const ParamsIn& P, float* g_means,
+                          float* g_chol, float* g_color, float* g_conic, const AdamCfg* adam,
+                          float* params, float* m, float* v, float* grads_aos, cudaStream_t s);
+
+cudaError_t launch_vq_decode(const uint16_t* means16, const uint8_t* idx, const float* cb, int32_t n,
+                             int32_t stages, int32_t cb_size, float* means, float* chol, float* color,
+                             int32_t out_stride_aos, cudaStream_t s);
+
+// Per-device error word that kernels OR error bits into.
+uint32_t* device_status();
+gi_status set_cuda_error(cudaError_t e, const char* what);
+gi_status set_error(gi_status st, const char* fmt, ...);
+
+}  // namespace gi

@@ -1,0 +1,202 @@
+// render.cu -- forward accumulated-summation render (Sec. 3.2, Eq. 7) with
+// the L2 reconstruction loss (Sec. 3.4) fused into the epilogue.
+//
+//   C_i = sum over the tile's list (ascending g) of c'_g exp(-sigma_g(i)),
+//   sigma = 1/2 d^T Sigma^-1 d, d = (x + 0.5, y + 0.5) - mu.
+//
+// One CTA per tile. The tile's records are contiguous in rec_binned and are
+// staged into shared memory by the TMA unit (1-D bulk copy, mbarrier
+// completion). SPLIT warp groups each take a fixed contiguous share of every
+// staged batch and accumulate all of the tile's pixels in FP32 registers (a
+// lane owns a strip of PX pixels of one row, so per-row terms are hoisted);
+// the SPLIT partial images are then summed in shared memory in a fixed order.
+// The result is deterministic run to run. exp(-sigma) is evaluated as
+// exp2 on the SFU (MUFU.EX2) with the log2(e) factor folded into the conic.
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace gi {
+namespace {
+
+template <int T_, int PX_, int SPLIT_>
+struct RCfg {
+    static constexpr int T = T_, PX = PX_, SPLIT = SPLIT_;
+    static constexpr int kPix = T * T;
+    static constexpr int kStrips = kPix / PX;
+    static constexpr int kStripsPerRow = T / PX;
+    static constexpr int kWarpsPerGroup = kStrips / 32;
+    static constexpr int kWarps = kWarpsPerGroup * SPLIT;
+    static constexpr int kThreads = kWarps * 32;
+    static constexpr int kStage = 768;  // records per staging batch (24 KB)
+    static constexpr int kStageBytes = kStage * 32;
+    static constexpr int kPartBytes = SPLIT * 3 * kPix * 4;
+    static constexpr int kSmem = kStageBytes > kPartBytes ? kStageBytes : kPartBytes;
+    static_assert(kStrips % 32 == 0, "strips must fill warps");
+};
+
+template <class Cfg>
+__global__ void __launch_bounds__(Cfg::kThreads) k_render(const float4* __restrict__ rec_binned,
+                                                          const int2* __restrict__ ranges, Batch B,
+                                                          const float* __restrict__ target, float* __restrict__ out,
+                                                          float* __restrict__ dl_hwc, float4* __restrict__ dl_tiled,
+                                                          double* __restrict__ loss_sum, uint32_t* status) {
+    constexpr int T = Cfg::T, PX = Cfg::PX, SPLIT = Cfg::SPLIT, NT = Cfg::kThreads, NPIX = Cfg::kPix;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float4* srec = reinterpret_cast<float4*>(smem);
+    float* spart = reinterpret_cast<float*>(smem);  // reused after the last batch
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ float s_red[32];
+
+    const int t = blockIdx.x;
+    const int bimg = image_of_tile(B, t);
+    const ImgDesc d = img_desc(B, bimg);
+    const int lt = t - d.tile_base;
+    const int tx = lt % d.tw, ty = lt / d.tw;
+    const int x0 = tx * T, y0 = ty * T;
+    const int2 rg = ranges[t];
+    const int L = rg.y - rg.x;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int split = warp / Cfg::kWarpsPerGroup;
+    const int strip = (warp % Cfg::kWarpsPerGroup) * 32 + lane;
+    const int row = strip / Cfg::kStripsPerRow;
+    const int col0 = (strip % Cfg::kStripsPerRow) * PX;
+    const float py = (float)(y0 + row) + 0.5f;
+    const float px0 = (float)(x0 + col0) + 0.5f;
+
+    float acc[PX][3];
+#pragma unroll
+    for (int i = 0; i < PX; ++i) acc[i][0] = acc[i][1] = acc[i][2] = 0.f;
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int j0 = 0; j0 < L && ok; j0 += Cfg::kStage) {
+        const int nb = min(Cfg::kStage, L - j0);
+        if (threadIdx.x == 0) {
+            mbar_arrive_expect_tx(&bar, (uint32_t)nb * 32u);
+            bulk_g2s(srec, rec_binned + 2 * ((int64_t)rg.x + j0), (uint32_t)nb * 32u, &bar);
+        }
+        bool arrived = mbar_wait(&bar, phase);
+        if (!arrived) {
+            // Give up on this tile after a second bounded wait for the copy.
+            flag_error(status, kErrTimeout);
+            mbar_wait(&bar, phase);
+        }
+        ok = __syncthreads_and(arrived) != 0;  // block-uniform decision
+        phase ^= 1u;
+        const int k0 = (nb * split) / SPLIT, k1 = (nb * (split + 1)) / SPLIT;
+        if (ok) {
+#pragma unroll 2
+            for (int k = k0; k < k1; ++k) {
+                const float4 r0 = srec[2 * k];      // mx, my, A', B'
+                const float4 r1 = srec[2 * k + 1];  // C', c'r, c'g, c'b
+                const float dy = py - r0.y;
+                const float bdy = r0.w * dy;
+                const float cdy2 = r1.x * dy * dy;
+                const float dx0 = px0 - r0.x;
+#pragma unroll
+                for (int i = 0; i < PX; ++i) {
+                    const float dx = dx0 + (float)i;
+                    const float s = fmaf(fmaf(r0.z, dx, bdy), dx, cdy2);
+                    const float w = ex2(-s);
+                    acc[i][0] = fmaf(r1.y, w, acc[i][0]);
+                    acc[i][1] = fmaf(r1.z, w, acc[i][1]);
+                    acc[i][2] = fmaf(r1.w, w, acc[i][2]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+
+    // Partial images of the SPLIT groups -> shared memory, [split][c][pixel].
+#pragma unroll
+    for (int i = 0; i < PX; ++i) {
+        const int p = row * T + col0 + i;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) spart[(split * 3 + c) * NPIX + p] = acc[i][c];
+    }
+    __syncthreads();
+
+    const float scale = 2.0f / (3.0f * (float)d.W * (float)d.H);
+    float lsum = 0.f;
+    for (int p = threadIdx.x; p < NPIX; p += NT) {
+        float C[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float s = 0.f;
+#pragma unroll
+            for (int sp = 0; sp < SPLIT; ++sp) s += spart[(sp * 3 + c) * NPIX + p];
+            C[c] = s;
+        }
+        const int x = x0 + p % T, y = y0 + p / T;
+        float dl[3] = {0.f, 0.f, 0.f};
+        if (x < d.W && y < d.H) {
+            const int64_t pix = d.pix_base + (int64_t)y * d.W + x;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) out[3 * pix + c] = C[c];
+            if (target) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    const float r = C[c] - target[3 * pix + c];
+                    lsum = fmaf(r, r, lsum);
+                    dl[c] = r * scale;
+                }
+                if (dl_hwc) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) dl_hwc[3 * pix + c] = dl[c];
+                }
+            }
+        }
+        if (dl_tiled) dl_tiled[(int64_t)t * NPIX + p] = make_float4(dl[0], dl[1], dl[2], 0.f);
+    }
+    if (target && loss_sum) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+        if (lane == 0) s_red[warp] = lsum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float s = 0.f;
+            for (int w = 0; w < Cfg::kWarps; ++w) s += s_red[w];
+            atomicAdd(&loss_sum[bimg], (double)s);
+        }
+    }
+}
+
+template <class Cfg>
+cudaError_t launch_cfg(const float4* rec_binned, const int2* ranges, const Batch& B, const float* target,
+                       float* out, float* dl_hwc, float4* dl_tiled, double* loss_sum, uint32_t* status,
+                       cudaStream_t s) {
+    static_assert(Cfg::kSmem <= 48 * 1024, "dynamic shared memory above the default limit");
+    if (B.total_tiles <= 0) return cudaSuccess;
+    k_render<Cfg><<<B.total_tiles, Cfg::kThreads, Cfg::kSmem, s>>>(rec_binned, ranges, B, target, out, dl_hwc,
+                                                                   dl_tiled, loss_sum, status);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_render(const float4* rec_binned, const int2* ranges, const Batch& B, const float* target,
+                          float* out, float* dl_hwc, float4* dl_tiled, double* loss_sum, uint32_t* status,
+                          cudaStream_t s) {
+    switch (B.tile) {
+        case 8:
+            return launch_cfg<RCfg<8, 2, 4>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
+                                             status, s);
+        case 16:
+            return launch_cfg<RCfg<16, 8, 8>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
+                                              status, s);
+        case 32:
+            return launch_cfg<RCfg<32, 8, 2>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
+                                              status, s);
+        default:
+            return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace gi

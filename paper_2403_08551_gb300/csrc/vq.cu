@@ -1,0 +1,99 @@
+// vq.cu -- codec decode (Sec. 3.3): FP16 positions, and Cholesky / colour
+// attributes as the sum over M residual-VQ stages of codebook rows,
+//   hat c^M = sum_{k=1..M} C^k[i^k].
+// The result equals the sum evaluated exactly and rounded once to FP32: for
+// M <= 2 a single FP32 addition already is that (rounding a double-precision
+// sum of two floats to float is innocuous since 53 >= 2*24 + 2); for M > 2
+// the stages are accumulated in FP64 and rounded once.
+#include <algorithm>
+
+#include <cuda_fp16.h>
+
+#include "kernels.cuh"
+
+namespace gi {
+namespace {
+
+__global__ void __launch_bounds__(256) k_vq_decode(const uint16_t* __restrict__ means16,
+                                                   const uint8_t* __restrict__ idx, const float* __restrict__ cb,
+                                                   int n, int stages, int cbs, float* __restrict__ means,
+                                                   float* __restrict__ chol, float* __restrict__ color,
+                                                   int aos_stride, uint32_t* status) {
+    extern __shared__ float scb[];  // [2][stages][cbs][3]
+    const int ncb = 2 * stages * cbs * 3;
+    for (int i = threadIdx.x; i < ncb; i += blockDim.x) scb[i] = cb[i];
+    __syncthreads();
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+        const float mx = __half2float(__ushort_as_half(means16[2 * (size_t)g]));
+        const float my = __half2float(__ushort_as_half(means16[2 * (size_t)g + 1]));
+        float o[2][3];
+        for (int a = 0; a < 2; ++a) {
+            if (stages <= 2) {
+                float acc[3] = {0.f, 0.f, 0.f};
+                for (int s = 0; s < stages; ++s) {
+                    int i = idx[((size_t)a * stages + s) * n + g];
+                    if (i >= cbs) {  // index outside the codebook: skip the read
+                        flag_error(status, kErrBounds);
+                        i = 0;
+                    }
+                    const float* row = scb + (((size_t)a * stages + s) * cbs + i) * 3;
+                    acc[0] = __fadd_rn(acc[0], row[0]);
+                    acc[1] = __fadd_rn(acc[1], row[1]);
+                    acc[2] = __fadd_rn(acc[2], row[2]);
+                }
+                o[a][0] = acc[0]; o[a][1] = acc[1]; o[a][2] = acc[2];
+            } else {
+                double acc[3] = {0.0, 0.0, 0.0};
+                for (int s = 0; s < stages; ++s) {
+                    int i = idx[((size_t)a * stages + s) * n + g];
+                    if (i >= cbs) {
+                        flag_error(status, kErrBounds);
+                        i = 0;
+                    }
+                    const float* row = scb + (((size_t)a * stages + s) * cbs + i) * 3;
+                    acc[0] += (double)row[0];
+                    acc[1] += (double)row[1];
+                    acc[2] += (double)row[2];
+                }
+                o[a][0] = (float)acc[0]; o[a][1] = (float)acc[1]; o[a][2] = (float)acc[2];
+            }
+        }
+        if (aos_stride == 8) {
+            float4* p = reinterpret_cast<float4*>(means) + 2 * (size_t)g;
+            p[0] = make_float4(mx, my, o[0][0], o[0][1]);
+            p[1] = make_float4(o[0][2], o[1][0], o[1][1], o[1][2]);
+        } else {
+            means[2 * (size_t)g] = mx;
+            means[2 * (size_t)g + 1] = my;
+            chol[3 * (size_t)g] = o[0][0];
+            chol[3 * (size_t)g + 1] = o[0][1];
+            chol[3 * (size_t)g + 2] = o[0][2];
+            color[3 * (size_t)g] = o[1][0];
+            color[3 * (size_t)g + 1] = o[1][1];
+            color[3 * (size_t)g + 2] = o[1][2];
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_vq_decode(const uint16_t* means16, const uint8_t* idx, const float* cb, int32_t n, int32_t stages,
+                             int32_t cb_size, float* means, float* chol, float* color, int32_t out_stride_aos,
+                             cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const size_t smem = (size_t)2 * stages * cb_size * 3 * sizeof(float);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k_vq_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 148;
+    const int blocks = std::max(1, std::min((n + 255) / 256, nsm * 4));
+    k_vq_decode<<<blocks, 256, smem, s>>>(means16, idx, cb, n, stages, cb_size, means, chol, color, out_stride_aos,
+                                          device_status());
+    return cudaGetLastError();
+}
+
+}  // namespace gi

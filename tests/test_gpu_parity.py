@@ -1,0 +1,257 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+Tolerances (written where used):
+  support rect, counts, binning keys/ids/ranges/pair offsets: bit-exact;
+  rendered pixels: |C - C_ref| <= 1e-5 * max(1, |C_ref|);
+  gradients, per parameter group:
+      |g - g_ref| <= 1e-4 * max(|g_ref|, 1e-3 ||g_ref||_inf)
+   or |g - g_ref| <= 16 u |g|_abs   (u = 2^-24, the FP32 unit roundoff;
+      |g|_abs = the oracle's sum over pixels of |per-pixel contribution|),
+   the second clause being the error bound of an FP32 sum whose terms cancel;
+   at most 0.1 % of the elements may rely on it;
+  codec decode: bit-exact.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PIX_TOL = 1e-5
+GRAD_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def gi():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2403_08551_gb300 as m
+    m.load()
+    return m
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def check_pixels(out, ref):
+    out = out.detach().cpu().numpy().astype(np.float64)
+    err = np.abs(out - ref)
+    tol = PIX_TOL * np.maximum(1.0, np.abs(ref))
+    assert np.all(err <= tol), f"max pixel err {err.max():.3e}"
+    return err.max()
+
+
+U32 = 2.0 ** -24
+COND_ULPS = 16
+COND_FRACTION = 1e-3
+
+
+def check_grads(g, ref, name, absref=None, rel=GRAD_TOL):
+    g = g.detach().cpu().numpy().astype(np.float64)
+    scale = np.abs(ref).max()
+    err = np.abs(g - ref)
+    tol = rel * np.maximum(np.abs(ref), 1e-3 * scale)
+    bad = err > tol
+    if absref is not None:
+        cond = bad & (err <= COND_ULPS * U32 * absref)
+        assert cond.mean() <= COND_FRACTION, f"{name}: {cond.sum()} elements need the conditioning bound"
+        bad &= ~cond
+    assert not bad.any(), (f"{name}: {bad.sum()} of {bad.size} outside tolerance; worst rel "
+                           f"{(err / np.maximum(np.abs(ref), 1e-3 * scale)).max():.3e}")
+
+
+def run_gpu(gi, means, chol, color, target, T, capacity=None):
+    H, W, _ = target.shape
+    m, l, c = dev(means), dev(chol), dev(color)
+    rec, rect, cnt = gi.project(m, l, c, W, H, T)
+    bins = gi.bin_tiles(rect, cnt, rec, W, H, T, capacity=capacity)
+    out, dl, loss = gi.render(bins, W, H, T, target=dev(target), want_dl=True)
+    gm, gl, gc, gq = gi.render_backward(bins, rect, cnt, l, dl, W, H, T, want_conic=True)
+    torch.cuda.synchronize()
+    return dict(rec=rec, rect=rect, cnt=cnt, bins=bins, out=out, dl=dl, loss=loss, gm=gm, gl=gl, gc=gc, gq=gq)
+
+
+CASES = [
+    # (W, H, n, T, seed): several tiles and ragged edges
+    (256, 256, 2000, 16, 0),   # the small parity workload (256x256, 2k, 16x16 tiles)
+    (100, 70, 300, 8, 1),
+    (161, 97, 500, 16, 2),
+    (130, 99, 400, 32, 3),
+    (64, 48, 1, 16, 4),
+]
+
+
+@pytest.mark.parametrize("W,H,n,T,seed", CASES)
+def test_forward_backward_matches_oracle(gi, W, H, n, T, seed):
+    target = synth.image(W, H, seed, n_blobs=20)
+    means, chol, color = synth.init_gaussians(n, W, H, seed)
+    g = run_gpu(gi, means, chol, color, target, T)
+    ref = oracle.forward_backward(means, chol, color, target, T)
+    # formation: support rectangles and counts bit-exact; conic to FP32 rounding
+    np.testing.assert_array_equal(g["rect"].cpu().numpy(), ref["rect"])
+    np.testing.assert_array_equal(g["cnt"].cpu().numpy(), ref["cnt"])
+    q = oracle.conic(chol)
+    rec = g["rec"].cpu().numpy().astype(np.float64)
+    live = ref["cnt"] > 0
+    h = 0.5 * oracle.LOG2E
+    np.testing.assert_allclose(rec[live, 2], q[live, 0] * h, rtol=2e-6)
+    np.testing.assert_allclose(rec[live, 4], q[live, 2] * h, rtol=2e-6)
+    np.testing.assert_allclose(rec[live, 3], q[live, 1] * 2 * h, rtol=2e-6, atol=2e-6 * np.abs(q[live, 1]).max())
+    # binning bit-exact
+    b = g["bins"]
+    K = ref["ids"].shape[0]
+    assert b.K == K
+    np.testing.assert_array_equal(b.ids[:K].cpu().numpy().astype(np.uint32), ref["ids"])
+    np.testing.assert_array_equal(b.ranges.cpu().numpy(), ref["ranges"])
+    np.testing.assert_array_equal(b.pair_off.cpu().numpy(), ref["pair_off"])
+    tw, th = oracle.tiles(W, H, T)
+    key_ref = np.repeat(np.arange(tw * th), ref["ranges"][:, 1] - ref["ranges"][:, 0])
+    np.testing.assert_array_equal(b.keys[:K].cpu().numpy(), key_ref)
+    # render, loss, dL/dC
+    check_pixels(g["out"], ref["out"])
+    assert float(g["loss"].item()) == pytest.approx(ref["loss"], rel=1e-5)
+    np.testing.assert_allclose(g["dl"].cpu().numpy(), ref["dldc"], rtol=1e-4,
+                               atol=1e-4 * np.abs(ref["dldc"]).max())
+    # gradients
+    ab = ref["grads"]["abs"]
+    check_grads(g["gm"], ref["grads"]["means"], "means", ab["means"])
+    check_grads(g["gl"], ref["grads"]["chol"], "chol", ab["chol"])
+    check_grads(g["gc"], ref["grads"]["color"], "color", ab["color"])
+    # The conic gradient is an intermediate, not a parameter: dL/dB sums
+    # e dx dy over pixels with strong cancellation in FP32; checked at 3e-4.
+    check_grads(g["gq"], ref["grads"]["conic"], "conic", rel=3e-4)
+
+
+def test_backward_arbitrary_upstream(gi):
+    """Backward with a seeded random dL/dC (not from an L2 loss)."""
+    W, H, T, n = 120, 88, 16, 700
+    means, chol, color = synth.init_gaussians(n, W, H, 11)
+    G = synth.upstream_grad(W, H, 11)
+    rect, cnt = oracle.rect_rule(means, chol, color, W, H, T)
+    ref = oracle.backward(means, chol, color, rect, cnt, W, H, T, G.astype(np.float64))
+    m, l, c = dev(means), dev(chol), dev(color)
+    rec, rect_g, cnt_g = gi.project(m, l, c, W, H, T)
+    bins = gi.bin_tiles(rect_g, cnt_g, rec, W, H, T)
+    gm, gl, gc, _ = gi.render_backward(bins, rect_g, cnt_g, l, dev(G), W, H, T)
+    check_grads(gm, ref["means"], "means", ref["abs"]["means"])
+    check_grads(gl, ref["chol"], "chol", ref["abs"]["chol"])
+    check_grads(gc, ref["color"], "color", ref["abs"]["color"])
+
+
+def test_edge_cases(gi):
+    """Culled, off-screen, degenerate and image-covering Gaussians; empty tiles."""
+    W, H, T = 77, 45, 16
+    means = np.array([[10, 10], [np.nan, 3], [-100, 10], [38, 22], [76.9, 44.9], [0, 0], [40, 20]], np.float32)
+    chol = np.array([[2, 0, 2], [2, 0, 2], [2, 0, 2], [40, 5, 30], [1, -1, 0.5], [0, 1, 1], [1e-20, 0, 1e-20]],
+                    np.float32)
+    color = np.full((7, 3), 0.1, np.float32)
+    target = synth.image(W, H, 12, n_blobs=3)
+    g = run_gpu(gi, means, chol, color, target, T)
+    ref = oracle.forward_backward(means, chol, color, target, T)
+    np.testing.assert_array_equal(g["rect"].cpu().numpy(), ref["rect"])
+    np.testing.assert_array_equal(g["cnt"].cpu().numpy(), ref["cnt"])
+    np.testing.assert_array_equal(g["bins"].ids[:g["bins"].K].cpu().numpy().astype(np.uint32), ref["ids"])
+    np.testing.assert_array_equal(g["bins"].ranges.cpu().numpy(), ref["ranges"])
+    check_pixels(g["out"], ref["out"])
+    for name, key in (("gm", "means"), ("gl", "chol"), ("gc", "color")):
+        gg = g[name].cpu().numpy()
+        assert np.all(np.isfinite(gg))
+        assert np.all(gg[ref["cnt"] == 0] == 0)
+
+
+def test_empty_set(gi):
+    W, H, T = 40, 30, 8
+    z2 = torch.zeros((0, 2), device="cuda")
+    z3 = torch.zeros((0, 3), device="cuda")
+    rec, rect, cnt = gi.project(z2, z3, z3, W, H, T)
+    bins = gi.bin_tiles(rect, cnt, rec, W, H, T)
+    assert bins.K == 0
+    assert int(bins.ranges.abs().sum()) == 0
+    out, _, _ = gi.render(bins, W, H, T)
+    assert float(out.abs().sum()) == 0.0
+
+
+def test_deterministic(gi):
+    W, H, T, n = 200, 150, 16, 3000
+    target = synth.image(W, H, 13, n_blobs=20)
+    means, chol, color = synth.init_gaussians(n, W, H, 13)
+    a = run_gpu(gi, means, chol, color, target, T)
+    b = run_gpu(gi, means, chol, color, target, T)
+    for k in ("out", "dl", "gm", "gl", "gc"):
+        assert torch.equal(a[k], b[k]), k
+
+
+def test_capacity_overflow_reported(gi):
+    W, H, T, n = 128, 128, 16, 500
+    means, chol, color = synth.init_gaussians(n, W, H, 14)
+    m, l, c = dev(means), dev(chol), dev(color)
+    rec, rect, cnt = gi.project(m, l, c, W, H, T)
+    K = int(cnt.sum().item())
+    gi.device_errors(clear=True)
+    with pytest.raises(gi.GIError):
+        gi.bin_tiles(rect, cnt, rec, W, H, T, capacity=K // 2)
+    assert gi.device_errors(clear=True) & 1  # GI_DEVERR_CAPACITY
+    bins = gi.bin_tiles(rect, cnt, rec, W, H, T, capacity=K)
+    assert bins.K == K
+    assert gi.device_errors(clear=True) == 0
+
+
+def test_autograd_function(gi):
+    W, H, T, n = 96, 64, 16, 400
+    target = dev(synth.image(W, H, 15, n_blobs=10))
+    means, chol, color = synth.init_gaussians(n, W, H, 15)
+    m = dev(means).requires_grad_()
+    l = dev(chol).requires_grad_()
+    c = dev(color).requires_grad_()
+    out = gi.rasterize(m, l, c, W, H, T)
+    loss = ((out - target) ** 2).mean()
+    loss.backward()
+    ref = oracle.forward_backward(means, chol, color, target.cpu().numpy(), T)
+    ab = ref["grads"]["abs"]
+    check_grads(m.grad, ref["grads"]["means"], "means", ab["means"])
+    check_grads(l.grad, ref["grads"]["chol"], "chol", ab["chol"])
+    check_grads(c.grad, ref["grads"]["color"], "color", ab["color"])
+
+
+def test_vq_decode_bit_exact(gi):
+    n = 50000
+    cb = synth.codebooks(4000)
+    means = synth.init_gaussians(n, 768, 512, 4000)[0]
+    x = synth.init_gaussians(n, 768, 512, 4001)
+    idx = np.stack([oracle.rvq_encode(x[1], cb[0]), oracle.rvq_encode(x[2], cb[1])])
+    m16 = means.astype(np.float16)
+    rm, rl, rc = oracle.vq_decode(m16, idx, cb)
+    gm, gl, gc = gi.vq_decode(dev(m16.view(np.int16)), dev(idx), dev(cb))
+    for a, r in ((gm, rm), (gl, rl), (gc, rc)):
+        np.testing.assert_array_equal(a.cpu().numpy().view(np.uint32), r.view(np.uint32))
+    # three stages: FP64 accumulation, rounded once
+    cb3 = np.concatenate([cb, synth.codebooks(4002)[:, 1:2]], axis=1)
+    idx3 = synth.vq_indices(n, 4003, stages=3)
+    rm, rl, rc = oracle.vq_decode(m16, idx3, cb3)
+    gm, gl, gc = gi.vq_decode(dev(m16.view(np.int16)), dev(idx3), dev(cb3))
+    for a, r in ((gl, rl), (gc, rc)):
+        np.testing.assert_array_equal(a.cpu().numpy().view(np.uint32), r.view(np.uint32))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name,T", [("c1_768x512_70k", 16), ("c1_768x512_70k", 8), ("c2_2040x1356_200k", 16)])
+def test_full_size_parity(gi, name, T):
+    """Full-size workloads in the configuration the benchmark times: binning
+    bit-exact, every pixel and every gradient against the oracle."""
+    w = synth.workload(name)
+    g = run_gpu(gi, w.means, w.chol, w.color, w.target, T)
+    ref = oracle.forward_backward(w.means, w.chol, w.color, w.target, T)
+    np.testing.assert_array_equal(g["rect"].cpu().numpy(), ref["rect"])
+    K = ref["ids"].shape[0]
+    assert g["bins"].K == K
+    np.testing.assert_array_equal(g["bins"].ids[:K].cpu().numpy().astype(np.uint32), ref["ids"])
+    np.testing.assert_array_equal(g["bins"].ranges.cpu().numpy(), ref["ranges"])
+    check_pixels(g["out"], ref["out"])
+    ab = ref["grads"]["abs"]
+    check_grads(g["gm"], ref["grads"]["means"], "means", ab["means"])
+    check_grads(g["gl"], ref["grads"]["chol"], "chol", ab["chol"])
+    check_grads(g["gc"], ref["grads"]["color"], "color", ab["color"])

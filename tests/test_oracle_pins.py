@@ -357,3 +357,23 @@ def test_rvq_encode_greedy_argmin():
             k = int(idx[m, i])
             assert d2[k] == d2.min() and k == int(np.flatnonzero(d2 == d2.min())[0])
         res = res - c[idx[m].astype(int)]
+
+
+def test_gradient_abs_sums():
+    """The condition magnitudes bound the gradients (triangle inequality); for
+    an axis-aligned Gaussian (l2 = 0, so B = 0) and a single contributing
+    pixel nothing cancels and they equal |gradient|."""
+    W, H, T, n = 40, 32, 8, 30
+    means, chol, color = synth.init_gaussians(n, W, H, 51)
+    rect, cnt = oracle.rect_rule(means, chol, color, W, H, T)
+    G = np.random.default_rng(9).standard_normal((H, W, 3))
+    gr = oracle.backward(means, chol, color, rect, cnt, W, H, T, G)
+    for k in ("means", "chol", "color"):
+        assert np.all(gr["abs"][k] >= np.abs(gr[k]) * (1 - 1e-12))
+    chol1 = chol.copy()
+    chol1[:, 1] = 0.0
+    G1 = np.zeros((H, W, 3))
+    G1[17, 21, :] = [0.3, -0.2, 0.7]
+    gr1 = oracle.backward(means, chol1, color, rect, cnt, W, H, T, G1)
+    for k in ("means", "chol", "color"):
+        np.testing.assert_allclose(gr1["abs"][k], np.abs(gr1[k]), rtol=1e-12, atol=1e-300)
