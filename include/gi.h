@@ -127,6 +127,34 @@ GI_API gi_status gi_bin_tiles(const int32_t* rect, const int32_t* cnt, const flo
                        gi_stream stream);
 
 /* ------------------------------------------------------------------------
+ * gi_bin_tiles_noalloc -- gi_bin_tiles for callers that cannot allocate
+ * device memory. It has no counterpart in the paper: it exists because some
+ * callers cannot provide gi_bin_tiles' scratch workspace -- code hosted in
+ * another framework's memory pool that may not call cudaMalloc itself,
+ * latency-critical loops that must avoid the device synchronisation an
+ * allocation can cause, or fixed-budget deployments that reserve all memory
+ * up front. Arguments and outputs are those of gi_bin_tiles without ws and
+ * ws_bytes; results are identical (bit for bit).
+ * Scratch: a fixed array of 6 MiB of this library's device memory, held by
+ * every GPU that loads the library until the process exits. Sizes beyond
+ * n <= GI_NOALLOC_MAX_GAUSSIANS or capacity <= GI_NOALLOC_MAX_PAIRS are
+ * rejected with GI_ERR_INVALID_ARG before anything is launched. The call
+ * allocates nothing (no cudaMalloc/cudaFree, no allocating library call).
+ * Every call on a device shares the array, which keeps the previous call's
+ * contents; the call clears what must start at zero itself. Calls whose
+ * work overlaps on the GPU (e.g. on two unordered streams) race on the
+ * array and must not be issued. The first call on each device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current:
+ * make this first call before any stream capture.
+ * ---------------------------------------------------------------------- */
+#define GI_NOALLOC_MAX_GAUSSIANS 262144
+#define GI_NOALLOC_MAX_PAIRS 524288
+GI_API gi_status gi_bin_tiles_noalloc(const int32_t* rect, const int32_t* cnt, const float* rec, int32_t n,
+                                      gi_image img, int64_t capacity, uint32_t* keys, uint32_t* ids,
+                                      int32_t* ranges, float* rec_binned, int64_t* pair_off, int64_t* k_dev,
+                                      gi_stream stream);
+
+/* ------------------------------------------------------------------------
  * gi_render -- accumulated-summation render (Sec. 3.2, Eq. 7) with an
  * optional fused L2 reconstruction loss (Sec. 3.4, read as the mean over the
  * 3*H*W values).

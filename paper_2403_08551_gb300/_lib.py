@@ -34,6 +34,7 @@ SIGNATURES = {
     "gi_project": (i32, [P, P, P, i32, None, P, P, P, P]),
     "gi_bin_workspace_size": (i32, [i32, None, i64, P]),
     "gi_bin_tiles": (i32, [P, P, P, i32, None, i64, P, size_t, P, P, P, P, P, P, P]),
+    "gi_bin_tiles_noalloc": (i32, [P, P, P, i32, None, i64, P, P, P, P, P, P, P]),
     "gi_render": (i32, [P, P, None, P, P, P, P, P]),
     "gi_backward_workspace_size": (i32, [i32, None, i64, P]),
     "gi_render_backward": (i32, [P, P, P, P, P, P, P, P, P, i32, None, i64, P, P, size_t, P, P, P, P, P]),
