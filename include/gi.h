@@ -75,8 +75,8 @@ typedef struct {
 } gi_image;
 
 /* Floats per projected record: (mx, my, A', B', C', c'r, c'g, c'b) where
- * Sigma^-1 = [[A, B], [B, C]] and A' = A log2(e)/2, B' = B log2(e),
- * C' = C log2(e)/2, so exp(-sigma) = exp2(-(A'dx^2 + B'dx dy + C'dy^2)). */
+ * Sigma^-1 = [[A, B], [B, C]] and A' = -A log2(e)/2, B' = -B log2(e),
+ * C' = -C log2(e)/2, so exp(-sigma) = exp2(A'dx^2 + B'dx dy + C'dy^2). */
 #define GI_REC_FLOATS 8
 
 GI_API int32_t gi_abi_version(void);

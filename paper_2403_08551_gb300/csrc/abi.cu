@@ -189,7 +189,7 @@ gi_status gi_backward_workspace_size(int32_t n, gi_image img, int64_t capacity, 
     GI_REQUIRE(n >= 0 && capacity >= 1 && capacity <= kMaxCapacity, "gi_backward_workspace_size: bad n or capacity");
     const Batch B = single(img, n);
     const size_t part = ((size_t)capacity * 32 + 255) / 256 * 256;
-    const size_t dl = (size_t)B.total_tiles * img.tile * img.tile * 16;
+    const size_t dl = (size_t)B.total_tiles * img.tile * img.tile * 12;
     *bytes = part + dl;
     return GI_OK;
 }
@@ -217,8 +217,7 @@ gi_status gi_render_backward(const float* rec_binned, const uint32_t* keys, cons
     const Batch B = single(img, n);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     float4* partial = static_cast<float4*>(ws);
-    float4* dl_tiled =
-        reinterpret_cast<float4*>(static_cast<char*>(ws) + ((size_t)capacity * 32 + 255) / 256 * 256);
+    float* dl_tiled = reinterpret_cast<float*>(static_cast<char*>(ws) + ((size_t)capacity * 32 + 255) / 256 * 256);
     cudaError_t e = launch_pack_dl(dl_dout, B, dl_tiled, s);
     if (e == cudaSuccess)
         e = launch_backward(reinterpret_cast<const float4*>(rec_binned), keys, ids, reinterpret_cast<const int4*>(rect),

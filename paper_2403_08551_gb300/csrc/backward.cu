@@ -1,8 +1,9 @@
 // backward.cu -- gradients of the accumulated-summation render (App. A).
 //
-// Pass 1 (k_backward): one lane per (tile, Gaussian) pair. The lane walks
-// every pixel of its tile, recomputing w = exp(-sigma) (no per-pixel state is
-// kept from the forward pass) and accumulates eight sums for its pair:
+// Pass 1 (k_backward): a lane owns one (tile, Gaussian) pair at a time. It
+// walks every pixel of the tile, recomputing
+// w = exp(-sigma) (no per-pixel state is kept from the forward pass) and
+// accumulates eight sums per pair:
 //   gc      = sum_i G_i w_i                        -> dL/dc'       (App. A.1)
 //   e~_i    = <G_i, c'> w_i  (dL/dsigma_i = -e~_i; App. A.1 writes
 //             dC/dsigma = -exp(-sigma) without the factor c', restored here)
@@ -35,102 +36,161 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
     s = t;
 }
 
+// Walks the T x T pixels of one tile for one pair. dL/dC is planar per tile
+// (R, G, B planes of T*T floats), so one float4 load gives four neighbouring
+// pixels of a channel and the arithmetic runs on packed FP32 pairs
+// (fma/add/mul.rn.f32x2): each instruction advances two pixels.
 template <int T>
-__global__ void __launch_bounds__(256) k_backward(const float4* __restrict__ rec_binned,
+__device__ __forceinline__ void pair_sums(const float* __restrict__ G, float4 r0, float4 r1, float dx0, float dyb,
+                                          float (&out)[8]) {
+    constexpr int NPIX = T * T;
+    const float2 A2 = make_float2(r0.z, r0.z);
+    const float2 cr = make_float2(r1.y, r1.y), cg = make_float2(r1.z, r1.z), cb = make_float2(r1.w, r1.w);
+    float2 gcr = make_float2(0.f, 0.f), gcg = gcr, gcb = gcr;
+    // Moment sums with Kahan compensation across rows: the per-pair sums
+    // cancel strongly for Gaussians near equilibrium, and the row partials
+    // are the large terms of that cancellation.
+    float S[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, cS[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 1
+    for (int y = 0; y < T; ++y) {
+        const float dy = dyb + (float)y;
+        const float bdy = r0.w * dy, cdy2 = r1.x * dy * dy;
+        const float2 B2 = make_float2(bdy, bdy), C2 = make_float2(cdy2, cdy2);
+        float2 u = make_float2(0.f, 0.f), v = u, q = u;
+        const float4* Rr = reinterpret_cast<const float4*>(G + y * T);
+        const float4* Rg = reinterpret_cast<const float4*>(G + NPIX + y * T);
+        const float4* Rb = reinterpret_cast<const float4*>(G + 2 * NPIX + y * T);
+#pragma unroll
+        for (int x4 = 0; x4 < T / 4; ++x4) {
+            const float4 R = __ldg(Rr + x4), Gg = __ldg(Rg + x4), Bb = __ldg(Rb + x4);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const float2 gr = h ? make_float2(R.z, R.w) : make_float2(R.x, R.y);
+                const float2 gg = h ? make_float2(Gg.z, Gg.w) : make_float2(Gg.x, Gg.y);
+                const float2 gb = h ? make_float2(Bb.z, Bb.w) : make_float2(Bb.x, Bb.y);
+                const float xo = (float)(4 * x4 + 2 * h);
+                const float2 dx = make_float2(dx0 + xo, dx0 + (xo + 1.0f));
+                const float2 s = __ffma2_rn(__ffma2_rn(A2, dx, B2), dx, C2);
+                const float2 w = make_float2(ex2(s.x), ex2(s.y));  // exp(-sigma)
+                gcr = __ffma2_rn(gr, w, gcr);
+                gcg = __ffma2_rn(gg, w, gcg);
+                gcb = __ffma2_rn(gb, w, gcb);
+                const float2 gw = __ffma2_rn(gb, cb, __ffma2_rn(gg, cg, __fmul2_rn(gr, cr)));
+                const float2 e = __fmul2_rn(gw, w);
+                u = __fadd2_rn(u, e);
+                const float2 t1 = __fmul2_rn(e, dx);
+                v = __fadd2_rn(v, t1);
+                q = __ffma2_rn(t1, dx, q);
+            }
+        }
+        const float us = u.x + u.y, vs = v.x + v.y, qs = q.x + q.y;
+        kahan_add(S[0], cS[0], vs);
+        kahan_add(S[1], cS[1], us * dy);
+        kahan_add(S[2], cS[2], qs);
+        kahan_add(S[3], cS[3], vs * dy);
+        kahan_add(S[4], cS[4], us * dy * dy);
+    }
+    out[0] = gcr.x + gcr.y;
+    out[1] = gcg.x + gcg.y;
+    out[2] = gcb.x + gcb.y;
+#pragma unroll
+    for (int m = 0; m < 5; ++m) out[3 + m] = S[m] - cS[m];
+}
+
+__device__ __forceinline__ void tile_origin(const Batch& B, uint32_t t, int T, int& tx, int& ty) {
+    const ImgDesc d = img_desc(B, image_of_tile(B, (int)t));
+    const int lt = (int)t - d.tile_base;
+    tx = lt % d.tw;
+    ty = lt / d.tw;
+}
+
+// One warp task = 32 consecutive pairs of the sorted list, one per lane
+// (uniform work: every pair walks T x T pixels). The next task's record,
+// tile key and Gaussian id, and the current pair's rect and pair offset, are
+// loaded before the pixel loop so their latency overlaps the arithmetic.
+template <int T>
+__global__ void __launch_bounds__(256, 3) k_backward(const float4* __restrict__ rec_binned,
                                                   const uint32_t* __restrict__ keys,
                                                   const uint32_t* __restrict__ ids, const int4* __restrict__ rect,
                                                   const int64_t* __restrict__ pair_off,
-                                                  const float4* __restrict__ dl_tiled, Batch B,
+                                                  const float* __restrict__ dl_tiled, Batch B,
                                                   const int64_t* __restrict__ k_dev, int64_t capacity,
                                                   float4* __restrict__ partial) {
     constexpr int NPIX = T * T;
+    pdl_wait();
     const int K = (int)min(*k_dev, capacity);
     const int lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int task = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; task * 32 < K; task += nwarps) {
-        int k = task * 32 + lane;
-        const bool valid = k < K;
-        if (!valid) k = K - 1;
-        const float4 r0 = rec_binned[2 * (size_t)k];      // mx, my, A', B'
-        const float4 r1 = rec_binned[2 * (size_t)k + 1];  // C', c'r, c'g, c'b
-        const uint32_t t = keys[k];
-        const ImgDesc d = img_desc(B, image_of_tile(B, (int)t));
-        const int lt = (int)t - d.tile_base;
-        const int tx = lt % d.tw, ty = lt / d.tw;
-        const float4* __restrict__ G = dl_tiled + (size_t)t * NPIX;
-        const float dx0 = (float)(tx * T) + 0.5f - r0.x;
-        const float dyb = (float)(ty * T) + 0.5f - r0.y;
-        float gcr = 0.f, gcg = 0.f, gcb = 0.f;
-        // Moment sums with Kahan compensation across rows: the per-pair sums
-        // cancel strongly for Gaussians near equilibrium, and the row
-        // partials are the large terms of that cancellation.
-        float Sx = 0.f, Sy = 0.f, Sxx = 0.f, Sxy = 0.f, Syy = 0.f;
-        float cSx = 0.f, cSy = 0.f, cSxx = 0.f, cSxy = 0.f, cSyy = 0.f;
-#pragma unroll 1
-        for (int y = 0; y < T; ++y) {
-            const float dy = dyb + (float)y;
-            const float bdy = r0.w * dy;
-            const float cdy2 = r1.x * dy * dy;
-            float u = 0.f, v = 0.f, q = 0.f;
-#pragma unroll
-            for (int x = 0; x < T; ++x) {
-                const float4 g = __ldg(G + y * T + x);
-                const float dx = dx0 + (float)x;
-                const float s = fmaf(fmaf(r0.z, dx, bdy), dx, cdy2);
-                const float w = ex2(-s);
-                gcr = fmaf(g.x, w, gcr);
-                gcg = fmaf(g.y, w, gcg);
-                gcb = fmaf(g.z, w, gcb);
-                const float gw = fmaf(g.z, r1.w, fmaf(g.y, r1.z, g.x * r1.y));
-                const float e = gw * w;
-                u += e;
-                const float t1 = e * dx;
-                v += t1;
-                q = fmaf(t1, dx, q);
-            }
-            kahan_add(Sx, cSx, v);
-            kahan_add(Sy, cSy, u * dy);
-            kahan_add(Sxx, cSxx, q);
-            kahan_add(Sxy, cSxy, v * dy);
-            kahan_add(Syy, cSyy, u * dy * dy);
+    int task = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (task * 32 >= K) return;
+    int k = min(task * 32 + lane, K - 1);
+    float4 r0 = rec_binned[2 * (size_t)k], r1 = rec_binned[2 * (size_t)k + 1];
+    uint32_t t = keys[k], g = ids[k];
+    while (true) {
+        const bool valid = task * 32 + lane < K;
+        const int4 r = rect[g];
+        const int64_t po = pair_off[g];
+        const int next = task + nwarps;
+        const bool more = next * 32 < K;
+        float4 n0 = r0, n1 = r1;
+        uint32_t nt = t, ng = g;
+        if (more) {
+            const int kn = min(next * 32 + lane, K - 1);
+            n0 = rec_binned[2 * (size_t)kn];
+            n1 = rec_binned[2 * (size_t)kn + 1];
+            nt = keys[kn];
+            ng = ids[kn];
         }
-        Sx -= cSx;
-        Sy -= cSy;
-        Sxx -= cSxx;
-        Sxy -= cSxy;
-        Syy -= cSyy;
+        int tx, ty;
+        tile_origin(B, t, T, tx, ty);
+        float o[8];
+        pair_sums<T>(dl_tiled + (size_t)t * 3 * NPIX, r0, r1, (float)(tx * T) + 0.5f - r0.x,
+                     (float)(ty * T) + 0.5f - r0.y, o);
         if (valid) {
-            const uint32_t g = ids[k];
-            const int4 r = rect[g];
-            const int64_t p = pair_off[g] + (int64_t)(ty - r.y) * (r.z - r.x) + (tx - r.x);
+            const int64_t p = po + (int64_t)(ty - r.y) * (r.z - r.x) + (tx - r.x);
             if (p >= 0 && p < capacity) {
-                partial[2 * p] = make_float4(gcr, gcg, gcb, Sx);
-                partial[2 * p + 1] = make_float4(Sy, Sxx, Sxy, Syy);
+                partial[2 * p] = make_float4(o[0], o[1], o[2], o[3]);
+                partial[2 * p + 1] = make_float4(o[4], o[5], o[6], o[7]);
             }
         }
+        if (!more) break;
+        task = next;
+        r0 = n0;
+        r1 = n1;
+        t = nt;
+        g = ng;
     }
 }
 
-// HWC dL/dC -> tiled float4 layout, zero outside the image.
+// HWC dL/dC -> planar per-tile layout (R, G, B planes), zero outside the image.
 template <int T>
-__global__ void k_pack_dl(const float* __restrict__ dl, Batch B, float4* __restrict__ out) {
+__global__ void k_pack_dl(const float* __restrict__ dl, Batch B, float* __restrict__ out) {
+    constexpr int NPIX = T * T;
+    pdl_wait();
     const int t = blockIdx.x;
     const ImgDesc d = img_desc(B, image_of_tile(B, t));
     const int lt = t - d.tile_base;
     const int tx = lt % d.tw, ty = lt / d.tw;
-    for (int p = threadIdx.x; p < T * T; p += blockDim.x) {
+    for (int p = threadIdx.x; p < NPIX; p += blockDim.x) {
         const int x = tx * T + p % T, y = ty * T + p / T;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        float r = 0.f, g = 0.f, bl = 0.f;
         if (x < d.W && y < d.H) {
             const int64_t pix = d.pix_base + (int64_t)y * d.W + x;
-            v = make_float4(dl[3 * pix], dl[3 * pix + 1], dl[3 * pix + 2], 0.f);
+            r = dl[3 * pix];
+            g = dl[3 * pix + 1];
+            bl = dl[3 * pix + 2];
         }
-        out[(size_t)t * T * T + p] = v;
+        float* o = out + (size_t)t * 3 * NPIX;
+        o[p] = r;
+        o[NPIX + p] = g;
+        o[2 * NPIX + p] = bl;
     }
 }
 
+constexpr int kReduceThreads = 128;
+
 template <bool ADAM>
-__global__ void __launch_bounds__(256) k_reduce(const float4* __restrict__ partial,
+__global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restrict__ partial,
                                                 const int64_t* __restrict__ pair_off,
                                                 const int32_t* __restrict__ cnt, int64_t capacity, int n,
                                                 ParamsIn P, float* __restrict__ g_means, float* __restrict__ g_chol,
@@ -138,6 +198,7 @@ __global__ void __launch_bounds__(256) k_reduce(const float4* __restrict__ parti
                                                 AdamCfg cfg, float* __restrict__ params, float* __restrict__ m,
                                                 float* __restrict__ v, float* __restrict__ grads_aos) {
     __shared__ int s_step;
+    pdl_wait();
     if (ADAM) {
         if (threadIdx.x == 0) s_step = *cfg.step + 1;
         __syncthreads();
@@ -149,7 +210,24 @@ __global__ void __launch_bounds__(256) k_reduce(const float4* __restrict__ parti
         const int c = cnt[g];
         const int64_t p0 = pair_off[g];
         const int64_t p1 = min(p0 + (int64_t)c, capacity);
-        for (int64_t p = p0; p < p1; ++p) {  // emission order, compensated
+        // Emission order, compensated; four pairs' loads are issued together.
+        int64_t p = p0;
+        for (; p + 4 <= p1; p += 4) {
+            float4 x[4], y[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                x[i] = partial[2 * (p + i)];
+                y[i] = partial[2 * (p + i) + 1];
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                kahan_add(a[0], ca[0], x[i].x); kahan_add(a[1], ca[1], x[i].y);
+                kahan_add(a[2], ca[2], x[i].z); kahan_add(a[3], ca[3], x[i].w);
+                kahan_add(a[4], ca[4], y[i].x); kahan_add(a[5], ca[5], y[i].y);
+                kahan_add(a[6], ca[6], y[i].z); kahan_add(a[7], ca[7], y[i].w);
+            }
+        }
+        for (; p < p1; ++p) {
             const float4 x = partial[2 * p], y = partial[2 * p + 1];
             kahan_add(a[0], ca[0], x.x); kahan_add(a[1], ca[1], x.y);
             kahan_add(a[2], ca[2], x.z); kahan_add(a[3], ca[3], x.w);
@@ -243,7 +321,7 @@ int sm_count_b() {
 }  // namespace
 
 cudaError_t launch_backward(const float4* rec_binned, const uint32_t* keys, const uint32_t* ids, const int4* rect,
-                            const int64_t* pair_off, const float4* dl_tiled, const Batch& B, const int64_t* k_dev,
+                            const int64_t* pair_off, const float* dl_tiled, const Batch& B, const int64_t* k_dev,
                             int64_t capacity, float4* partial, cudaStream_t s) {
     if (capacity <= 0) return cudaSuccess;
     static int nsm = 0;
@@ -252,48 +330,43 @@ cudaError_t launch_backward(const float4* rec_binned, const uint32_t* keys, cons
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)nsm * 8));
     switch (B.tile) {
         case 8:
-            k_backward<8><<<blocks, 256, 0, s>>>(rec_binned, keys, ids, rect, pair_off, dl_tiled, B, k_dev, capacity,
-                                                 partial);
-            break;
+            return launch_pdl(k_backward<8>, dim3(blocks), dim3(256), 0, s, rec_binned, keys, ids, rect, pair_off,
+                              dl_tiled, B, k_dev, capacity, partial);
         case 16:
-            k_backward<16><<<blocks, 256, 0, s>>>(rec_binned, keys, ids, rect, pair_off, dl_tiled, B, k_dev,
-                                                  capacity, partial);
-            break;
+            return launch_pdl(k_backward<16>, dim3(blocks), dim3(256), 0, s, rec_binned, keys, ids, rect, pair_off,
+                              dl_tiled, B, k_dev, capacity, partial);
         case 32:
-            k_backward<32><<<blocks, 256, 0, s>>>(rec_binned, keys, ids, rect, pair_off, dl_tiled, B, k_dev,
-                                                  capacity, partial);
-            break;
+            return launch_pdl(k_backward<32>, dim3(blocks), dim3(256), 0, s, rec_binned, keys, ids, rect, pair_off,
+                              dl_tiled, B, k_dev, capacity, partial);
         default:
             return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
-cudaError_t launch_pack_dl(const float* dl_hwc, const Batch& B, float4* dl_tiled, cudaStream_t s) {
+cudaError_t launch_pack_dl(const float* dl_hwc, const Batch& B, float* dl_tiled, cudaStream_t s) {
     if (B.total_tiles <= 0) return cudaSuccess;
     switch (B.tile) {
-        case 8: k_pack_dl<8><<<B.total_tiles, 64, 0, s>>>(dl_hwc, B, dl_tiled); break;
-        case 16: k_pack_dl<16><<<B.total_tiles, 256, 0, s>>>(dl_hwc, B, dl_tiled); break;
-        case 32: k_pack_dl<32><<<B.total_tiles, 256, 0, s>>>(dl_hwc, B, dl_tiled); break;
+        case 8: return launch_pdl(k_pack_dl<8>, dim3(B.total_tiles), dim3(64), 0, s, dl_hwc, B, dl_tiled);
+        case 16: return launch_pdl(k_pack_dl<16>, dim3(B.total_tiles), dim3(256), 0, s, dl_hwc, B, dl_tiled);
+        case 32: return launch_pdl(k_pack_dl<32>, dim3(B.total_tiles), dim3(256), 0, s, dl_hwc, B, dl_tiled);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 cudaError_t launch_reduce(const float4* partial, const int64_t* pair_off, const int32_t* cnt, int64_t capacity,
                           int32_t n, const ParamsIn& P, float* g_means, float* g_chol, float* g_color,
                           float* g_conic, const AdamCfg* adam, float* params, float* m, float* v, float* grads_aos,
                           cudaStream_t s) {
-    const int blocks = std::max(1, (n + 255) / 256);
+    const int blocks = std::max(1, (n + kReduceThreads - 1) / kReduceThreads);
     if (adam) {
-        k_reduce<true><<<blocks, 256, 0, s>>>(partial, pair_off, cnt, capacity, n, P, nullptr, nullptr, nullptr,
-                                              nullptr, *adam, params, m, v, grads_aos);
-    } else {
-        AdamCfg none{};
-        k_reduce<false><<<blocks, 256, 0, s>>>(partial, pair_off, cnt, capacity, n, P, g_means, g_chol, g_color,
-                                               g_conic, none, nullptr, nullptr, nullptr, nullptr);
+        return launch_pdl(k_reduce<true>, dim3(blocks), dim3(kReduceThreads), 0, s, partial, pair_off, cnt, capacity, n,
+                          P, (float*)nullptr, (float*)nullptr, (float*)nullptr, (float*)nullptr, *adam, params, m, v,
+                          grads_aos);
     }
-    return cudaGetLastError();
+    AdamCfg none{};
+    return launch_pdl(k_reduce<false>, dim3(blocks), dim3(kReduceThreads), 0, s, partial, pair_off, cnt, capacity, n, P,
+                      g_means, g_chol, g_color, g_conic, none, (float*)nullptr, (float*)nullptr, (float*)nullptr,
+                      (float*)nullptr);
 }
 
 }  // namespace gi

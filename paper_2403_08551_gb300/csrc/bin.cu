@@ -22,6 +22,7 @@ constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagPre = 2u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1;
 constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr int kWin = 16;  // look-back window (predecessor words loaded at once)
 
 __device__ __forceinline__ float clampf_(float v, float lo, float hi) {
     return v < lo ? lo : (v > hi ? hi : v);
@@ -102,6 +103,7 @@ __global__ void __launch_bounds__(kProjBlock) k_project(ParamsIn P, Batch B, flo
                                                         int4* __restrict__ rect, int32_t* __restrict__ cnt,
                                                         int64_t* __restrict__ blk_sum, ZeroJob zj) {
     __shared__ int64_t s_warp[32];
+    pdl_wait();
     zero_job(zj);
     const int g = blockIdx.x * kProjBlock + threadIdx.x;
     int c = 0;
@@ -151,9 +153,9 @@ __global__ void __launch_bounds__(kProjBlock) k_project(ParamsIn P, Batch B, flo
         }
         if (ok) {
             c = (r.z - r.x) * (r.w - r.y);
-            const float h = 0.5f * kLog2e;
+            const float h = -0.5f * kLog2e;  // negated: exp(-sigma) = exp2(quadratic form)
             r0.z = ca * h;
-            r0.w = cbb * kLog2e;
+            r0.w = cbb * -kLog2e;
             r1.x = cc * h;
         }
         rec[2 * (int64_t)g] = r0;
@@ -169,6 +171,7 @@ __global__ void __launch_bounds__(kProjBlock) k_project(ParamsIn P, Batch B, flo
 __global__ void __launch_bounds__(kProjBlock) k_blocksum(const int32_t* __restrict__ cnt, int32_t n,
                                                          int64_t* __restrict__ blk_sum, ZeroJob zj) {
     __shared__ int64_t s_warp[32];
+    pdl_wait();
     zero_job(zj);
     const int g = blockIdx.x * kProjBlock + threadIdx.x;
     const int c = g < n ? cnt[g] : 0;
@@ -189,6 +192,7 @@ __global__ void __launch_bounds__(kProjBlock) k_emit(const int4* __restrict__ re
                                                      RadixPlan rp, uint32_t* __restrict__ status) {
     __shared__ int64_t s_warp[32];
     __shared__ uint32_t s_hist[4 * 256];
+    pdl_wait();
     const int n = B.total_gauss;
     for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) s_hist[i] = 0;
     int64_t pre = 0;
@@ -240,13 +244,13 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
     uint32_t* __restrict__ vals_out, const int64_t* __restrict__ k_dev, int64_t capacity, int shift, int dbits,
     const uint32_t* __restrict__ hist, uint32_t* __restrict__ lookback, uint32_t* __restrict__ ticket,
-    const float4* __restrict__ rec, float4* __restrict__ rec_binned, int32_t n_gauss,
     uint32_t* __restrict__ status) {
     constexpr int NW = kSortThreads / 32;
     __shared__ uint32_t s_wc[NW][256];
     __shared__ uint32_t s_base[256];
     __shared__ uint32_t s_warp[32];
     __shared__ uint32_t s_ticket;
+    pdl_wait();
     const int K = (int)min(*k_dev, capacity);
     if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1u);
     for (int i = threadIdx.x; i < NW * 256; i += kSortThreads) (&s_wc[0][0])[i] = 0;
@@ -291,7 +295,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     }
     __syncthreads();
 
-    const int d = threadIdx.x;  // kSortThreads == 256 >= radix
+    const int d = threadIdx.x;  // kSortThreads >= 256 >= radix
     uint32_t tot = 0;
     if (d < radix) {
 #pragma unroll
@@ -311,22 +315,35 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
             st_release_u32(mine, kFlagPre | tot);
         } else {
             st_release_u32(mine, kFlagAgg | tot);
+            // Windowed look-back: kWin predecessor words are loaded at once
+            // (independent loads), then consumed nearest first until an
+            // inclusive prefix is found or a word is not published yet.
             int j = blk - 1;
             uint32_t spins = 0;
-            while (j >= 0) {
-                const uint32_t v = ld_relaxed_u32(lookback + (size_t)j * 256 + d);
-                const uint32_t f = v & (3u << 30);
-                if (f == 0) {
+            bool found = false;
+            while (!found && j >= 0) {
+                uint32_t v[kWin];
+#pragma unroll
+                for (int i = 0; i < kWin; ++i)
+                    v[i] = (j - i >= 0) ? ld_relaxed_u32(lookback + (size_t)(j - i) * 256 + d) : kFlagPre;
+                int used = 0;
+#pragma unroll
+                for (int i = 0; i < kWin; ++i) {
+                    if (found || used != i) break;
+                    const uint32_t f = v[i] & (3u << 30);
+                    if (f == 0) break;
+                    excl += v[i] & kValMask;
+                    used = i + 1;
+                    if (f == kFlagPre) found = true;
+                }
+                j -= used;
+                if (used == 0) {
                     if (++spins > kSpinLimit) {
                         flag_error(status, kErrTimeout);
                         break;
                     }
-                    if (spins > 32) __nanosleep(100);
-                    continue;
+                    if (spins > 16) __nanosleep(64);
                 }
-                excl += v & kValMask;
-                if (f == kFlagPre) break;
-                --j;
             }
             st_release_u32(mine, kFlagPre | ((excl + tot) & kValMask));
         }
@@ -344,24 +361,30 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
             }
             keys_out[pos] = key[r];
             vals_out[pos] = val[r];
-            if (rec_binned) {
-                if (val[r] < (uint32_t)n_gauss) {
-                    rec_binned[2 * (size_t)pos] = rec[2 * (size_t)val[r]];
-                    rec_binned[2 * (size_t)pos + 1] = rec[2 * (size_t)val[r] + 1];
-                } else {
-                    flag_error(status, kErrBounds);
-                }
-            }
         }
     }
 }
 
-// ranges[t] = [first, last + 1) of key t in the sorted keys.
-__global__ void k_ranges(const uint32_t* __restrict__ keys, const int64_t* __restrict__ k_dev, int64_t capacity,
-                         int2* __restrict__ ranges, int total_tiles) {
+// ranges[t] = [first, last + 1) of key t in the sorted keys; with rec_binned,
+// also gathers the record of each sorted pair (rec_binned[k] = rec[ids[k]]),
+// one pair per thread so the random reads overlap across the whole grid.
+__global__ void k_ranges(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ ids,
+                         const int64_t* __restrict__ k_dev, int64_t capacity, int2* __restrict__ ranges,
+                         int total_tiles, const float4* __restrict__ rec, float4* __restrict__ rec_binned,
+                         int n_gauss, uint32_t* __restrict__ status) {
+    pdl_wait();
     const int K = (int)min(*k_dev, capacity);
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
         const uint32_t t = keys[k];
+        if (rec_binned) {
+            const uint32_t g = ids[k];
+            if (g < (uint32_t)n_gauss) {
+                rec_binned[2 * (size_t)k] = rec[2 * (size_t)g];
+                rec_binned[2 * (size_t)k + 1] = rec[2 * (size_t)g + 1];
+            } else {
+                flag_error(status, kErrBounds);
+            }
+        }
         if (t >= (uint32_t)total_tiles) continue;
         if (k == 0 || keys[k - 1] != t) ranges[t].x = k;
         if (k == K - 1 || keys[k + 1] != t) ranges[t].y = k + 1;
@@ -419,8 +442,7 @@ BinWs bin_ws_layout(void* base, int64_t n, int64_t capacity, int total_tiles) {
 cudaError_t launch_project(const ParamsIn& P, const Batch& B, float4* rec, int4* rect, int32_t* cnt,
                            int64_t* blk_sum, const ZeroJob& zj, cudaStream_t s) {
     const int nblk = std::max(1, (B.total_gauss + kProjBlock - 1) / kProjBlock);
-    k_project<<<nblk, kProjBlock, 0, s>>>(P, B, rec, rect, cnt, blk_sum, zj);
-    return cudaGetLastError();
+    return launch_pdl(k_project, dim3(nblk), dim3(kProjBlock), 0, s, P, B, rec, rect, cnt, blk_sum, zj);
 }
 
 cudaError_t launch_bin(const int4* rect, const int32_t* cnt, const float4* rec, const Batch& B, int64_t capacity,
@@ -441,32 +463,27 @@ cudaError_t launch_bin(const int4* rect, const int32_t* cnt, const float4* rec, 
         zj.n32[2] = 4;
         zj.p[3] = reinterpret_cast<uint32_t*>(ranges);
         zj.n32[3] = (int64_t)B.total_tiles * 2;
-        k_blocksum<<<nblk, kProjBlock, 0, s>>>(cnt, n, ws.blk_sum, zj);
-        cudaError_t e = cudaGetLastError();
+        cudaError_t e = launch_pdl(k_blocksum, dim3(nblk), dim3(kProjBlock), 0, s, cnt, n, ws.blk_sum, zj);
         if (e != cudaSuccess) return e;
     }
     uint32_t* ka = (rp.passes & 1) ? ws.keys_tmp : keys;
     uint32_t* va = (rp.passes & 1) ? ws.vals_tmp : ids;
     uint32_t* kb = (rp.passes & 1) ? keys : ws.keys_tmp;
     uint32_t* vb = (rp.passes & 1) ? ids : ws.vals_tmp;
-    k_emit<<<nblk, kProjBlock, 0, s>>>(rect, cnt, ws.blk_sum, B, capacity, ka, va, pair_off, k_dev, k_max, ws.hist,
-                                       rp, status);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_pdl(k_emit, dim3(nblk), dim3(kProjBlock), 0, s, rect, cnt, ws.blk_sum, B, capacity, ka, va,
+                               pair_off, k_dev, k_max, ws.hist, rp, status);
     if (e != cudaSuccess) return e;
     for (int ps = 0; ps < rp.passes; ++ps) {
-        const bool last = ps == rp.passes - 1;
-        k_onesweep<<<(unsigned)sblk, kSortThreads, 0, s>>>(
-            ka, va, kb, vb, k_dev, capacity, ps * rp.dbits, rp.dbits, ws.hist + ps * 256,
-            ws.lookback + (size_t)ps * sblk * 256, ws.tickets + ps, last ? rec : nullptr,
-            last ? rec_binned : nullptr, n, status);
-        e = cudaGetLastError();
+        e = launch_pdl(k_onesweep, dim3((unsigned)sblk), dim3(kSortThreads), 0, s, ka, va, kb, vb, k_dev, capacity,
+                       ps * rp.dbits, rp.dbits, ws.hist + ps * 256, ws.lookback + (size_t)ps * sblk * 256,
+                       ws.tickets + ps, status);
         if (e != cudaSuccess) return e;
         std::swap(ka, kb);
         std::swap(va, vb);
     }
-    const int rblk = std::max(1, std::min<int>(sm_count() * 4, (int)((capacity + 255) / 256)));
-    k_ranges<<<rblk, 256, 0, s>>>(keys, k_dev, capacity, ranges, B.total_tiles);
-    return cudaGetLastError();
+    const int rblk = std::max(1, std::min<int>(sm_count() * 8, (int)((capacity + 255) / 256)));
+    return launch_pdl(k_ranges, dim3(rblk), dim3(256), 0, s, keys, ids, k_dev, capacity, ranges, B.total_tiles, rec,
+                      rec_binned, n, status);
 }
 
 }  // namespace gi

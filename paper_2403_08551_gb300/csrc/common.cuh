@@ -2,9 +2,10 @@
 //
 // Data layout (all device memory, caller-owned unless noted):
 //   rec[g]        8 x f32 = (mx, my, A', B', C', c'r, c'g, c'b); the conic
-//                 is pre-scaled so that exp(-sigma) = exp2(-(A'dx^2 +
-//                 B'dx dy + C'dy^2)), A' = A log2(e)/2, B' = B log2(e),
-//                 C' = C log2(e)/2 with Sigma^-1 = [[A, B], [B, C]].
+//                 is pre-scaled and negated so that exp(-sigma) =
+//                 exp2(A'dx^2 + B'dx dy + C'dy^2), A' = -A log2(e)/2,
+//                 B' = -B log2(e), C' = -C log2(e)/2 with
+//                 Sigma^-1 = [[A, B], [B, C]].
 //   rect[g]       int4 (tx0, ty0, tx1, ty1), image-local tile coordinates.
 //   cnt[g]        int32 number of tiles in rect (0 = culled).
 //   pair_off[g]   int64 exclusive prefix of cnt: index of g's first pair in
@@ -149,6 +150,31 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 
 __device__ __forceinline__ void flag_error(uint32_t* status, uint32_t bits) {
     if (status) atomicOr(status, bits);
+}
+
+// Programmatic dependent launch: every kernel of the library starts with this
+// wait, so a kernel launched with launch_pdl may be scheduled while its
+// predecessor drains, and still sees all of the predecessor's results (and
+// no predecessor still reads what it overwrites). A no-op for plain launches.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Launch with the programmatic-stream-serialisation attribute (the launch
+// overlaps the previous kernel's tail; captured into graphs as a
+// programmatic dependency edge).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args&&... args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
 }  // namespace gi

@@ -30,7 +30,8 @@ struct gi_fit {
     ImgDesc* d_desc = nullptr;
     float *params = nullptr, *m = nullptr, *v = nullptr, *grads = nullptr;
     float *targets = nullptr, *out = nullptr;
-    float4 *rec = nullptr, *rec_binned = nullptr, *dl_tiled = nullptr, *partial = nullptr;
+    float4 *rec = nullptr, *rec_binned = nullptr, *partial = nullptr;
+    float* dl_tiled = nullptr;
     int4* rect = nullptr;
     int32_t* cnt = nullptr;
     int64_t *pair_off = nullptr, *k_dev = nullptr, *k_max = nullptr;
@@ -164,7 +165,7 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
         up256((size_t)P * 12), up256((size_t)P * 12),                                                // 5-6
         up256((size_t)N * 32),                                  // 7 rec
         up256((size_t)f->capacity * 32),                        // 8 rec_binned
-        up256((size_t)tiles * npx * 16),                        // 9 dl_tiled
+        up256((size_t)tiles * npx * 12),                        // 9 dl_tiled
         up256((size_t)f->capacity * 32),                        // 10 partial
         up256((size_t)N * 16),                                  // 11 rect
         up256((size_t)N * 4),                                   // 12 cnt
@@ -198,7 +199,7 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
     f->out = reinterpret_cast<float*>(at(6));
     f->rec = reinterpret_cast<float4*>(at(7));
     f->rec_binned = reinterpret_cast<float4*>(at(8));
-    f->dl_tiled = reinterpret_cast<float4*>(at(9));
+    f->dl_tiled = reinterpret_cast<float*>(at(9));
     f->partial = reinterpret_cast<float4*>(at(10));
     f->rect = reinterpret_cast<int4*>(at(11));
     f->cnt = reinterpret_cast<int32_t*>(at(12));

@@ -31,9 +31,9 @@ struct RadixPlan {
 };
 RadixPlan radix_plan(int total_tiles);
 
-constexpr int kProjBlock = 1024;       // Gaussians per projection / emit block
+constexpr int kProjBlock = 256;        // Gaussians per projection / emit block
 constexpr int kSortThreads = 256;      // threads per onesweep block
-constexpr int kSortItems = 16;         // keys per thread
+constexpr int kSortItems = 8;          // keys per thread
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per onesweep block
 
 // Binning workspace carve-up.
@@ -57,17 +57,17 @@ cudaError_t launch_bin(const int4* rect, const int32_t* cnt, const float4* rec, 
                        int64_t* k_dev, int64_t* k_max, uint32_t* status, cudaStream_t s);
 
 // Forward render: out (HWC), optional loss sum (double per image), dL/dC in
-// HWC (dl_hwc) and/or tiled float4 (dl_tiled).
+// HWC (dl_hwc) and/or planar per tile (dl_tiled: [tile][R,G,B][T*T] f32).
 cudaError_t launch_render(const float4* rec_binned, const int2* ranges, const Batch& B,
-                          const float* target, float* out, float* dl_hwc, float4* dl_tiled,
+                          const float* target, float* out, float* dl_hwc, float* dl_tiled,
                           double* loss_sum, uint32_t* status, cudaStream_t s);
 
 // Backward: per-pair partial sums (8 floats per pair at its emission index).
 cudaError_t launch_backward(const float4* rec_binned, const uint32_t* keys, const uint32_t* ids,
-                            const int4* rect, const int64_t* pair_off, const float4* dl_tiled,
+                            const int4* rect, const int64_t* pair_off, const float* dl_tiled,
                             const Batch& B, const int64_t* k_dev, int64_t capacity, float4* partial,
                             cudaStream_t s);
-cudaError_t launch_pack_dl(const float* dl_hwc, const Batch& B, float4* dl_tiled, cudaStream_t s);
+cudaError_t launch_pack_dl(const float* dl_hwc, const Batch& B, float* dl_tiled, cudaStream_t s);
 
 struct AdamCfg {
     float lr[3];  // means, chol, color

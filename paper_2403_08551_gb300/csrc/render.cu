@@ -10,8 +10,10 @@
 // staged batch and accumulate all of the tile's pixels in FP32 registers (a
 // lane owns a strip of PX pixels of one row, so per-row terms are hoisted);
 // the SPLIT partial images are then summed in shared memory in a fixed order.
+// Neighbouring pixels of a strip are evaluated as packed FP32 pairs
+// (fma.rn.f32x2), halving the issue slots of the FP32 work.
 // The result is deterministic run to run. exp(-sigma) is evaluated as
-// exp2 on the SFU (MUFU.EX2) with the log2(e) factor folded into the conic.
+// exp2 on the SFU (MUFU.EX2) with -log2(e) folded into the conic.
 #include <algorithm>
 
 #include "kernels.cuh"
@@ -39,7 +41,7 @@ template <class Cfg>
 __global__ void __launch_bounds__(Cfg::kThreads) k_render(const float4* __restrict__ rec_binned,
                                                           const int2* __restrict__ ranges, Batch B,
                                                           const float* __restrict__ target, float* __restrict__ out,
-                                                          float* __restrict__ dl_hwc, float4* __restrict__ dl_tiled,
+                                                          float* __restrict__ dl_hwc, float* __restrict__ dl_tiled,
                                                           double* __restrict__ loss_sum, uint32_t* status) {
     constexpr int T = Cfg::T, PX = Cfg::PX, SPLIT = Cfg::SPLIT, NT = Cfg::kThreads, NPIX = Cfg::kPix;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -47,6 +49,7 @@ __global__ void __launch_bounds__(Cfg::kThreads) k_render(const float4* __restri
     float* spart = reinterpret_cast<float*>(smem);  // reused after the last batch
     __shared__ __align__(8) uint64_t bar;
     __shared__ float s_red[32];
+    pdl_wait();
 
     const int t = blockIdx.x;
     const int bimg = image_of_tile(B, t);
@@ -65,9 +68,11 @@ __global__ void __launch_bounds__(Cfg::kThreads) k_render(const float4* __restri
     const float py = (float)(y0 + row) + 0.5f;
     const float px0 = (float)(x0 + col0) + 0.5f;
 
-    float acc[PX][3];
+    // Packed FP32 pairs: acc[p] holds two neighbouring pixels of the strip.
+    constexpr int NP2 = PX / 2;
+    float2 accr[NP2], accg[NP2], accb[NP2];
 #pragma unroll
-    for (int i = 0; i < PX; ++i) acc[i][0] = acc[i][1] = acc[i][2] = 0.f;
+    for (int p = 0; p < NP2; ++p) accr[p] = accg[p] = accb[p] = make_float2(0.f, 0.f);
 
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
@@ -92,22 +97,25 @@ __global__ void __launch_bounds__(Cfg::kThreads) k_render(const float4* __restri
         phase ^= 1u;
         const int k0 = (nb * split) / SPLIT, k1 = (nb * (split + 1)) / SPLIT;
         if (ok) {
-#pragma unroll 2
+#pragma unroll 1
             for (int k = k0; k < k1; ++k) {
-                const float4 r0 = srec[2 * k];      // mx, my, A', B'
+                const float4 r0 = srec[2 * k];      // mx, my, A', B' (negated, log2 units)
                 const float4 r1 = srec[2 * k + 1];  // C', c'r, c'g, c'b
                 const float dy = py - r0.y;
                 const float bdy = r0.w * dy;
                 const float cdy2 = r1.x * dy * dy;
                 const float dx0 = px0 - r0.x;
+                const float2 A2 = make_float2(r0.z, r0.z), B2 = make_float2(bdy, bdy), C2 = make_float2(cdy2, cdy2);
+                const float2 cr = make_float2(r1.y, r1.y), cg = make_float2(r1.z, r1.z), cb = make_float2(r1.w, r1.w);
+                const float2 d0 = make_float2(dx0, dx0 + 1.0f);
 #pragma unroll
-                for (int i = 0; i < PX; ++i) {
-                    const float dx = dx0 + (float)i;
-                    const float s = fmaf(fmaf(r0.z, dx, bdy), dx, cdy2);
-                    const float w = ex2(-s);
-                    acc[i][0] = fmaf(r1.y, w, acc[i][0]);
-                    acc[i][1] = fmaf(r1.z, w, acc[i][1]);
-                    acc[i][2] = fmaf(r1.w, w, acc[i][2]);
+                for (int p = 0; p < NP2; ++p) {
+                    const float2 dx = __fadd2_rn(d0, make_float2(2.0f * p, 2.0f * p));
+                    const float2 s = __ffma2_rn(__ffma2_rn(A2, dx, B2), dx, C2);
+                    const float2 w = make_float2(ex2(s.x), ex2(s.y));  // exp(-sigma) of both pixels
+                    accr[p] = __ffma2_rn(cr, w, accr[p]);
+                    accg[p] = __ffma2_rn(cg, w, accg[p]);
+                    accb[p] = __ffma2_rn(cb, w, accb[p]);
                 }
             }
         }
@@ -116,10 +124,14 @@ __global__ void __launch_bounds__(Cfg::kThreads) k_render(const float4* __restri
 
     // Partial images of the SPLIT groups -> shared memory, [split][c][pixel].
 #pragma unroll
-    for (int i = 0; i < PX; ++i) {
-        const int p = row * T + col0 + i;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) spart[(split * 3 + c) * NPIX + p] = acc[i][c];
+    for (int q = 0; q < NP2; ++q) {
+        const int p = row * T + col0 + 2 * q;
+        spart[(split * 3 + 0) * NPIX + p] = accr[q].x;
+        spart[(split * 3 + 0) * NPIX + p + 1] = accr[q].y;
+        spart[(split * 3 + 1) * NPIX + p] = accg[q].x;
+        spart[(split * 3 + 1) * NPIX + p + 1] = accg[q].y;
+        spart[(split * 3 + 2) * NPIX + p] = accb[q].x;
+        spart[(split * 3 + 2) * NPIX + p + 1] = accb[q].y;
     }
     __syncthreads();
 
@@ -153,7 +165,12 @@ __global__ void __launch_bounds__(Cfg::kThreads) k_render(const float4* __restri
                 }
             }
         }
-        if (dl_tiled) dl_tiled[(int64_t)t * NPIX + p] = make_float4(dl[0], dl[1], dl[2], 0.f);
+        if (dl_tiled) {  // planar per tile: R, G, B planes of T*T floats
+            float* dt = dl_tiled + (int64_t)t * 3 * NPIX;
+            dt[p] = dl[0];
+            dt[NPIX + p] = dl[1];
+            dt[2 * NPIX + p] = dl[2];
+        }
     }
     if (target && loss_sum) {
 #pragma unroll
@@ -170,19 +187,18 @@ __global__ void __launch_bounds__(Cfg::kThreads) k_render(const float4* __restri
 
 template <class Cfg>
 cudaError_t launch_cfg(const float4* rec_binned, const int2* ranges, const Batch& B, const float* target,
-                       float* out, float* dl_hwc, float4* dl_tiled, double* loss_sum, uint32_t* status,
+                       float* out, float* dl_hwc, float* dl_tiled, double* loss_sum, uint32_t* status,
                        cudaStream_t s) {
     static_assert(Cfg::kSmem <= 48 * 1024, "dynamic shared memory above the default limit");
     if (B.total_tiles <= 0) return cudaSuccess;
-    k_render<Cfg><<<B.total_tiles, Cfg::kThreads, Cfg::kSmem, s>>>(rec_binned, ranges, B, target, out, dl_hwc,
-                                                                   dl_tiled, loss_sum, status);
-    return cudaGetLastError();
+    return launch_pdl(k_render<Cfg>, dim3(B.total_tiles), dim3(Cfg::kThreads), Cfg::kSmem, s, rec_binned, ranges, B,
+                      target, out, dl_hwc, dl_tiled, loss_sum, status);
 }
 
 }  // namespace
 
 cudaError_t launch_render(const float4* rec_binned, const int2* ranges, const Batch& B, const float* target,
-                          float* out, float* dl_hwc, float4* dl_tiled, double* loss_sum, uint32_t* status,
+                          float* out, float* dl_hwc, float* dl_tiled, double* loss_sum, uint32_t* status,
                           cudaStream_t s) {
     switch (B.tile) {
         case 8:

@@ -97,7 +97,7 @@ def test_forward_backward_matches_oracle(gi, W, H, n, T, seed):
     q = oracle.conic(chol)
     rec = g["rec"].cpu().numpy().astype(np.float64)
     live = ref["cnt"] > 0
-    h = 0.5 * oracle.LOG2E
+    h = -0.5 * oracle.LOG2E  # records hold the conic times -log2(e)/2 (B' times -log2(e))
     np.testing.assert_allclose(rec[live, 2], q[live, 0] * h, rtol=2e-6)
     np.testing.assert_allclose(rec[live, 4], q[live, 2] * h, rtol=2e-6)
     np.testing.assert_allclose(rec[live, 3], q[live, 1] * 2 * h, rtol=2e-6, atol=2e-6 * np.abs(q[live, 1]).max())
