@@ -173,12 +173,30 @@ def run_reference(args):
     return 0
 
 
-def batched_vs_plain(gi, torch, n_images, steps, T, stream):
-    """Images of uneven sizes fitted in one launch per stage vs one at a time."""
+def _time(torch, stream, fn, reps, flush=None):
+    """Average device ms of fn() over reps calls (CUDA events on `stream`,
+    optional L2 flush before each call, outside the timed window)."""
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        if flush is not None:
+            flush.zero_()
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in ev) / reps
+
+
+def batched_vs_plain(gi, torch, n_images, steps, stream):
+    """Images of uneven sizes fitted in one launch per stage (tile edge and
+    render split chosen by the autotuner) vs the same images one at a time
+    with the same configuration (identical arithmetic, so equal PSNR)."""
     ws = synth.batch_workload(n_images)
     tg = [torch.from_numpy(w.target).cuda() for w in ws]
     pr = [torch.from_numpy(pack(w)).cuda() for w in ws]
-    fit = gi.Fit(tg, pr, tile=T, lr=LR)
+    tune = gi.autotune(tg, pr, steps=5, warmup=2, lr=LR)
+    T, sp = tune["tile"], tune["render_split"]
+    fit = gi.Fit(tg, pr, tile=T, lr=LR, render_split=sp)
     fit.step(2)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -189,7 +207,7 @@ def batched_vs_plain(gi, torch, n_images, steps, T, stream):
     t_b = e0.elapsed_time(e1) / 1e3
     mse_b = fit.mse()
     fit.close()
-    plain = [gi.Fit([t], [p], tile=T, lr=LR) for t, p in zip(tg, pr)]
+    plain = [gi.Fit([t], [p], tile=T, lr=LR, render_split=sp) for t, p in zip(tg, pr)]
     for f in plain:
         f.step(2)
     torch.cuda.synchronize()
@@ -205,9 +223,62 @@ def batched_vs_plain(gi, torch, n_images, steps, T, stream):
     psnr = lambda e: 10 * math.log10(1.0 / e) if e > 0 else float("inf")  # noqa: E731
     dpsnr = max(abs(psnr(a) - psnr(b)) for a, b in zip(mse_b, mse_p))
     return {"images": n_images, "steps": steps, "sizes": "uniform over 256x256, 512x384, 768x512, 1024x768",
-            "gaussians": int(sum(w.n for w in ws)),
+            "gaussians": int(sum(w.n for w in ws)), "tile": T, "render_split": sp,
+            "autotune_ms_per_step": {f"{k[0]}/{k[1]}": v for k, v in tune["ms_per_step"].items()},
             "batched_image_steps_per_s": n_images * steps / t_b, "plain_image_steps_per_s": n_images * steps / t_p,
+            "batched_images_fitted_per_s": n_images / t_b, "plain_images_fitted_per_s": n_images / t_p,
             "speedup": t_p / t_b, "max_abs_dpsnr_db": dpsnr}
+
+
+def large_image(gi, torch, stream, flush, T=16, reps=20):
+    """2040x1356 synthetic image, 30% of the means in 10% of the area:
+    forward-only render FPS and fit-step (forward + backward) throughput."""
+    out = {}
+    for name in ("c2_2040x1356_100k", "c2_2040x1356_200k"):
+        w = synth.workload(name)
+        fit = gi.Fit([torch.from_numpy(w.target).cuda()], [torch.from_numpy(pack(w)).cuda()], tile=T, lr=LR)
+        fit.step(3)
+        render_ms = _time(torch, stream, fit.render, reps, flush)
+        step_ms = _time(torch, stream, lambda: fit.step(1), reps, flush)
+        p = fit.params
+        _, rect, cnt = gi.project(p[:, 0:2].contiguous(), p[:, 2:5].contiguous(), p[:, 5:8].contiguous(), w.W, w.H, T)
+        bins = gi.bin_tiles(rect, cnt, None, w.W, w.H, T)
+        ev_in, ev_all = evals_per_render(bins.ranges.cpu().numpy(), w.W, w.H, T)
+        out[name] = {"render_fps": 1e3 / render_ms, "render_ms": render_ms, "fit_step_ms": step_ms,
+                     "fit_iter_s": 1e3 / step_ms, "pairs": bins.K, "evals_per_render": ev_in,
+                     "fwd_bwd_evals_per_s": ev_all / (step_ms * 1e-3)}
+        fit.close()
+    return out
+
+
+def codec_decode(gi, torch, stream, flush, T=16, reps=50):
+    """RVQ decode (FP16 means, 2-stage 256-entry codebooks) then render, at
+    768x512 with 50,000 Gaussians; and decode alone over a batch of 64 such
+    Gaussian sets (3.2M Gaussians) in one call."""
+    w = synth.workload("c4_768x512_50k")
+    n = w.n
+    cb = torch.from_numpy(synth.codebooks(4000)).cuda()
+    idx = torch.from_numpy(synth.vq_indices(n, 4000)).cuda()
+    m16 = torch.from_numpy(w.means.astype(np.float16)).cuda()
+    means, chol, color = gi.vq_decode(m16, idx, cb)
+    _, rect, cnt = gi.project(means, chol, color, w.W, w.H, T)
+    K = gi.bin_tiles(rect, cnt, None, w.W, w.H, T).K
+    r = gi.Renderer(w.W, w.H, n, T, capacity=int(K * 1.5) + 4096)
+
+    def decode_render():
+        mm, ll, cc = gi.vq_decode(m16, idx, cb)
+        r(mm, ll, cc)
+
+    dr_ms = _time(torch, stream, decode_render, reps, flush)
+    nb = 64 * n
+    idx_b = torch.from_numpy(synth.vq_indices(nb, 4001)).cuda()
+    m16_b = torch.from_numpy(np.tile(w.means, (64, 1)).astype(np.float16)).cuda()
+    dec_ms = _time(torch, stream, lambda: gi.vq_decode(m16_b, idx_b, cb), reps, flush)
+    bytes_dec = nb * (4 + 4 + 32)
+    assert gi.device_errors(clear=True) == 0
+    return {"workload": "768x512, 50,000 Gaussians, FP16 means, 2x256-entry RVQ codebooks", "decode_render_fps":
+            1e3 / dr_ms, "decode_render_ms": dr_ms, "batch64_decode": {"gaussians": nb, "ms": dec_ms,
+            "gaussians_per_s": nb / (dec_ms * 1e-3), "gb_per_s": bytes_dec / (dec_ms * 1e-3) / 1e9}}
 
 
 def main():
@@ -219,6 +290,7 @@ def main():
     ap.add_argument("--tile", type=int, default=16)
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the large-image and codec measurements")
     ap.add_argument("--batch-images", type=int, default=64)
     ap.add_argument("--out", default=os.path.join(ROOT, "gpurun_out"))
     args = ap.parse_args()
@@ -345,7 +417,10 @@ def main():
     if rank == 0:
         out["clocks"] = clk.summary()
     if not args.no_batched and rank == 0:
-        out["batched"] = batched_vs_plain(gi, torch, args.batch_images, 20, T, stream)
+        out["batched"] = batched_vs_plain(gi, torch, args.batch_images, 20, stream)
+    if not args.no_extra and rank == 0:
+        out["large_image"] = large_image(gi, torch, stream, flush)
+        out["codec"] = codec_decode(gi, torch, stream, flush)
     if not args.no_cpu and rank == 0:
         out["cpu_baseline"] = cpu_baseline(w, T)
     fit.close()

@@ -5,9 +5,9 @@ The compute path is libgi.so (CUDA kernels for sm_103a behind the C ABI in
 include/gi.h); this package is its Python binding: per-stage calls, an
 autograd Function and multi-image fitting contexts.
 """
-from .api import (Bins, Fit, GIRender, alu_peaks, bin_tiles, device_errors, project, rasterize, render,
-                  render_backward, tiles, vq_decode)
+from .api import (RENDER_SPLITS, Bins, Fit, GIRender, Renderer, alu_peaks, autotune, bin_tiles, device_errors, project,
+                  rasterize, render, render_backward, tiles, vq_decode)
 from ._lib import GIError, load
 
-__all__ = ["Bins", "Fit", "GIRender", "GIError", "alu_peaks", "bin_tiles", "device_errors", "load", "project",
-           "rasterize", "render", "render_backward", "tiles", "vq_decode"]
+__all__ = ["RENDER_SPLITS", "Bins", "Fit", "GIRender", "Renderer", "GIError", "alu_peaks", "autotune", "bin_tiles",
+           "device_errors", "load", "project", "rasterize", "render", "render_backward", "tiles", "vq_decode"]

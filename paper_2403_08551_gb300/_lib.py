@@ -57,7 +57,7 @@ class GIFitDesc(ctypes.Structure):
     _fields_ = [("n_images", i32), ("widths", P), ("heights", P), ("counts", P), ("targets", P),
                 ("params", P), ("tile", i32), ("lr_means", f32), ("lr_chol", f32), ("lr_color", f32),
                 ("beta1", f32), ("beta2", f32), ("eps", f32), ("capacity", i64), ("use_graph", i32),
-                ("stage_events", i32)]
+                ("stage_events", i32), ("render_split", i32)]
 
 
 class GIError(RuntimeError):

@@ -13,7 +13,10 @@ import torch
 from . import _lib as L
 
 __all__ = ["project", "bin_tiles", "render", "render_backward", "vq_decode", "device_errors",
-           "GIRender", "rasterize", "Fit", "Bins", "alu_peaks", "tiles"]
+           "GIRender", "rasterize", "Fit", "Bins", "alu_peaks", "tiles", "autotune", "RENDER_SPLITS", "Renderer"]
+
+# Render splits (warp groups sharing one tile's list) available per tile edge.
+RENDER_SPLITS = {8: (2, 4), 16: (4, 8), 32: (1, 2)}
 
 
 def tiles(W: int, H: int, T: int):
@@ -207,7 +210,8 @@ class Fit:
 
     def __init__(self, targets: Sequence[torch.Tensor], params: Sequence[torch.Tensor], tile: int = 16,
                  lr=(1e-3, 1e-2, 1e-2), betas=(0.9, 0.999), eps=1e-8, capacity: Optional[int] = None,
-                 capacity_factor: float = 1.5, use_graph: bool = True, stage_events: bool = False):
+                 capacity_factor: float = 1.5, use_graph: bool = True, stage_events: bool = False,
+                 render_split: int = 0):
         lib = L.load()
         assert len(targets) == len(params) and len(targets) >= 1
         self.shapes = [(int(t.shape[1]), int(t.shape[0])) for t in targets]
@@ -232,7 +236,7 @@ class Fit:
         desc = L.GIFitDesc(n_img, ctypes.cast(self._w, ctypes.c_void_p), ctypes.cast(self._h, ctypes.c_void_p),
                            ctypes.cast(self._n, ctypes.c_void_p), tgt.data_ptr(), prm.data_ptr(), tile,
                            lr[0], lr[1], lr[2], betas[0], betas[1], eps, self.capacity, int(use_graph),
-                           int(stage_events))
+                           int(stage_events), int(render_split))
         h = ctypes.c_void_p()
         L.check(lib.gi_fit_create(ctypes.byref(desc), L.stream_handle(), ctypes.byref(h)), "gi_fit_create")
         self._h_fit = h
@@ -289,6 +293,69 @@ class Fit:
             self.close()
         except Exception:
             pass
+
+
+class Renderer:
+    """Forward-only pipeline with preallocated buffers for a fixed image size
+    and Gaussian count: formation, binning and render (Eq. 7), enqueued on
+    the current stream without host synchronisation. `capacity` bounds the
+    pair count; overflow is reported by device_errors()."""
+
+    def __init__(self, W: int, H: int, n: int, tile: int = 16, capacity: int = 1 << 20, device="cuda"):
+        lib = L.load()
+        self.W, self.H, self.n, self.tile, self.capacity = W, H, n, tile, int(capacity)
+        tw, th = tiles(W, H, tile)
+        f32, i32 = torch.float32, torch.int32
+        self.rec = torch.empty((n, 8), dtype=f32, device=device)
+        self.rect = torch.empty((n, 4), dtype=i32, device=device)
+        self.cnt = torch.empty((n,), dtype=i32, device=device)
+        nb = ctypes.c_size_t(0)
+        L.check(lib.gi_bin_workspace_size(n, _img(W, H, tile), self.capacity, ctypes.byref(nb)), "gi_bin_workspace_size")
+        self.ws_bytes = nb.value
+        self.ws = torch.empty((nb.value,), dtype=torch.uint8, device=device)
+        self.keys = torch.empty((self.capacity,), dtype=i32, device=device)
+        self.ids = torch.empty((self.capacity,), dtype=i32, device=device)
+        self.ranges = torch.empty((tw * th, 2), dtype=i32, device=device)
+        self.rec_binned = torch.empty((self.capacity, 8), dtype=f32, device=device)
+        self.pair_off = torch.empty((n + 1,), dtype=torch.int64, device=device)
+        self.k_dev = torch.empty((1,), dtype=torch.int64, device=device)
+        self.out = torch.empty((H, W, 3), dtype=f32, device=device)
+
+    def __call__(self, means, chol, color):
+        lib = L.load()
+        img = _img(self.W, self.H, self.tile)
+        s = L.stream_handle()
+        L.check(lib.gi_project(L.ptr(means), L.ptr(chol), L.ptr(color), self.n, img, L.ptr(self.rec),
+                               L.ptr(self.rect), L.ptr(self.cnt), s), "gi_project")
+        L.check(lib.gi_bin_tiles(L.ptr(self.rect), L.ptr(self.cnt), L.ptr(self.rec), self.n, img, self.capacity,
+                                 L.ptr(self.ws), self.ws_bytes, L.ptr(self.keys), L.ptr(self.ids), L.ptr(self.ranges),
+                                 L.ptr(self.rec_binned), L.ptr(self.pair_off), L.ptr(self.k_dev), s), "gi_bin_tiles")
+        L.check(lib.gi_render(L.ptr(self.rec_binned), L.ptr(self.ranges), img, None, L.ptr(self.out), None, None, s),
+                "gi_render")
+        return self.out
+
+
+def autotune(targets, params, tiles=(8, 16, 32), splits=None, steps=10, warmup=3, lr=(1e-3, 1e-2, 1e-2)):
+    """Chooses the tile edge and the render's warps-per-tile split for a fit
+    of these images by timing `steps` graph-replayed fit steps of every
+    candidate (CUDA events on the current stream) after `warmup` steps.
+    Every candidate runs on fresh copies of the parameters, which are left
+    untouched. Returns {"tile", "render_split", "ms_per_step": {(T, split): ms}}."""
+    stream = torch.cuda.current_stream()
+    times = {}
+    for T in tiles:
+        for sp in (splits or {}).get(T, RENDER_SPLITS[T]):
+            f = Fit(targets, [p.clone() for p in params], tile=T, lr=lr, render_split=sp)
+            f.step(warmup)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            f.step(steps)
+            e1.record(stream)
+            e1.synchronize()
+            times[(T, sp)] = e0.elapsed_time(e1) / steps
+            f.close()
+    best = min(times, key=times.get)
+    return {"tile": best[0], "render_split": best[1], "ms_per_step": times}
 
 
 def alu_peaks():

@@ -46,6 +46,7 @@ __device__ __forceinline__ void pair_sums(const float* __restrict__ G, float4 r0
     constexpr int NPIX = T * T;
     const float2 A2 = make_float2(r0.z, r0.z);
     const float2 cr = make_float2(r1.y, r1.y), cg = make_float2(r1.z, r1.z), cb = make_float2(r1.w, r1.w);
+    const float2 d0 = make_float2(dx0, dx0 + 1.0f);
     float2 gcr = make_float2(0.f, 0.f), gcg = gcr, gcb = gcr;
     // Moment sums with Kahan compensation across rows: the per-pair sums
     // cancel strongly for Gaussians near equilibrium, and the row partials
@@ -69,7 +70,7 @@ __device__ __forceinline__ void pair_sums(const float* __restrict__ G, float4 r0
                 const float2 gg = h ? make_float2(Gg.z, Gg.w) : make_float2(Gg.x, Gg.y);
                 const float2 gb = h ? make_float2(Bb.z, Bb.w) : make_float2(Bb.x, Bb.y);
                 const float xo = (float)(4 * x4 + 2 * h);
-                const float2 dx = make_float2(dx0 + xo, dx0 + (xo + 1.0f));
+                const float2 dx = __fadd2_rn(d0, make_float2(xo, xo));
                 const float2 s = __ffma2_rn(__ffma2_rn(A2, dx, B2), dx, C2);
                 const float2 w = make_float2(ex2(s.x), ex2(s.y));  // exp(-sigma)
                 gcr = __ffma2_rn(gr, w, gcr);
@@ -189,6 +190,11 @@ __global__ void k_pack_dl(const float* __restrict__ dl, Batch B, float* __restri
 
 constexpr int kReduceThreads = 128;
 
+// One thread per Gaussian. Every load that does not depend on another is
+// issued first (parameters, Adam state, Cholesky vector, pair offset), then
+// up to eight pair-partial rows at once, so the thread waits for about two
+// memory round trips. Per slot the partials are summed in emission order,
+// Kahan-compensated.
 template <bool ADAM>
 __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restrict__ partial,
                                                 const int64_t* __restrict__ pair_off,
@@ -197,37 +203,61 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
                                                 float* __restrict__ g_color, float* __restrict__ g_conic,
                                                 AdamCfg cfg, float* __restrict__ params, float* __restrict__ m,
                                                 float* __restrict__ v, float* __restrict__ grads_aos) {
+    constexpr int kBatch = 8;
     __shared__ int s_step;
+    __shared__ float s_bc[2];  // lr scale 1/(1 - beta1^t) and 1/sqrt(1 - beta2^t)
     pdl_wait();
     if (ADAM) {
-        if (threadIdx.x == 0) s_step = *cfg.step + 1;
+        if (threadIdx.x == 0) {
+            const int step = *cfg.step + 1;
+            s_step = step;
+            s_bc[0] = 1.f / (1.f - powf(cfg.beta1, (float)step));
+            s_bc[1] = rsqrtf(1.f - powf(cfg.beta2, (float)step));
+        }
         __syncthreads();
     }
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g < n) {
-        float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        float ca[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float pp[8], mm[8], vv[8];
+        float4* P4 = nullptr;
+        float4* M4 = nullptr;
+        float4* V4 = nullptr;
+        if (ADAM) {
+            P4 = reinterpret_cast<float4*>(params) + 2 * (size_t)g;
+            M4 = reinterpret_cast<float4*>(m) + 2 * (size_t)g;
+            V4 = reinterpret_cast<float4*>(v) + 2 * (size_t)g;
+            *reinterpret_cast<float4*>(pp) = P4[0]; *reinterpret_cast<float4*>(pp + 4) = P4[1];
+            *reinterpret_cast<float4*>(mm) = M4[0]; *reinterpret_cast<float4*>(mm + 4) = M4[1];
+            *reinterpret_cast<float4*>(vv) = V4[0]; *reinterpret_cast<float4*>(vv + 4) = V4[1];
+        }
+        const float l1 = P.chol[(int64_t)g * P.ls], l2 = P.chol[(int64_t)g * P.ls + 1],
+                    l3 = P.chol[(int64_t)g * P.ls + 2];
         const int c = cnt[g];
         const int64_t p0 = pair_off[g];
         const int64_t p1 = min(p0 + (int64_t)c, capacity);
-        // Emission order, compensated; four pairs' loads are issued together.
-        int64_t p = p0;
-        for (; p + 4 <= p1; p += 4) {
-            float4 x[4], y[4];
+        const int np = (int)max((int64_t)0, p1 - p0);
+        float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        float ca[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        {
+            float4 x[kBatch], y[kBatch];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                x[i] = partial[2 * (p + i)];
-                y[i] = partial[2 * (p + i) + 1];
+            for (int u = 0; u < kBatch; ++u) {
+                if (u < np) {
+                    x[u] = partial[2 * (p0 + u)];
+                    y[u] = partial[2 * (p0 + u) + 1];
+                }
             }
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                kahan_add(a[0], ca[0], x[i].x); kahan_add(a[1], ca[1], x[i].y);
-                kahan_add(a[2], ca[2], x[i].z); kahan_add(a[3], ca[3], x[i].w);
-                kahan_add(a[4], ca[4], y[i].x); kahan_add(a[5], ca[5], y[i].y);
-                kahan_add(a[6], ca[6], y[i].z); kahan_add(a[7], ca[7], y[i].w);
+            for (int u = 0; u < kBatch; ++u) {
+                if (u < np) {
+                    kahan_add(a[0], ca[0], x[u].x); kahan_add(a[1], ca[1], x[u].y);
+                    kahan_add(a[2], ca[2], x[u].z); kahan_add(a[3], ca[3], x[u].w);
+                    kahan_add(a[4], ca[4], y[u].x); kahan_add(a[5], ca[5], y[u].y);
+                    kahan_add(a[6], ca[6], y[u].z); kahan_add(a[7], ca[7], y[u].w);
+                }
             }
         }
-        for (; p < p1; ++p) {
+        for (int64_t p = p0 + kBatch; p < p1; ++p) {
             const float4 x = partial[2 * p], y = partial[2 * p + 1];
             kahan_add(a[0], ca[0], x.x); kahan_add(a[1], ca[1], x.y);
             kahan_add(a[2], ca[2], x.z); kahan_add(a[3], ca[3], x.w);
@@ -235,9 +265,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
             kahan_add(a[6], ca[6], y.z); kahan_add(a[7], ca[7], y.w);
         }
 #pragma unroll
-        for (int j = 0; j < 8; ++j) a[j] -= ca[j];
-        const float l1 = P.chol[(int64_t)g * P.ls], l2 = P.chol[(int64_t)g * P.ls + 1],
-                    l3 = P.chol[(int64_t)g * P.ls + 2];
+        for (int s = 0; s < 8; ++s) a[s] -= ca[s];
         float gr[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         float gq[3] = {0.f, 0.f, 0.f};
         if (c > 0) {
@@ -271,24 +299,13 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
                 go[0] = make_float4(gr[0], gr[1], gr[2], gr[3]);
                 go[1] = make_float4(gr[4], gr[5], gr[6], gr[7]);
             }
-            const int step = s_step;
-            const float bc1 = 1.f - powf(cfg.beta1, (float)step);
-            const float bc2 = 1.f - powf(cfg.beta2, (float)step);
-            const float rs2 = rsqrtf(bc2);
-            float4* P4 = reinterpret_cast<float4*>(params) + 2 * (size_t)g;
-            float4* M4 = reinterpret_cast<float4*>(m) + 2 * (size_t)g;
-            float4* V4 = reinterpret_cast<float4*>(v) + 2 * (size_t)g;
-            float pp[8], mm[8], vv[8];
-            *reinterpret_cast<float4*>(pp) = P4[0]; *reinterpret_cast<float4*>(pp + 4) = P4[1];
-            *reinterpret_cast<float4*>(mm) = M4[0]; *reinterpret_cast<float4*>(mm + 4) = M4[1];
-            *reinterpret_cast<float4*>(vv) = V4[0]; *reinterpret_cast<float4*>(vv + 4) = V4[1];
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const float lr = cfg.lr[j < 2 ? 0 : (j < 5 ? 1 : 2)];
-                mm[j] = cfg.beta1 * mm[j] + (1.f - cfg.beta1) * gr[j];
-                vv[j] = cfg.beta2 * vv[j] + (1.f - cfg.beta2) * gr[j] * gr[j];
-                const float denom = sqrtf(vv[j]) * rs2 + cfg.eps;
-                pp[j] -= (lr / bc1) * mm[j] / denom;
+            for (int s = 0; s < 8; ++s) {
+                const float lr = cfg.lr[s < 2 ? 0 : (s < 5 ? 1 : 2)];
+                mm[s] = cfg.beta1 * mm[s] + (1.f - cfg.beta1) * gr[s];
+                vv[s] = cfg.beta2 * vv[s] + (1.f - cfg.beta2) * gr[s] * gr[s];
+                const float denom = sqrtf(vv[s]) * s_bc[1] + cfg.eps;
+                pp[s] -= (lr * s_bc[0]) * mm[s] / denom;
             }
             P4[0] = *reinterpret_cast<float4*>(pp); P4[1] = *reinterpret_cast<float4*>(pp + 4);
             M4[0] = *reinterpret_cast<float4*>(mm); M4[1] = *reinterpret_cast<float4*>(mm + 4);

@@ -49,6 +49,7 @@ struct Batch {
     int32_t tile;         // tile edge T (8, 16 or 32)
     int32_t total_tiles;  // sum of tw*th
     int32_t total_gauss;  // sum of n
+    int32_t split;        // render: warp groups sharing one tile's list (0 = default for the tile edge)
 };
 
 __device__ __forceinline__ ImgDesc img_desc(const Batch& b, int i) {

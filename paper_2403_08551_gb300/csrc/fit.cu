@@ -121,6 +121,13 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
         return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: bad image list or NULL buffer");
     if (d->tile != 8 && d->tile != 16 && d->tile != 32)
         return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: tile must be 8, 16 or 32");
+    {
+        const int sp = d->render_split;
+        const bool ok = sp == 0 || (d->tile == 8 && (sp == 2 || sp == 4)) || (d->tile == 16 && (sp == 4 || sp == 8)) ||
+                        (d->tile == 32 && (sp == 1 || sp == 2));
+        if (!ok) return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: render_split %d not available for tile %d", sp,
+                                  d->tile);
+    }
     if (d->capacity < 1 || d->capacity > kMaxCapacity)
         return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: capacity outside [1, 2^30)");
     if ((reinterpret_cast<uintptr_t>(d->params) & 15) != 0)
@@ -155,6 +162,7 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
     f->B.tile = d->tile;
     f->B.total_tiles = (int32_t)tiles;
     f->B.total_gauss = (int32_t)gauss;
+    f->B.split = d->render_split;
 
     const int64_t N = std::max<int64_t>(1, gauss), P = std::max<int64_t>(1, pix);
     const int npx = d->tile * d->tile;

@@ -200,16 +200,34 @@ cudaError_t launch_cfg(const float4* rec_binned, const int2* ranges, const Batch
 cudaError_t launch_render(const float4* rec_binned, const int2* ranges, const Batch& B, const float* target,
                           float* out, float* dl_hwc, float* dl_tiled, double* loss_sum, uint32_t* status,
                           cudaStream_t s) {
+    // split: warp groups that share one tile's list (each group covers all
+    // of the tile's pixels); 0 picks the default for the tile edge.
+    const int sp = B.split;
     switch (B.tile) {
         case 8:
-            return launch_cfg<RCfg<8, 2, 4>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
-                                             status, s);
+            if (sp == 2)
+                return launch_cfg<RCfg<8, 2, 2>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
+                                                 status, s);
+            if (sp == 0 || sp == 4)
+                return launch_cfg<RCfg<8, 2, 4>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
+                                                 status, s);
+            return cudaErrorInvalidValue;
         case 16:
-            return launch_cfg<RCfg<16, 8, 8>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
-                                              status, s);
+            if (sp == 4)
+                return launch_cfg<RCfg<16, 8, 4>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
+                                                  status, s);
+            if (sp == 0 || sp == 8)
+                return launch_cfg<RCfg<16, 8, 8>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
+                                                  status, s);
+            return cudaErrorInvalidValue;
         case 32:
-            return launch_cfg<RCfg<32, 8, 2>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
-                                              status, s);
+            if (sp == 1)
+                return launch_cfg<RCfg<32, 8, 1>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
+                                                  status, s);
+            if (sp == 0 || sp == 2)
+                return launch_cfg<RCfg<32, 8, 2>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
+                                                  status, s);
+            return cudaErrorInvalidValue;
         default:
             return cudaErrorInvalidValue;
     }

@@ -114,23 +114,24 @@ def test_graph_replay_equals_eager(gi):
     b.close()
 
 
-@pytest.mark.parametrize("T", [8, 16, 32])
-def test_batched_equals_single(gi, T):
+@pytest.mark.parametrize("T,split", [(8, 2), (8, 4), (16, 4), (16, 8), (32, 1), (32, 2)])
+def test_batched_equals_single(gi, T, split):
     """Images fitted together in one launch per stage give bit-identical
-    parameters to the same images fitted alone."""
+    parameters to the same images fitted alone (every tile edge and render
+    split)."""
     shapes = [(96, 64, 700), (130, 77, 1100), (64, 64, 300)]
     targets, params = [], []
     for i, (W, H, n) in enumerate(shapes):
         targets.append(torch.from_numpy(synth.image(W, H, 30 + i, n_blobs=10)).cuda())
         params.append(torch.from_numpy(pack(*synth.init_gaussians(n, W, H, 30 + i))).cuda())
-    batched = gi.Fit(targets, params, tile=T, lr=LR)
+    batched = gi.Fit(targets, params, tile=T, lr=LR, render_split=split)
     batched.step(3)
     torch.cuda.synchronize()
     pb = batched.params.clone()
     mse_b = batched.mse()
     off = 0
     for i, (W, H, n) in enumerate(shapes):
-        single = gi.Fit([targets[i]], [params[i]], tile=T, lr=LR)
+        single = gi.Fit([targets[i]], [params[i]], tile=T, lr=LR, render_split=split)
         single.step(3)
         torch.cuda.synchronize()
         assert torch.equal(single.params, pb[off:off + n]), f"image {i}"
@@ -154,3 +155,24 @@ def test_fit_reduces_loss(gi):
     assert last < 0.5 * first
     assert gi.device_errors(clear=True) == 0
     fit.close()
+
+
+def test_autotune_picks_a_measured_configuration(gi):
+    shapes = [(96, 64, 600), (64, 64, 300)]
+    targets = [torch.from_numpy(synth.image(W, H, 40 + i, n_blobs=8)).cuda() for i, (W, H, _) in enumerate(shapes)]
+    params = [torch.from_numpy(pack(*synth.init_gaussians(n, W, H, 40 + i))).cuda()
+              for i, (W, H, n) in enumerate(shapes)]
+    before = [p.clone() for p in params]
+    res = gi.autotune(targets, params, steps=3, warmup=1)
+    assert (res["tile"], res["render_split"]) in res["ms_per_step"]
+    assert len(res["ms_per_step"]) == 6 and all(v > 0 for v in res["ms_per_step"].values())
+    assert res["ms_per_step"][(res["tile"], res["render_split"])] == min(res["ms_per_step"].values())
+    for p, b in zip(params, before):
+        assert torch.equal(p, b)
+
+
+def test_render_split_is_validated(gi):
+    t = torch.from_numpy(synth.image(32, 32, 41, n_blobs=2)).cuda()
+    p = torch.from_numpy(pack(*synth.init_gaussians(10, 32, 32, 41))).cuda()
+    with pytest.raises(gi.GIError):
+        gi.Fit([t], [p], tile=16, render_split=2)
