@@ -60,10 +60,10 @@ __device__ __forceinline__ void pair_sums(const float* __restrict__ G, float4 r0
         float2 u = make_float2(0.f, 0.f), v = u, q = u;
         const float4* Rr = reinterpret_cast<const float4*>(G + y * T);
         const float4* Rg = reinterpret_cast<const float4*>(G + NPIX + y * T);
-        const float4* Rb = reinterpret_cast<const float4*>(G + 2 * NPIX + y * T);
+        const float4* Bb_ = reinterpret_cast<const float4*>(G + 2 * NPIX + y * T);
 #pragma unroll
         for (int x4 = 0; x4 < T / 4; ++x4) {
-            const float4 R = __ldg(Rr + x4), Gg = __ldg(Rg + x4), Bb = __ldg(Rb + x4);
+            const float4 R = Rr[x4], Gg = Rg[x4], Bb = Bb_[x4];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
                 const float2 gr = h ? make_float2(R.z, R.w) : make_float2(R.x, R.y);
@@ -105,10 +105,22 @@ __device__ __forceinline__ void tile_origin(const Batch& B, uint32_t t, int T, i
     ty = lt / d.tw;
 }
 
+// Planar dL/dC floats of one tile.
+template <int T>
+__host__ __device__ constexpr int tile_floats() { return 3 * T * T; }
+// Tiles of up to 16 x 16 pixels are staged in shared memory, two per warp.
+template <int T>
+__host__ __device__ constexpr bool stage_dl() { return T <= 16; }
+template <int T>
+constexpr size_t backward_smem() { return stage_dl<T>() ? 8 * 2 * tile_floats<T>() * sizeof(float) : 0; }
+
 // One warp task = 32 consecutive pairs of the sorted list, one per lane
-// (uniform work: every pair walks T x T pixels). The next task's record,
-// tile key and Gaussian id, and the current pair's rect and pair offset, are
-// loaded before the pixel loop so their latency overlaps the arithmetic.
+// (uniform work: every pair walks T x T pixels). Tiles of up to 16 x 16:
+// the warp copies the planar dL/dC of the tiles of its first and last
+// pending lane into its shared buffer (cp.async), then every lane whose pair
+// lies on one of those two tiles walks it from shared memory; a task that
+// spans more than two tiles (only tiles with fewer than 32 pairs do) repeats
+// this for the lanes left. Larger tiles read dL/dC from global memory.
 template <int T>
 __global__ void __launch_bounds__(256, 3) k_backward(const float4* __restrict__ rec_binned,
                                                   const uint32_t* __restrict__ keys,
@@ -117,49 +129,57 @@ __global__ void __launch_bounds__(256, 3) k_backward(const float4* __restrict__ 
                                                   const float* __restrict__ dl_tiled, Batch B,
                                                   const int64_t* __restrict__ k_dev, int64_t capacity,
                                                   float4* __restrict__ partial) {
-    constexpr int NPIX = T * T;
+    constexpr int TF = tile_floats<T>();
+    extern __shared__ float4 s_dl[];
     pdl_wait();
     const int K = (int)min(*k_dev, capacity);
     const int lane = threadIdx.x & 31;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    int task = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (task * 32 >= K) return;
-    int k = min(task * 32 + lane, K - 1);
-    float4 r0 = rec_binned[2 * (size_t)k], r1 = rec_binned[2 * (size_t)k + 1];
-    uint32_t t = keys[k], g = ids[k];
-    while (true) {
-        const bool valid = task * 32 + lane < K;
+    float* wbuf = reinterpret_cast<float*>(s_dl) + (stage_dl<T>() ? (threadIdx.x >> 5) * 2 * TF : 0);
+    for (int task = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; task * 32 < K; task += nwarps) {
+        const int k = min(task * 32 + lane, K - 1);
+        const float4 r0 = rec_binned[2 * (size_t)k], r1 = rec_binned[2 * (size_t)k + 1];
+        const uint32_t t = keys[k], g = ids[k];
         const int4 r = rect[g];
         const int64_t po = pair_off[g];
-        const int next = task + nwarps;
-        const bool more = next * 32 < K;
-        float4 n0 = r0, n1 = r1;
-        uint32_t nt = t, ng = g;
-        if (more) {
-            const int kn = min(next * 32 + lane, K - 1);
-            n0 = rec_binned[2 * (size_t)kn];
-            n1 = rec_binned[2 * (size_t)kn + 1];
-            nt = keys[kn];
-            ng = ids[kn];
-        }
         int tx, ty;
         tile_origin(B, t, T, tx, ty);
+        const float dx0 = (float)(tx * T) + 0.5f - r0.x, dyb = (float)(ty * T) + 0.5f - r0.y;
         float o[8];
-        pair_sums<T>(dl_tiled + (size_t)t * 3 * NPIX, r0, r1, (float)(tx * T) + 0.5f - r0.x,
-                     (float)(ty * T) + 0.5f - r0.y, o);
-        if (valid) {
+        bool have = false;
+        if (stage_dl<T>()) {
+            uint32_t pending = __ballot_sync(0xffffffffu, task * 32 + lane < K);
+            while (pending) {
+                const uint32_t ta = __shfl_sync(0xffffffffu, t, __ffs(pending) - 1);
+                const uint32_t tb = __shfl_sync(0xffffffffu, t, 31 - __clz(pending));
+                const float4* sa = reinterpret_cast<const float4*>(dl_tiled + (size_t)ta * TF);
+                const float4* sb = reinterpret_cast<const float4*>(dl_tiled + (size_t)tb * TF);
+                float4* da = reinterpret_cast<float4*>(wbuf);
+                for (int i = lane; i < TF / 4; i += 32) {
+                    cp_async16(da + i, sa + i);
+                    if (tb != ta) cp_async16(da + TF / 4 + i, sb + i);
+                }
+                cp_async_wait_all();
+                __syncwarp();
+                const bool mine = ((pending >> lane) & 1u) && (t == ta || t == tb);
+                if (mine) {
+                    pair_sums<T>(wbuf + (t == ta ? 0 : TF), r0, r1, dx0, dyb, o);
+                    have = true;
+                }
+                pending &= ~__ballot_sync(0xffffffffu, mine);
+                __syncwarp();
+            }
+        } else if (task * 32 + lane < K) {
+            pair_sums<T>(dl_tiled + (size_t)t * TF, r0, r1, dx0, dyb, o);
+            have = true;
+        }
+        if (have) {
             const int64_t p = po + (int64_t)(ty - r.y) * (r.z - r.x) + (tx - r.x);
             if (p >= 0 && p < capacity) {
                 partial[2 * p] = make_float4(o[0], o[1], o[2], o[3]);
                 partial[2 * p + 1] = make_float4(o[4], o[5], o[6], o[7]);
             }
         }
-        if (!more) break;
-        task = next;
-        r0 = n0;
-        r1 = n1;
-        t = nt;
-        g = ng;
     }
 }
 
@@ -345,13 +365,23 @@ cudaError_t launch_backward(const float4* rec_binned, const uint32_t* keys, cons
     if (!nsm) nsm = sm_count_b();
     const int64_t need = (capacity + 255) / 256;  // 8 warps x 32 pairs per block-iteration
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)nsm * 8));
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_backward<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)backward_smem<8>());
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_backward<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)backward_smem<16>());
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
     switch (B.tile) {
         case 8:
-            return launch_pdl(k_backward<8>, dim3(blocks), dim3(256), 0, s, rec_binned, keys, ids, rect, pair_off,
-                              dl_tiled, B, k_dev, capacity, partial);
+            return launch_pdl(k_backward<8>, dim3(blocks), dim3(256), backward_smem<8>(), s, rec_binned, keys, ids,
+                              rect, pair_off, dl_tiled, B, k_dev, capacity, partial);
         case 16:
-            return launch_pdl(k_backward<16>, dim3(blocks), dim3(256), 0, s, rec_binned, keys, ids, rect, pair_off,
-                              dl_tiled, B, k_dev, capacity, partial);
+            return launch_pdl(k_backward<16>, dim3(blocks), dim3(256), backward_smem<16>(), s, rec_binned, keys, ids,
+                              rect, pair_off, dl_tiled, B, k_dev, capacity, partial);
         case 32:
             return launch_pdl(k_backward<32>, dim3(blocks), dim3(256), 0, s, rec_binned, keys, ids, rect, pair_off,
                               dl_tiled, B, k_dev, capacity, partial);

@@ -149,6 +149,16 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         : "memory");
 }
 
+// 16-byte asynchronous global -> shared copy through L2 only (cp.async.cg);
+// both addresses 16-byte aligned. cp_async_wait_all() waits for every copy
+// the thread issued.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+}
+
 __device__ __forceinline__ void flag_error(uint32_t* status, uint32_t bits) {
     if (status) atomicOr(status, bits);
 }
