@@ -18,10 +18,6 @@ namespace gi {
 
 namespace {
 
-constexpr uint32_t kFlagAgg = 1u << 30;
-constexpr uint32_t kFlagPre = 2u << 30;
-constexpr uint32_t kValMask = (1u << 30) - 1;
-constexpr uint32_t kSpinLimit = 1u << 22;
 constexpr int kWin = 16;  // look-back window (predecessor words loaded at once)
 
 __device__ __forceinline__ float clampf_(float v, float lo, float hi) {
@@ -40,60 +36,6 @@ __device__ void zero_job(const ZeroJob& zj) {
         for (int64_t i = tid; i < n4; i += nth) p4[i] = make_uint4(0, 0, 0, 0);
         for (int64_t i = (n4 << 2) + tid; i < n; i += nth) p[i] = 0u;
     }
-}
-
-template <typename Tv>
-__device__ __forceinline__ Tv warp_incl_scan(Tv v) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        Tv u = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += u;
-    }
-    return v;
-}
-
-template <typename Tv>
-__device__ __forceinline__ Tv warp_sum(Tv v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Inclusive scan over the block (blockDim.x a multiple of 32, <= 1024).
-template <typename Tv>
-__device__ Tv block_incl_scan(Tv v, Tv* s_warp /*[32]*/) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    v = warp_incl_scan(v);
-    if (lane == 31) s_warp[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        Tv w = lane < nw ? s_warp[lane] : Tv(0);
-        w = warp_incl_scan(w);
-        if (lane < nw) s_warp[lane] = w;
-    }
-    __syncthreads();
-    if (warp > 0) v += s_warp[warp - 1];
-    __syncthreads();
-    return v;
-}
-
-template <typename Tv>
-__device__ Tv block_sum(Tv v, Tv* s_warp /*[32]*/) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    v = warp_sum(v);
-    if (lane == 0) s_warp[warp] = v;
-    __syncthreads();
-    Tv r = Tv(0);
-    if (warp == 0) {
-        r = lane < nw ? s_warp[lane] : Tv(0);
-        r = warp_sum(r);
-        if (lane == 0) s_warp[0] = r;
-    }
-    __syncthreads();
-    r = s_warp[0];
-    __syncthreads();
-    return r;
 }
 
 // ---------------------------------------------------------------------------
@@ -420,6 +362,8 @@ BinWs bin_ws_layout(void* base, int64_t n, int64_t capacity, int total_tiles) {
     const RadixPlan rp = radix_plan(total_tiles);
     const int64_t nblk = std::max<int64_t>(1, (n + kProjBlock - 1) / kProjBlock);
     const int64_t sblk = std::max<int64_t>(1, (capacity + kSortTile - 1) / kSortTile);
+    const int64_t nchunks = std::max<int64_t>(1, (n + kCmChunk - 1) / kCmChunk);
+    const int64_t groups = std::max<int64_t>(1, (total_tiles + 31) / 32);
     const int64_t cap = std::max<int64_t>(1, capacity);
     char* b = static_cast<char*>(base);
     size_t off = 0;
@@ -428,13 +372,22 @@ BinWs bin_ws_layout(void* base, int64_t n, int64_t capacity, int total_tiles) {
         off = align_up(off + bytes, 256);
         return b ? static_cast<void*>(b + o) : nullptr;
     };
-    BinWs w;
+    BinWs w{};
+    w.cm_path = cm_applies(n, total_tiles);
     w.blk_sum = static_cast<int64_t*>(take(nblk * sizeof(int64_t)));
-    w.keys_tmp = static_cast<uint32_t*>(take(cap * 4));
-    w.vals_tmp = static_cast<uint32_t*>(take(cap * 4));
-    w.hist = static_cast<uint32_t*>(take((size_t)rp.passes * 256 * 4));
-    w.lookback = static_cast<uint32_t*>(take((size_t)rp.passes * sblk * 256 * 4));
+    if (w.cm_path) {
+        w.cm = static_cast<uint32_t*>(take((size_t)nchunks * total_tiles * 4));
+        w.chunk_sum = static_cast<uint32_t*>(take((size_t)nchunks * 4));
+    } else {
+        w.keys_tmp = static_cast<uint32_t*>(take(cap * 4));
+        w.vals_tmp = static_cast<uint32_t*>(take(cap * 4));
+    }
+    const size_t zero_off = off;
+    if (!w.cm_path) w.hist = static_cast<uint32_t*>(take((size_t)rp.passes * 256 * 4));
+    w.lookback = static_cast<uint32_t*>(take(w.cm_path ? (size_t)groups * 4 : (size_t)rp.passes * sblk * 256 * 4));
     w.tickets = static_cast<uint32_t*>(take(16));
+    w.zero = b ? reinterpret_cast<uint32_t*>(b + zero_off) : nullptr;
+    w.zero_words = (int64_t)((off - zero_off) / 4);
     w.bytes = off;
     return w;
 }
@@ -449,20 +402,19 @@ cudaError_t launch_bin(const int4* rect, const int32_t* cnt, const float4* rec, 
                        const BinWs& ws, bool blk_sum_ready, uint32_t* keys, uint32_t* ids, int2* ranges,
                        float4* rec_binned, int64_t* pair_off, int64_t* k_dev, int64_t* k_max, uint32_t* status,
                        cudaStream_t s) {
+    if (ws.cm_path)
+        return launch_bin_cm(rect, cnt, rec, B, capacity, ws, blk_sum_ready, keys, ids, ranges, rec_binned, pair_off,
+                             k_dev, k_max, status, s);
     const RadixPlan rp = radix_plan(B.total_tiles);
     const int n = B.total_gauss;
     const int nblk = std::max(1, (n + kProjBlock - 1) / kProjBlock);
     const int64_t sblk = std::max<int64_t>(1, (capacity + kSortTile - 1) / kSortTile);
     if (!blk_sum_ready) {
         ZeroJob zj{};
-        zj.p[0] = ws.hist;
-        zj.n32[0] = (int64_t)rp.passes * 256;
-        zj.p[1] = ws.lookback;
-        zj.n32[1] = (int64_t)rp.passes * sblk * 256;
-        zj.p[2] = ws.tickets;
-        zj.n32[2] = 4;
-        zj.p[3] = reinterpret_cast<uint32_t*>(ranges);
-        zj.n32[3] = (int64_t)B.total_tiles * 2;
+        zj.p[0] = ws.zero;
+        zj.n32[0] = ws.zero_words;
+        zj.p[1] = reinterpret_cast<uint32_t*>(ranges);
+        zj.n32[1] = (int64_t)B.total_tiles * 2;
         cudaError_t e = launch_pdl(k_blocksum, dim3(nblk), dim3(kProjBlock), 0, s, cnt, n, ws.blk_sum, zj);
         if (e != cudaSuccess) return e;
     }

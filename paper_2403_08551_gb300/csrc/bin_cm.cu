@@ -1,0 +1,383 @@
+// bin_cm.cu -- tile binning as a stable counting sort over a count matrix,
+// used when the batch has few tiles (cm_applies).
+//
+// The Gaussians are cut into chunks of kCmChunk consecutive indices. With
+// M[b][t] = number of Gaussians of chunk b whose rect covers tile t, the
+// sorted position of the pair (t, g), g in chunk b, is
+//   start[t] + sum_{b' < b} M[b'][t] + #{g' in chunk b : g' < g, t in rect(g')}
+// with start = exclusive scan of the column sums over tiles. This is the
+// order the LSD radix path produces (tiles ascending, Gaussian index
+// ascending inside a tile), obtained without a sort:
+//   k_count   one block per two chunks: shared-memory tile histograms give
+//             the rows of M and the chunk pair totals; clears the binning
+//             scratch when asked.
+//   k_colscan one block per 32 tiles: column prefix sums over the chunks
+//             (P[b][t] = start[t] + sum_{b' < b} M[b'][t], written over M),
+//             chained scan of the column totals across tile groups (bounded
+//             look-back) -> start, ranges, K and the capacity check.
+//   k_place   one block per chunk: a per-warp lane mask of every tile in
+//             shared memory gives each pair's rank inside the chunk; the
+//             block scatters keys, ids and records and writes pair_off.
+#include <algorithm>
+
+#include "kernels.cuh"
+
+namespace gi {
+
+namespace {
+
+constexpr int kCmGroupTiles = 32;              // k_colscan: tiles per block (one per lane)
+constexpr int kCmScanWarps = 32;               // k_colscan: warps splitting the chunk rows
+constexpr int kCmRowRegs = 24;                 // k_colscan: rows a lane keeps in registers between passes
+
+__device__ __forceinline__ void zero_words(uint32_t* p, int64_t n) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = tid; i < n; i += nth) p[i] = 0u;
+}
+
+// True when rect r is a valid tile rectangle of image d holding c tiles.
+__device__ __forceinline__ bool rect_ok(const int4& r, const ImgDesc& d, int c) {
+    return r.x >= 0 && r.y >= 0 && r.z <= d.tw && r.w <= d.th && r.x < r.z && r.y < r.w &&
+           (r.z - r.x) * (r.w - r.y) == c;
+}
+
+// Chunk layout shared by k_count and k_place: per Gaussian of the chunk its
+// rect, image tile base and tile-row width, and the exclusive prefix of the
+// pair counts (off[0..kCmChunk], emission order inside the chunk).
+struct ChunkSmem {
+    int off[kCmChunk + 1];
+    int4 rect[kCmChunk];
+    int2 img[kCmChunk];  // (tile_base, tw)
+};
+
+// Loads this thread's Gaussian (count, rect, image) into the chunk layout
+// and returns its count (0 for a bad rect, with *bad set). Ends with the
+// block scan's barrier.
+__device__ __forceinline__ int load_chunk(const int4* __restrict__ rect, const int32_t* __restrict__ cnt,
+                                          const Batch& B, int g, ChunkSmem& cs, int* s_warp, bool* bad) {
+    int c = g < B.total_gauss ? cnt[g] : 0;
+    int4 r = c > 0 ? rect[g] : make_int4(0, 0, 0, 0);
+    int2 im = make_int2(0, 0);
+    *bad = false;
+    if (c > 0) {
+        const ImgDesc d = img_desc(B, image_of_gauss(B, g));
+        if (rect_ok(r, d, c)) {
+            im = make_int2(d.tile_base, d.tw);
+        } else {
+            *bad = c != 0;
+            c = 0;
+        }
+    }
+    cs.rect[threadIdx.x] = r;
+    cs.img[threadIdx.x] = im;
+    const int incl = block_incl_scan<int>(c, s_warp);
+    cs.off[threadIdx.x + 1] = incl;
+    if (threadIdx.x == 0) cs.off[0] = 0;
+    __syncthreads();
+    return c;
+}
+
+// ---------------------------------------------------------------------------
+// Count: block = chunk b (kCmChunk threads, one Gaussian each). Every pair
+// adds one to the chunk's shared tile histogram, which is written as row b
+// of M (all tiles, zeros included); chunk_sum[b] = the chunk's pair count.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kCmChunk) k_count(const int4* __restrict__ rect, const int32_t* __restrict__ cnt,
+                                                    Batch B, uint32_t* __restrict__ M,
+                                                    uint32_t* __restrict__ chunk_sum, uint32_t* __restrict__ zero,
+                                                    int64_t zero_n) {
+    extern __shared__ uint32_t s_h[];  // [total_tiles]
+    __shared__ ChunkSmem cs;
+    __shared__ int s_warp[32];
+    pdl_wait();
+    if (zero) zero_words(zero, zero_n);
+    const int Tn = B.total_tiles;
+    const int b = blockIdx.x;
+    for (int i = threadIdx.x; i < Tn; i += blockDim.x) s_h[i] = 0u;
+    bool bad;
+    const int c = load_chunk(rect, cnt, B, b * kCmChunk + threadIdx.x, cs, s_warp, &bad);  // k_place raises the error
+    const int total = cs.off[kCmChunk];
+    const int4 r = cs.rect[threadIdx.x];
+    const int base = cs.img[threadIdx.x].x, tw = cs.img[threadIdx.x].y;
+    if (c > 0)
+        for (int ty = r.y; ty < r.w; ++ty)
+            for (int tx = r.x; tx < r.z; ++tx) atomicAdd(&s_h[base + ty * tw + tx], 1u);
+    __syncthreads();
+    uint32_t* row = M + (size_t)b * Tn;
+    for (int i = threadIdx.x; i < Tn; i += blockDim.x) row[i] = s_h[i];
+    if (threadIdx.x == 0) chunk_sum[b] = (uint32_t)total;
+}
+
+// ---------------------------------------------------------------------------
+// Column scan: block (in ticket order) -> tiles [32 blk, 32 blk + 32), one
+// per lane; warp w -> chunk rows [w rs, (w + 1) rs). Pass 1 sums each warp's
+// rows per tile. The warp partials give every warp's offset inside the
+// column and the column totals; warp 0 scans the totals over the block's
+// tiles and chains the block total through lower tickets (warp-wide
+// look-back over 32 predecessors per round, retried until the words up to
+// the nearest inclusive prefix are all published; bounded spin). Pass 2
+// rereads the rows and writes P[r][t] = start[t] + prefix over M in place.
+// The block holding the last tile stores K, updates k_max and raises the
+// capacity error.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kCmScanWarps * 32) k_colscan(uint32_t* __restrict__ M, int nchunks, int total_tiles,
+                                                               int2* __restrict__ ranges, int64_t capacity,
+                                                               int64_t* __restrict__ k_dev, int64_t* __restrict__ k_max,
+                                                               uint32_t* __restrict__ lookback,
+                                                               uint32_t* __restrict__ ticket,
+                                                               uint32_t* __restrict__ status) {
+    __shared__ uint32_t s_part[kCmScanWarps][32];
+    __shared__ uint32_t s_start[32];
+    __shared__ uint32_t s_ticket;
+    pdl_wait();
+    if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1u);
+    __syncthreads();
+    const int blk = (int)s_ticket;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int t = blk * kCmGroupTiles + lane;
+    const bool tv = t < total_tiles;
+    const int rs = (nchunks + kCmScanWarps - 1) / kCmScanWarps;
+    const int r0 = min(nchunks, warp * rs), r1 = min(nchunks, r0 + rs);
+    const bool in_regs = r1 - r0 <= kCmRowRegs;  // block-uniform
+    uint32_t sum = 0;
+    uint32_t v[kCmRowRegs];
+    if (tv) {
+        if (in_regs) {
+#pragma unroll
+            for (int i = 0; i < kCmRowRegs; ++i) v[i] = r0 + i < r1 ? M[(size_t)(r0 + i) * total_tiles + t] : 0u;
+#pragma unroll
+            for (int i = 0; i < kCmRowRegs; ++i) sum += v[i];
+        } else {
+            int r = r0;
+            for (; r + 8 <= r1; r += 8) {
+                uint32_t u[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) u[i] = M[(size_t)(r + i) * total_tiles + t];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) sum += u[i];
+            }
+            for (; r < r1; ++r) sum += M[(size_t)r * total_tiles + t];
+        }
+    }
+    s_part[warp][lane] = sum;
+    __syncthreads();
+    {
+        // warp j scans tile j's 32 warp partials (lane = warp index) in place
+        static_assert(kCmScanWarps == 32, "one warp per tile of the group");
+        const uint32_t x = s_part[lane][warp];
+        uint32_t in = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, in, o);
+            if (lane >= o) in += u;
+        }
+        s_part[lane][warp] = in - x;
+        if (lane == 31) s_start[warp] = in;  // column total, replaced by the start below
+    }
+    __syncthreads();
+    if (warp == 0) {
+        const uint32_t col = s_start[lane];
+        uint32_t incl = col;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+        uint32_t excl = 0;
+        if (blk == 0) {
+            if (lane == 0) st_release_u32(lookback, kFlagPre | (tot & kValMask));
+        } else {
+            if (lane == 0) st_release_u32(lookback + blk, kFlagAgg | (tot & kValMask));
+            int j = blk - 1;
+            uint32_t spins = 0;
+            while (j >= 0) {
+                const int idx = j - lane;  // lane 0 = nearest predecessor
+                const uint32_t w = idx >= 0 ? ld_relaxed_u32(lookback + idx) : kFlagPre;
+                const uint32_t f = w & (3u << 30);
+                const uint32_t pre = __ballot_sync(0xffffffffu, f == kFlagPre);
+                const int fp = pre ? __ffs(pre) - 1 : 31;
+                const uint32_t upto = fp == 31 ? 0xffffffffu : ((2u << fp) - 1u);  // lanes 0 .. fp
+                const uint32_t notready = __ballot_sync(0xffffffffu, f == 0u) & upto;
+                if (notready) {
+                    if (++spins > kSpinLimit) {
+                        if (lane == 0) flag_error(status, kErrTimeout);
+                        break;
+                    }
+                    if (spins > 16) __nanosleep(64);
+                    continue;
+                }
+                excl += warp_sum<uint32_t>(((upto >> lane) & 1u) ? (w & kValMask) : 0u);
+                if (pre) break;
+                j -= 32;
+            }
+            if (lane == 0) st_release_u32(lookback + blk, kFlagPre | ((excl + tot) & kValMask));
+        }
+        const uint32_t start = excl + incl - col;
+        s_start[lane] = start;
+        if (tv) {
+            int2 rg = make_int2(0, 0);
+            if (col) {
+                rg.x = (int)min((int64_t)start, capacity);
+                rg.y = (int)min((int64_t)start + col, capacity);
+            }
+            ranges[t] = rg;
+        }
+        if ((blk + 1) * kCmGroupTiles >= total_tiles && lane == 0) {
+            const int64_t K = (int64_t)excl + tot;
+            *k_dev = K;
+            if (k_max) atomicMax(reinterpret_cast<unsigned long long*>(k_max), (unsigned long long)K);
+            if (K > capacity) flag_error(status, kErrCapacity);
+        }
+    }
+    __syncthreads();
+    if (tv && in_regs) {
+        uint32_t run = s_start[lane] + s_part[warp][lane];
+#pragma unroll
+        for (int i = 0; i < kCmRowRegs; ++i) {
+            if (r0 + i < r1) M[(size_t)(r0 + i) * total_tiles + t] = run;
+            run += v[i];
+        }
+    } else if (tv) {
+        uint32_t run = s_start[lane] + s_part[warp][lane];
+        int r = r0;
+        for (; r + 8 <= r1; r += 8) {
+            uint32_t v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = M[(size_t)(r + i) * total_tiles + t];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                M[(size_t)(r + i) * total_tiles + t] = run;
+                run += v[i];
+            }
+        }
+        for (; r < r1; ++r) {
+            const uint32_t v = M[(size_t)r * total_tiles + t];
+            M[(size_t)r * total_tiles + t] = run;
+            run += v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Place: block = chunk b. Lane masks s_m[w][t] (bit l set when local
+// Gaussian 32 w + l covers tile t) are built with atomicOr, which is
+// order-independent; then pair (t, g), g = 128 b + 32 w + l, lands at
+//   P[b][t] + sum_{w' < w} popc(s_m[w'][t]) + popc(s_m[w][t] & bits below l),
+// i.e. ascending g inside the tile. The chunk's row of P and its records
+// are staged in shared memory. pair_off = exclusive scan of cnt in emission order, the
+// chunk base from the chunk totals.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(kCmChunk) k_place(const int4* __restrict__ rect, const int32_t* __restrict__ cnt,
+                                                    const float4* __restrict__ rec, Batch B,
+                                                    const uint32_t* __restrict__ P,
+                                                    const uint32_t* __restrict__ chunk_sum, int nchunks,
+                                                    int64_t capacity, uint32_t* __restrict__ keys,
+                                                    uint32_t* __restrict__ ids, float4* __restrict__ rec_binned,
+                                                    int64_t* __restrict__ pair_off, uint32_t* __restrict__ status) {
+    constexpr int NW = kCmChunk / 32;
+    constexpr int kRowLoads = kCmMaxTiles / kCmChunk;
+    extern __shared__ uint32_t s_dyn[];  // [NW][total_tiles] lane masks, then [total_tiles] P row
+    __shared__ ChunkSmem cs;
+    __shared__ float4 s_rec[kCmChunk][2];
+    __shared__ int s_warp[32];
+    __shared__ int64_t s_warp64[32];
+    pdl_wait();
+    const int Tn = B.total_tiles;
+    uint32_t* s_m = s_dyn;
+    uint32_t* s_p = s_dyn + NW * Tn;
+    const int b = blockIdx.x;
+    const int g = b * kCmChunk + threadIdx.x;
+    // Independent loads first: the chunk's row of P, the chunk totals below
+    // b and this Gaussian's record.
+    const uint32_t* prow = P + (size_t)b * Tn;
+#pragma unroll
+    for (int i = 0; i < kRowLoads; ++i) {
+        const int idx = threadIdx.x + i * kCmChunk;
+        if (idx < Tn) s_p[idx] = prow[idx];
+    }
+    int64_t pre = 0;
+    for (int i = threadIdx.x; i < b; i += 8 * kCmChunk) {  // eight predicated loads in flight per round
+        uint32_t u[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) u[q] = i + q * kCmChunk < b ? chunk_sum[i + q * kCmChunk] : 0u;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) pre += u[q];
+    }
+    if (rec_binned && g < B.total_gauss) {
+        s_rec[threadIdx.x][0] = rec[2 * (size_t)g];
+        s_rec[threadIdx.x][1] = rec[2 * (size_t)g + 1];
+    }
+    for (int i = threadIdx.x; i < NW * Tn; i += blockDim.x) s_m[i] = 0u;
+    bool bad;
+    const int c = load_chunk(rect, cnt, B, g, cs, s_warp, &bad);
+    if (bad) flag_error(status, kErrBounds);
+    pre = block_sum<int64_t>(pre, s_warp64);
+    const int off = cs.off[threadIdx.x];
+    if (g < B.total_gauss) pair_off[g] = pre + off;
+    if (b == nchunks - 1 && threadIdx.x == blockDim.x - 1) pair_off[B.total_gauss] = pre + off + c;
+    // Each thread walks its own Gaussian's rect (row-major): fewer
+    // instructions than spreading pairs evenly, at the cost of warps waiting
+    // for their widest Gaussian.
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int4 r = cs.rect[threadIdx.x];
+    const int base = cs.img[threadIdx.x].x, tw = cs.img[threadIdx.x].y;
+    if (c > 0)
+        for (int ty = r.y; ty < r.w; ++ty)
+            for (int tx = r.x; tx < r.z; ++tx) atomicOr(&s_m[warp * Tn + base + ty * tw + tx], 1u << lane);
+    __syncthreads();
+    if (c > 0) {
+        const float4 ra = rec_binned ? s_rec[threadIdx.x][0] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 rb = rec_binned ? s_rec[threadIdx.x][1] : ra;
+        const uint32_t lt = lanemask_lt();
+        for (int ty = r.y; ty < r.w; ++ty) {
+            for (int tx = r.x; tx < r.z; ++tx) {
+                const int t = base + ty * tw + tx;
+                uint32_t pos = s_p[t] + __popc(s_m[warp * Tn + t] & lt);
+                for (int v = 0; v < warp; ++v) pos += __popc(s_m[v * Tn + t]);
+                if ((int64_t)pos >= capacity) continue;  // dropped; the scan raised the capacity error
+                keys[pos] = (uint32_t)t;
+                ids[pos] = (uint32_t)g;
+                if (rec_binned) {
+                    rec_binned[2 * (size_t)pos] = ra;
+                    rec_binned[2 * (size_t)pos + 1] = rb;
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+bool cm_applies(int64_t n, int total_tiles) {
+    const int64_t nchunks = std::max<int64_t>(1, (n + kCmChunk - 1) / kCmChunk);
+    return total_tiles >= 1 && total_tiles <= kCmMaxTiles && nchunks * total_tiles <= kCmMaxCells;
+}
+
+cudaError_t launch_bin_cm(const int4* rect, const int32_t* cnt, const float4* rec, const Batch& B, int64_t capacity,
+                          const BinWs& ws, bool zero_ready, uint32_t* keys, uint32_t* ids, int2* ranges,
+                          float4* rec_binned, int64_t* pair_off, int64_t* k_dev, int64_t* k_max, uint32_t* status,
+                          cudaStream_t s) {
+    const int n = B.total_gauss;
+    const int Tn = B.total_tiles;
+    const int nchunks = std::max(1, (n + kCmChunk - 1) / kCmChunk);
+    const int groups = (Tn + kCmGroupTiles - 1) / kCmGroupTiles;
+    cudaError_t e = launch_pdl(k_count, dim3(nchunks), dim3(kCmChunk), (size_t)Tn * 4, s, rect, cnt, B, ws.cm,
+                               ws.chunk_sum, zero_ready ? nullptr : ws.zero, zero_ready ? (int64_t)0 : ws.zero_words);
+    if (e != cudaSuccess) return e;
+    e = launch_pdl(k_colscan, dim3(groups), dim3(kCmScanWarps * 32), 0, s, ws.cm, nchunks, Tn, ranges, capacity, k_dev,
+                   k_max, ws.lookback, ws.tickets, status);
+    if (e != cudaSuccess) return e;
+    static bool attr = false;  // up to 40 KB dynamic + the static layout: above the default 48 KB window
+    if (!attr) {
+        e = cudaFuncSetAttribute(k_place, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (kCmChunk / 32 + 1) * kCmMaxTiles * 4);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    return launch_pdl(k_place, dim3(nchunks), dim3(kCmChunk), (size_t)(kCmChunk / 32 + 1) * Tn * 4, s, rect, cnt, rec,
+                      B, ws.cm, ws.chunk_sum, nchunks, capacity, keys, ids, rec_binned, pair_off, status);
+}
+
+}  // namespace gi

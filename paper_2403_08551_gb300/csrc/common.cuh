@@ -167,6 +167,67 @@ __device__ __forceinline__ void flag_error(uint32_t* status, uint32_t bits) {
 // wait, so a kernel launched with launch_pdl may be scheduled while its
 // predecessor drains, and still sees all of the predecessor's results (and
 // no predecessor still reads what it overwrites). A no-op for plain launches.
+// Look-back words: 2 flag bits (aggregate / inclusive prefix) over a 30-bit
+// value; spins on an unpublished word are bounded by kSpinLimit.
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagPre = 2u << 30;
+constexpr uint32_t kValMask = (1u << 30) - 1;
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+template <typename Tv>
+__device__ __forceinline__ Tv warp_incl_scan(Tv v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        Tv u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    return v;
+}
+
+template <typename Tv>
+__device__ __forceinline__ Tv warp_sum(Tv v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Inclusive scan over the block (blockDim.x a multiple of 32, <= 1024).
+template <typename Tv>
+__device__ Tv block_incl_scan(Tv v, Tv* s_warp /*[32]*/) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_incl_scan(v);
+    if (lane == 31) s_warp[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        Tv w = lane < nw ? s_warp[lane] : Tv(0);
+        w = warp_incl_scan(w);
+        if (lane < nw) s_warp[lane] = w;
+    }
+    __syncthreads();
+    if (warp > 0) v += s_warp[warp - 1];
+    __syncthreads();
+    return v;
+}
+
+template <typename Tv>
+__device__ Tv block_sum(Tv v, Tv* s_warp /*[32]*/) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum(v);
+    if (lane == 0) s_warp[warp] = v;
+    __syncthreads();
+    Tv r = Tv(0);
+    if (warp == 0) {
+        r = lane < nw ? s_warp[lane] : Tv(0);
+        r = warp_sum(r);
+        if (lane == 0) s_warp[0] = r;
+    }
+    __syncthreads();
+    r = s_warp[0];
+    __syncthreads();
+    return r;
+}
+
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // Launch with the programmatic-stream-serialisation attribute (the launch

@@ -58,19 +58,13 @@ cudaError_t mark(gi_fit* f, int i, cudaStream_t s) {
 }
 
 cudaError_t enqueue_forward(gi_fit* f, cudaStream_t s) {
-    const RadixPlan rp = radix_plan(f->B.total_tiles);
-    const int64_t sblk = std::max<int64_t>(1, (f->capacity + kSortTile - 1) / kSortTile);
     ZeroJob zj{};
-    zj.p[0] = f->bws.hist;
-    zj.n32[0] = (int64_t)rp.passes * 256;
-    zj.p[1] = f->bws.lookback;
-    zj.n32[1] = (int64_t)rp.passes * sblk * 256;
-    zj.p[2] = f->bws.tickets;
-    zj.n32[2] = 4;
-    zj.p[3] = reinterpret_cast<uint32_t*>(f->ranges);
-    zj.n32[3] = (int64_t)f->B.total_tiles * 2;
-    zj.p[4] = reinterpret_cast<uint32_t*>(f->loss);
-    zj.n32[4] = (int64_t)f->nimg * 2;
+    zj.p[0] = f->bws.zero;
+    zj.n32[0] = f->bws.zero_words;
+    zj.p[1] = reinterpret_cast<uint32_t*>(f->ranges);
+    zj.n32[1] = (int64_t)f->B.total_tiles * 2;
+    zj.p[2] = reinterpret_cast<uint32_t*>(f->loss);
+    zj.n32[2] = (int64_t)f->nimg * 2;
     cudaError_t e = mark(f, 0, s);
     if (e == cudaSuccess)
         e = launch_project(params_aos(f->params), f->B, f->rec, f->rect, f->cnt, f->bws.blk_sum, zj, s);

@@ -36,13 +36,28 @@ constexpr int kSortThreads = 256;      // threads per onesweep block
 constexpr int kSortItems = 8;          // keys per thread
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per onesweep block
 
-// Binning workspace carve-up.
+// Count-matrix binning (bin_cm.cu): chunks of kCmChunk Gaussians; used when
+// the batch has at most kCmMaxTiles tiles and chunks x tiles <= kCmMaxCells.
+constexpr int kCmChunk = 128;
+constexpr int kCmMaxTiles = 2048;
+constexpr int64_t kCmMaxCells = int64_t(1) << 20;
+bool cm_applies(int64_t n, int total_tiles);
+
+// Binning workspace carve-up. [zero, zero + zero_words) holds every buffer
+// that must be zero before a binning pass. Radix path: keys_tmp, vals_tmp,
+// hist, lookback [passes][sort_blocks][256]. Count-matrix path: cm
+// [chunks][tiles], chunk_sum [chunks], lookback [tile groups].
 struct BinWs {
+    bool cm_path;
     int64_t* blk_sum;     // [ceil(n / kProjBlock)]
-    uint32_t* keys_tmp;   // [capacity]
-    uint32_t* vals_tmp;   // [capacity]
-    uint32_t* hist;       // [passes][256]
-    uint32_t* lookback;   // [passes][sort_blocks][256]
+    uint32_t* keys_tmp;   // [capacity]          (radix)
+    uint32_t* vals_tmp;   // [capacity]          (radix)
+    uint32_t* cm;         // [chunks][tiles]     (count matrix)
+    uint32_t* chunk_sum;  // [chunks]            (count matrix)
+    uint32_t* zero;
+    int64_t zero_words;
+    uint32_t* hist;       // [passes][256]       (radix)
+    uint32_t* lookback;
     uint32_t* tickets;    // [4]
     size_t bytes;
 };
@@ -55,6 +70,11 @@ cudaError_t launch_bin(const int4* rect, const int32_t* cnt, const float4* rec, 
                        int64_t capacity, const BinWs& ws, bool blk_sum_ready, uint32_t* keys,
                        uint32_t* ids, int2* ranges, float4* rec_binned, int64_t* pair_off,
                        int64_t* k_dev, int64_t* k_max, uint32_t* status, cudaStream_t s);
+
+cudaError_t launch_bin_cm(const int4* rect, const int32_t* cnt, const float4* rec, const Batch& B,
+                          int64_t capacity, const BinWs& ws, bool zero_ready, uint32_t* keys, uint32_t* ids,
+                          int2* ranges, float4* rec_binned, int64_t* pair_off, int64_t* k_dev, int64_t* k_max,
+                          uint32_t* status, cudaStream_t s);
 
 // Forward render: out (HWC), optional loss sum (double per image), dL/dC in
 // HWC (dl_hwc) and/or planar per tile (dl_tiled: [tile][R,G,B][T*T] f32).

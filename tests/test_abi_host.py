@@ -56,9 +56,15 @@ def test_invalid_arguments_rejected_on_host(lib):
     sz = ctypes.c_size_t(0)
     assert lib.gi_bin_workspace_size(100, img, 0, ctypes.byref(sz)) == 1
     assert lib.gi_bin_workspace_size(100, img, 1 << 30, ctypes.byref(sz)) == 1
-    assert lib.gi_bin_workspace_size(100, img, 5000, ctypes.byref(sz)) == 0 and sz.value > 5000 * 8
+    # few tiles: count-matrix binning, scratch sized by chunks x tiles, not by capacity
+    assert lib.gi_bin_workspace_size(1000, img, 5000, ctypes.byref(sz)) == 0 and sz.value >= 8 * 16 * 4
     small = sz.value
-    assert lib.gi_bin_workspace_size(100, img, 50000, ctypes.byref(sz)) == 0 and sz.value > small
+    assert lib.gi_bin_workspace_size(1000, img, 50000, ctypes.byref(sz)) == 0 and sz.value == small
+    # many tiles: radix binning, two key/value buffers of the pair capacity
+    big = _lib.GIImage(4096, 4096, 16)
+    assert lib.gi_bin_workspace_size(100, big, 5000, ctypes.byref(sz)) == 0 and sz.value > 5000 * 8
+    small = sz.value
+    assert lib.gi_bin_workspace_size(100, big, 50000, ctypes.byref(sz)) == 0 and sz.value > small
     assert lib.gi_backward_workspace_size(100, img, 5000, ctypes.byref(sz)) == 0 and sz.value >= 5000 * 32
     # n = 0 is a no-op that needs no pointers
     assert lib.gi_project(None, None, None, 0, img, None, None, None, None) == 0

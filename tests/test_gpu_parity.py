@@ -126,6 +126,42 @@ def test_forward_backward_matches_oracle(gi, W, H, n, T, seed):
     check_grads(g["gq"], ref["grads"]["conic"], "conic", rel=3e-4)
 
 
+BIN_CASES = [
+    # (W, H, n, T, seed, scale): both binning paths on either side of the
+    # 2048-tile limit of the count-matrix path, several 128-Gaussian chunks
+    # with a ragged last one, and wide Gaussians whose tiles are shared by
+    # every lane of a warp.
+    (1024, 512, 5000, 16, 21, 1.0),    # 2048 tiles: count matrix
+    (1024, 528, 5000, 16, 22, 1.0),    # 2112 tiles: radix sort
+    (300, 200, 1000, 8, 23, 6.0),      # 1026 tiles, wide Gaussians: count matrix
+    (1400, 700, 3000, 16, 24, 6.0),    # 3872 tiles, wide Gaussians: radix sort
+    (96, 96, 129, 32, 25, 1.0),        # 9 tiles, two chunks (one Gaussian in the second)
+]
+
+
+@pytest.mark.parametrize("W,H,n,T,seed,scale", BIN_CASES)
+def test_binning_paths_match_oracle(gi, W, H, n, T, seed, scale):
+    means, chol, color = synth.init_gaussians(n, W, H, seed)
+    chol = (chol * np.float32(scale)).astype(np.float32)
+    rect_ref, cnt_ref = oracle.rect_rule(means, chol, color, W, H, T)
+    ids_ref, ranges_ref, off_ref = oracle.bin_tiles(rect_ref, cnt_ref, W, H, T)
+    rec, rect, cnt = gi.project(dev(means), dev(chol), dev(color), W, H, T)
+    np.testing.assert_array_equal(rect.cpu().numpy(), rect_ref)
+    bins = gi.bin_tiles(rect, cnt, rec, W, H, T)
+    torch.cuda.synchronize()
+    K = ids_ref.shape[0]
+    assert bins.K == K
+    np.testing.assert_array_equal(bins.ids[:K].cpu().numpy().astype(np.uint32), ids_ref)
+    np.testing.assert_array_equal(bins.ranges.cpu().numpy(), ranges_ref)
+    np.testing.assert_array_equal(bins.pair_off.cpu().numpy(), off_ref)
+    tw, th = oracle.tiles(W, H, T)
+    np.testing.assert_array_equal(bins.keys[:K].cpu().numpy(),
+                                  np.repeat(np.arange(tw * th), ranges_ref[:, 1] - ranges_ref[:, 0]))
+    # rec_binned[k] is the record of ids[k]
+    rb = bins.rec_binned[:K].cpu().numpy()
+    np.testing.assert_array_equal(rb, rec.cpu().numpy()[ids_ref.astype(np.int64)])
+
+
 def test_backward_arbitrary_upstream(gi):
     """Backward with a seeded random dL/dC (not from an L2 loss)."""
     W, H, T, n = 120, 88, 16, 700
