@@ -43,10 +43,19 @@ __device__ void zero_job(const ZeroJob& zj) {
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kProjBlock) k_project(ParamsIn P, Batch B, float4* __restrict__ rec,
                                                         int4* __restrict__ rect, int32_t* __restrict__ cnt,
-                                                        int64_t* __restrict__ blk_sum, ZeroJob zj) {
+                                                        int64_t* __restrict__ blk_sum, ZeroJob zj,
+                                                        uint32_t* __restrict__ M, uint32_t* __restrict__ chunk_sum) {
+    static_assert(kProjBlock == 2 * kCmChunk, "a projection block holds two count-matrix chunks");
+    extern __shared__ uint32_t s_h[];  // with M: [2][total_tiles] tile histograms of the block's two chunks
     __shared__ int64_t s_warp[32];
+    __shared__ uint32_t s_tot[2];
     pdl_wait();
     zero_job(zj);
+    if (M) {
+        for (int i = threadIdx.x; i < 2 * B.total_tiles; i += blockDim.x) s_h[i] = 0u;
+        if (threadIdx.x < 2) s_tot[threadIdx.x] = 0u;
+        __syncthreads();
+    }
     const int g = blockIdx.x * kProjBlock + threadIdx.x;
     int c = 0;
     if (g < B.total_gauss) {
@@ -104,9 +113,26 @@ __global__ void __launch_bounds__(kProjBlock) k_project(ParamsIn P, Batch B, flo
         rec[2 * (int64_t)g + 1] = r1;
         rect[g] = r;
         cnt[g] = c;
+        if (M && c > 0) {  // count-matrix rows of the fit path (see bin_cm.cu)
+            const int half = threadIdx.x / kCmChunk;
+            uint32_t* h = s_h + half * B.total_tiles;
+            for (int ty = r.y; ty < r.w; ++ty)
+                for (int tx = r.x; tx < r.z; ++tx) atomicAdd(&h[d.tile_base + ty * d.tw + tx], 1u);
+            atomicAdd(&s_tot[half], (uint32_t)c);
+        }
     }
-    const int64_t tot = block_sum<int64_t>((int64_t)c, s_warp);
+    const int64_t tot = block_sum<int64_t>((int64_t)c, s_warp);  // its barriers also complete the histograms
     if (threadIdx.x == 0 && blk_sum) blk_sum[blockIdx.x] = tot;
+    if (M) {
+        const int nchunks = (B.total_gauss + kCmChunk - 1) / kCmChunk;
+        for (int q = 0; q < 2; ++q) {
+            const int chunk = 2 * blockIdx.x + q;
+            if (chunk >= nchunks) break;
+            uint32_t* row = M + (size_t)chunk * B.total_tiles;
+            for (int i = threadIdx.x; i < B.total_tiles; i += blockDim.x) row[i] = s_h[q * B.total_tiles + i];
+            if (threadIdx.x == 0) chunk_sum[chunk] = s_tot[q];
+        }
+    }
 }
 
 // Block sums of an existing cnt[] (standalone binning), plus zeroing.
@@ -393,9 +419,11 @@ BinWs bin_ws_layout(void* base, int64_t n, int64_t capacity, int total_tiles) {
 }
 
 cudaError_t launch_project(const ParamsIn& P, const Batch& B, float4* rec, int4* rect, int32_t* cnt,
-                           int64_t* blk_sum, const ZeroJob& zj, cudaStream_t s) {
+                           int64_t* blk_sum, const ZeroJob& zj, cudaStream_t s, uint32_t* cm, uint32_t* chunk_sum) {
     const int nblk = std::max(1, (B.total_gauss + kProjBlock - 1) / kProjBlock);
-    return launch_pdl(k_project, dim3(nblk), dim3(kProjBlock), 0, s, P, B, rec, rect, cnt, blk_sum, zj);
+    const size_t smem = cm ? (size_t)2 * B.total_tiles * 4 : 0;
+    return launch_pdl(k_project, dim3(nblk), dim3(kProjBlock), smem, s, P, B, rec, rect, cnt, blk_sum, zj, cm,
+                      chunk_sum);
 }
 
 cudaError_t launch_bin(const int4* rect, const int32_t* cnt, const float4* rec, const Batch& B, int64_t capacity,

@@ -48,8 +48,35 @@ __device__ __forceinline__ bool rect_ok(const int4& r, const ImgDesc& d, int c) 
 struct ChunkSmem {
     int off[kCmChunk + 1];
     int4 rect[kCmChunk];
-    int2 img[kCmChunk];  // (tile_base, tw)
+    int2 img[kCmChunk];      // (tile_base, tw)
+    float inv_w[kCmChunk];  // 1 / rect width, correctly rounded
 };
+
+// Pairs are spread over the lanes of the warp that owns their Gaussians:
+// pair p of the warp's list (emission order) goes to lane p mod 32, which
+// finds the owning lane l (the last lane with woff[l] <= p, woff = the
+// warp's exclusive prefix of the counts, one value per lane) by a 5-step
+// shuffle search, then the tile from the pair's index j inside the rect.
+// The row q = floor(j / w) is computed as (j + 0.5) * (1/w) truncated: with
+// j < 2^11 the product's error stays below 2^-12 / w, less than the 0.5 / w
+// distance of (j + 0.5) / w from an integer, so q is exact.
+__device__ __forceinline__ int warp_owner(int woff, int p) {
+    int lo = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+        const int cand = lo + step;
+        const int o = __shfl_sync(0xffffffffu, woff, cand & 31);
+        if (cand < 32 && o <= p) lo = cand;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int pair_tile(const ChunkSmem& cs, int li, int j) {
+    const int4 r = cs.rect[li];
+    const int w = r.z - r.x;
+    const int q = __float2int_rz(((float)j + 0.5f) * cs.inv_w[li]);
+    return cs.img[li].x + (r.y + q) * cs.img[li].y + r.x + (j - q * w);
+}
 
 // Loads this thread's Gaussian (count, rect, image) into the chunk layout
 // and returns its count (0 for a bad rect, with *bad set). Ends with the
@@ -71,6 +98,7 @@ __device__ __forceinline__ int load_chunk(const int4* __restrict__ rect, const i
     }
     cs.rect[threadIdx.x] = r;
     cs.img[threadIdx.x] = im;
+    cs.inv_w[threadIdx.x] = c > 0 ? __frcp_rn((float)(r.z - r.x)) : 0.f;
     const int incl = block_incl_scan<int>(c, s_warp);
     cs.off[threadIdx.x + 1] = incl;
     if (threadIdx.x == 0) cs.off[0] = 0;
@@ -98,11 +126,16 @@ __global__ void __launch_bounds__(kCmChunk) k_count(const int4* __restrict__ rec
     bool bad;
     const int c = load_chunk(rect, cnt, B, b * kCmChunk + threadIdx.x, cs, s_warp, &bad);  // k_place raises the error
     const int total = cs.off[kCmChunk];
-    const int4 r = cs.rect[threadIdx.x];
-    const int base = cs.img[threadIdx.x].x, tw = cs.img[threadIdx.x].y;
-    if (c > 0)
-        for (int ty = r.y; ty < r.w; ++ty)
-            for (int tx = r.x; tx < r.z; ++tx) atomicAdd(&s_h[base + ty * tw + tx], 1u);
+    {
+        const int lane = threadIdx.x & 31, w0 = threadIdx.x & ~31;
+        const int woff = cs.off[threadIdx.x] - cs.off[w0];
+        const int wtot = cs.off[w0 + 32] - cs.off[w0];
+        for (int p = lane; p - lane < wtot; p += 32) {  // warp-uniform trip count
+            const int l = warp_owner(woff, p);
+            const int j = p - __shfl_sync(0xffffffffu, woff, l);
+            if (p < wtot) atomicAdd(&s_h[pair_tile(cs, w0 + l, j)], 1u);
+        }
+    }
     __syncthreads();
     uint32_t* row = M + (size_t)b * Tn;
     for (int i = threadIdx.x; i < Tn; i += blockDim.x) row[i] = s_h[i];
@@ -117,18 +150,21 @@ __global__ void __launch_bounds__(kCmChunk) k_count(const int4* __restrict__ rec
 // tiles and chains the block total through lower tickets (warp-wide
 // look-back over 32 predecessors per round, retried until the words up to
 // the nearest inclusive prefix are all published; bounded spin). Pass 2
-// rereads the rows and writes P[r][t] = start[t] + prefix over M in place.
-// The block holding the last tile stores K, updates k_max and raises the
-// capacity error.
+// rereads the rows and writes P[r][t] = start[t] + prefix over M in place,
+// and warp w writes the sorted keys of the group's tile w (the tile id over
+// its range). The block holding the last tile stores K, updates k_max and
+// raises the capacity error.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kCmScanWarps * 32) k_colscan(uint32_t* __restrict__ M, int nchunks, int total_tiles,
-                                                               int2* __restrict__ ranges, int64_t capacity,
+                                                               int2* __restrict__ ranges, uint32_t* __restrict__ keys,
+                                                               int64_t capacity,
                                                                int64_t* __restrict__ k_dev, int64_t* __restrict__ k_max,
                                                                uint32_t* __restrict__ lookback,
                                                                uint32_t* __restrict__ ticket,
                                                                uint32_t* __restrict__ status) {
     __shared__ uint32_t s_part[kCmScanWarps][32];
     __shared__ uint32_t s_start[32];
+    __shared__ uint32_t s_col[32];
     __shared__ uint32_t s_ticket;
     pdl_wait();
     if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1u);
@@ -173,7 +209,10 @@ __global__ void __launch_bounds__(kCmScanWarps * 32) k_colscan(uint32_t* __restr
             if (lane >= o) in += u;
         }
         s_part[lane][warp] = in - x;
-        if (lane == 31) s_start[warp] = in;  // column total, replaced by the start below
+        if (lane == 31) {
+            s_start[warp] = in;  // column total, replaced by the start below
+            s_col[warp] = in;
+        }
     }
     __syncthreads();
     if (warp == 0) {
@@ -232,6 +271,14 @@ __global__ void __launch_bounds__(kCmScanWarps * 32) k_colscan(uint32_t* __restr
         }
     }
     __syncthreads();
+    {
+        // keys: warp w writes tile (32 blk + w) over its sorted range
+        const int tk = blk * kCmGroupTiles + warp;
+        if (tk < total_tiles) {
+            const int64_t s0 = s_start[warp], e0 = min(s0 + (int64_t)s_col[warp], capacity);
+            for (int64_t q = s0 + lane; q < e0; q += 32) keys[q] = (uint32_t)tk;
+        }
+    }
     if (tv && in_regs) {
         uint32_t run = s_start[lane] + s_part[warp][lane];
 #pragma unroll
@@ -265,7 +312,8 @@ __global__ void __launch_bounds__(kCmScanWarps * 32) k_colscan(uint32_t* __restr
 // Gaussian 32 w + l covers tile t) are built with atomicOr, which is
 // order-independent; then pair (t, g), g = 128 b + 32 w + l, lands at
 //   P[b][t] + sum_{w' < w} popc(s_m[w'][t]) + popc(s_m[w][t] & bits below l),
-// i.e. ascending g inside the tile. The chunk's row of P and its records
+// i.e. ascending g inside the tile; the block writes ids and records there
+// (the keys come from the column scan). The chunk's row of P and its records
 // are staged in shared memory. pair_off = exclusive scan of cnt in emission order, the
 // chunk base from the chunk totals.
 // ---------------------------------------------------------------------------
@@ -273,9 +321,9 @@ __global__ void __launch_bounds__(kCmChunk) k_place(const int4* __restrict__ rec
                                                     const float4* __restrict__ rec, Batch B,
                                                     const uint32_t* __restrict__ P,
                                                     const uint32_t* __restrict__ chunk_sum, int nchunks,
-                                                    int64_t capacity, uint32_t* __restrict__ keys,
-                                                    uint32_t* __restrict__ ids, float4* __restrict__ rec_binned,
-                                                    int64_t* __restrict__ pair_off, uint32_t* __restrict__ status) {
+                                                    int64_t capacity, uint32_t* __restrict__ ids,
+                                                    float4* __restrict__ rec_binned, int64_t* __restrict__ pair_off,
+                                                    uint32_t* __restrict__ status) {
     constexpr int NW = kCmChunk / 32;
     constexpr int kRowLoads = kCmMaxTiles / kCmChunk;
     extern __shared__ uint32_t s_dyn[];  // [NW][total_tiles] lane masks, then [total_tiles] P row
@@ -317,33 +365,27 @@ __global__ void __launch_bounds__(kCmChunk) k_place(const int4* __restrict__ rec
     const int off = cs.off[threadIdx.x];
     if (g < B.total_gauss) pair_off[g] = pre + off;
     if (b == nchunks - 1 && threadIdx.x == blockDim.x - 1) pair_off[B.total_gauss] = pre + off + c;
-    // Each thread walks its own Gaussian's rect (row-major): fewer
-    // instructions than spreading pairs evenly, at the cost of warps waiting
-    // for their widest Gaussian.
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int4 r = cs.rect[threadIdx.x];
-    const int base = cs.img[threadIdx.x].x, tw = cs.img[threadIdx.x].y;
-    if (c > 0)
-        for (int ty = r.y; ty < r.w; ++ty)
-            for (int tx = r.x; tx < r.z; ++tx) atomicOr(&s_m[warp * Tn + base + ty * tw + tx], 1u << lane);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, w0 = threadIdx.x & ~31;
+    const int woff = cs.off[threadIdx.x] - cs.off[w0];
+    const int wtot = cs.off[w0 + 32] - cs.off[w0];
+    for (int p = lane; p - lane < wtot; p += 32) {  // warp-uniform trip count
+        const int l = warp_owner(woff, p);
+        const int j = p - __shfl_sync(0xffffffffu, woff, l);
+        if (p < wtot) atomicOr(&s_m[warp * Tn + pair_tile(cs, w0 + l, j)], 1u << l);
+    }
     __syncthreads();
-    if (c > 0) {
-        const float4 ra = rec_binned ? s_rec[threadIdx.x][0] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 rb = rec_binned ? s_rec[threadIdx.x][1] : ra;
-        const uint32_t lt = lanemask_lt();
-        for (int ty = r.y; ty < r.w; ++ty) {
-            for (int tx = r.x; tx < r.z; ++tx) {
-                const int t = base + ty * tw + tx;
-                uint32_t pos = s_p[t] + __popc(s_m[warp * Tn + t] & lt);
-                for (int v = 0; v < warp; ++v) pos += __popc(s_m[v * Tn + t]);
-                if ((int64_t)pos >= capacity) continue;  // dropped; the scan raised the capacity error
-                keys[pos] = (uint32_t)t;
-                ids[pos] = (uint32_t)g;
-                if (rec_binned) {
-                    rec_binned[2 * (size_t)pos] = ra;
-                    rec_binned[2 * (size_t)pos + 1] = rb;
-                }
-            }
+    for (int p = lane; p - lane < wtot; p += 32) {
+        const int l = warp_owner(woff, p);
+        const int j = p - __shfl_sync(0xffffffffu, woff, l);
+        if (p >= wtot) continue;
+        const int t = pair_tile(cs, w0 + l, j);
+        uint32_t pos = s_p[t] + __popc(s_m[warp * Tn + t] & ((1u << l) - 1u));
+        for (int v = 0; v < warp; ++v) pos += __popc(s_m[v * Tn + t]);
+        if ((int64_t)pos >= capacity) continue;  // dropped; the scan raised the capacity error
+        ids[pos] = (uint32_t)(b * kCmChunk + w0 + l);
+        if (rec_binned) {
+            rec_binned[2 * (size_t)pos] = s_rec[w0 + l][0];
+            rec_binned[2 * (size_t)pos + 1] = s_rec[w0 + l][1];
         }
     }
 }
@@ -356,18 +398,21 @@ bool cm_applies(int64_t n, int total_tiles) {
 }
 
 cudaError_t launch_bin_cm(const int4* rect, const int32_t* cnt, const float4* rec, const Batch& B, int64_t capacity,
-                          const BinWs& ws, bool zero_ready, uint32_t* keys, uint32_t* ids, int2* ranges,
+                          const BinWs& ws, bool prepared, uint32_t* keys, uint32_t* ids, int2* ranges,
                           float4* rec_binned, int64_t* pair_off, int64_t* k_dev, int64_t* k_max, uint32_t* status,
                           cudaStream_t s) {
     const int n = B.total_gauss;
     const int Tn = B.total_tiles;
     const int nchunks = std::max(1, (n + kCmChunk - 1) / kCmChunk);
     const int groups = (Tn + kCmGroupTiles - 1) / kCmGroupTiles;
-    cudaError_t e = launch_pdl(k_count, dim3(nchunks), dim3(kCmChunk), (size_t)Tn * 4, s, rect, cnt, B, ws.cm,
-                               ws.chunk_sum, zero_ready ? nullptr : ws.zero, zero_ready ? (int64_t)0 : ws.zero_words);
-    if (e != cudaSuccess) return e;
-    e = launch_pdl(k_colscan, dim3(groups), dim3(kCmScanWarps * 32), 0, s, ws.cm, nchunks, Tn, ranges, capacity, k_dev,
-                   k_max, ws.lookback, ws.tickets, status);
+    cudaError_t e = cudaSuccess;
+    if (!prepared) {
+        e = launch_pdl(k_count, dim3(nchunks), dim3(kCmChunk), (size_t)Tn * 4, s, rect, cnt, B, ws.cm, ws.chunk_sum,
+                       ws.zero, ws.zero_words);
+        if (e != cudaSuccess) return e;
+    }
+    e = launch_pdl(k_colscan, dim3(groups), dim3(kCmScanWarps * 32), 0, s, ws.cm, nchunks, Tn, ranges, keys, capacity,
+                   k_dev, k_max, ws.lookback, ws.tickets, status);
     if (e != cudaSuccess) return e;
     static bool attr = false;  // up to 40 KB dynamic + the static layout: above the default 48 KB window
     if (!attr) {
@@ -377,7 +422,7 @@ cudaError_t launch_bin_cm(const int4* rect, const int32_t* cnt, const float4* re
         attr = true;
     }
     return launch_pdl(k_place, dim3(nchunks), dim3(kCmChunk), (size_t)(kCmChunk / 32 + 1) * Tn * 4, s, rect, cnt, rec,
-                      B, ws.cm, ws.chunk_sum, nchunks, capacity, keys, ids, rec_binned, pair_off, status);
+                      B, ws.cm, ws.chunk_sum, nchunks, capacity, ids, rec_binned, pair_off, status);
 }
 
 }  // namespace gi

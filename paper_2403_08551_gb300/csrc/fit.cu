@@ -67,7 +67,8 @@ cudaError_t enqueue_forward(gi_fit* f, cudaStream_t s) {
     zj.n32[2] = (int64_t)f->nimg * 2;
     cudaError_t e = mark(f, 0, s);
     if (e == cudaSuccess)
-        e = launch_project(params_aos(f->params), f->B, f->rec, f->rect, f->cnt, f->bws.blk_sum, zj, s);
+        e = launch_project(params_aos(f->params), f->B, f->rec, f->rect, f->cnt, f->bws.blk_sum, zj, s, f->bws.cm,
+                           f->bws.chunk_sum);
     if (e == cudaSuccess) e = mark(f, 1, s);
     if (e == cudaSuccess)
         e = launch_bin(f->rect, f->cnt, f->rec, f->B, f->capacity, f->bws, true, f->keys, f->ids, f->ranges,

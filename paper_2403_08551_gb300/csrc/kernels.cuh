@@ -64,15 +64,20 @@ struct BinWs {
 BinWs bin_ws_layout(void* base, int64_t n, int64_t capacity, int total_tiles);
 
 // Launchers (stream-ordered, no host synchronisation).
+// With cm != null (count-matrix binning to follow) the projection also
+// writes the count-matrix rows and chunk totals of its Gaussians.
 cudaError_t launch_project(const ParamsIn& P, const Batch& B, float4* rec, int4* rect, int32_t* cnt,
-                           int64_t* blk_sum, const ZeroJob& zj, cudaStream_t s);
+                           int64_t* blk_sum, const ZeroJob& zj, cudaStream_t s, uint32_t* cm = nullptr,
+                           uint32_t* chunk_sum = nullptr);
 cudaError_t launch_bin(const int4* rect, const int32_t* cnt, const float4* rec, const Batch& B,
                        int64_t capacity, const BinWs& ws, bool blk_sum_ready, uint32_t* keys,
                        uint32_t* ids, int2* ranges, float4* rec_binned, int64_t* pair_off,
                        int64_t* k_dev, int64_t* k_max, uint32_t* status, cudaStream_t s);
 
+// prepared: the projection already wrote the count-matrix rows and cleared
+// the scratch (fit path); otherwise k_count does both.
 cudaError_t launch_bin_cm(const int4* rect, const int32_t* cnt, const float4* rec, const Batch& B,
-                          int64_t capacity, const BinWs& ws, bool zero_ready, uint32_t* keys, uint32_t* ids,
+                          int64_t capacity, const BinWs& ws, bool prepared, uint32_t* keys, uint32_t* ids,
                           int2* ranges, float4* rec_binned, int64_t* pair_off, int64_t* k_dev, int64_t* k_max,
                           uint32_t* status, cudaStream_t s);
 
