@@ -47,6 +47,19 @@ __device__ __forceinline__ void pair_sums(const float* __restrict__ G, float4 r0
     const float2 A2 = make_float2(r0.z, r0.z);
     const float2 cr = make_float2(r1.y, r1.y), cg = make_float2(r1.z, r1.z), cb = make_float2(r1.w, r1.w);
     const float2 d0 = make_float2(dx0, dx0 + 1.0f);
+    // dx and dx^2 of the strip's pixel pairs do not depend on the row: kept in
+    // registers for tiles of up to 16 x 16 (two packed FP32 operations fewer
+    // per pixel pair).
+    constexpr bool kHoist = T <= 16;
+    constexpr int NH = kHoist ? T / 2 : 1;
+    float2 DX[NH], DX2[NH];
+    if (kHoist) {
+#pragma unroll
+        for (int i = 0; i < NH; ++i) {
+            DX[i] = __fadd2_rn(d0, make_float2(2.0f * i, 2.0f * i));
+            DX2[i] = __fmul2_rn(DX[i], DX[i]);
+        }
+    }
     float2 gcr = make_float2(0.f, 0.f), gcg = gcr, gcb = gcr;
     // Moment sums with Kahan compensation across rows: the per-pair sums
     // cancel strongly for Gaussians near equilibrium, and the row partials
@@ -70,7 +83,7 @@ __device__ __forceinline__ void pair_sums(const float* __restrict__ G, float4 r0
                 const float2 gg = h ? make_float2(Gg.z, Gg.w) : make_float2(Gg.x, Gg.y);
                 const float2 gb = h ? make_float2(Bb.z, Bb.w) : make_float2(Bb.x, Bb.y);
                 const float xo = (float)(4 * x4 + 2 * h);
-                const float2 dx = __fadd2_rn(d0, make_float2(xo, xo));
+                const float2 dx = kHoist ? DX[kHoist ? 2 * x4 + h : 0] : __fadd2_rn(d0, make_float2(xo, xo));
                 const float2 s = __ffma2_rn(__ffma2_rn(A2, dx, B2), dx, C2);
                 const float2 w = make_float2(ex2(s.x), ex2(s.y));  // exp(-sigma)
                 gcr = __ffma2_rn(gr, w, gcr);
@@ -79,9 +92,14 @@ __device__ __forceinline__ void pair_sums(const float* __restrict__ G, float4 r0
                 const float2 gw = __ffma2_rn(gb, cb, __ffma2_rn(gg, cg, __fmul2_rn(gr, cr)));
                 const float2 e = __fmul2_rn(gw, w);
                 u = __fadd2_rn(u, e);
-                const float2 t1 = __fmul2_rn(e, dx);
-                v = __fadd2_rn(v, t1);
-                q = __ffma2_rn(t1, dx, q);
+                if (kHoist) {
+                    v = __ffma2_rn(e, dx, v);
+                    q = __ffma2_rn(e, DX2[kHoist ? 2 * x4 + h : 0], q);
+                } else {
+                    const float2 t1 = __fmul2_rn(e, dx);
+                    v = __fadd2_rn(v, t1);
+                    q = __ffma2_rn(t1, dx, q);
+                }
             }
         }
         const float us = u.x + u.y, vs = v.x + v.y, qs = q.x + q.y;
@@ -122,7 +140,7 @@ constexpr size_t backward_smem() { return stage_dl<T>() ? 8 * 2 * tile_floats<T>
 // spans more than two tiles (only tiles with fewer than 32 pairs do) repeats
 // this for the lanes left. Larger tiles read dL/dC from global memory.
 template <int T>
-__global__ void __launch_bounds__(256, 3) k_backward(const float4* __restrict__ rec_binned,
+__global__ void __launch_bounds__(256, T == 16 ? 2 : 3) k_backward(const float4* __restrict__ rec_binned,
                                                   const uint32_t* __restrict__ keys,
                                                   const uint32_t* __restrict__ ids, const int4* __restrict__ rect,
                                                   const int64_t* __restrict__ pair_off,
