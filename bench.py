@@ -40,6 +40,10 @@ WORKLOAD = "c1_768x512_70k"
 LR = (1e-3, 1e-2, 1e-2)
 FWD_FLOP_PER_EVAL = 11   # 1 FADD + 2 FFMA (quadratic form) + 3 FFMA (accumulate); exp on the SFU
 BWD_FLOP_PER_EVAL = 22   # 1 FADD + 2 FFMA + 3 FFMA + FMUL + 2 FFMA + FMUL + FADD + FMUL + FADD + FFMA
+# DRAM bytes (read + write) per launch of the ALU-bound kernels at this
+# workload, from one ncu --set full capture of the current kernels
+# (profiles/k_backward_c1_768x512_70k.md, profiles/k_render_c1_768x512_70k.md).
+NCU_TRAFFIC_BYTES = {"k_backward": 20.628e6, "k_render": 16.119e6}
 # SFU_LANES: ex2 results per clock per SM as measured by gi_alu_peaks on GB300
 # (9.99e12 ex2/s at 2064 MHz over 152 SMs = 32).
 SMS, FP32_LANES, SFU_LANES, SM_MAX_MHZ = 152, 128, 32, 2070.0
@@ -403,7 +407,9 @@ def main():
     dom = "backward" if stage_ms[3] >= stage_ms[2] else "render"
     ach = bwd_tflops if dom == "backward" else fwd_tflops
     roof = {"kernel": "k_backward" if dom == "backward" else "k_render", "bound": "alu", "achieved": ach,
-            "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+            "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
+            "traffic": (NCU_TRAFFIC_BYTES.get("k_backward" if dom == "backward" else "k_render")
+                        if T == 16 else None), "traffic_unit": "bytes per launch (ncu dram read + write)",
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz",
             "sfu_frac": (ev_all / (stage_ms[3 if dom == 'backward' else 2] * 1e-3))
             / (SMS * SFU_LANES * SM_MAX_MHZ * 1e6)}

@@ -99,6 +99,47 @@ def test_five_steps_track_oracle(gi):
     fit.close()
 
 
+@pytest.mark.slow
+def test_full_size_five_steps(gi):
+    """The 768x512, 70k-Gaussian fitting workload at tile 16 (the benchmark's
+    configuration), first five Adam steps. At every step the oracle is
+    evaluated at the GPU's own parameters, so each step's loss and gradients
+    are checked exactly (tolerance of test_gpu_parity with its conditioning
+    clause), and the Adam update from the GPU's own moments is checked
+    against the oracle's update inside the envelope a gradient error of that
+    size allows."""
+    w = synth.workload("c1_768x512_70k")
+    T = 16
+    p0 = pack(w.means, w.chol, w.color)
+    fit = gi.Fit([torch.from_numpy(w.target).cuda()], [torch.from_numpy(p0).cuda()], tile=T, lr=LR)
+    lr = lr_vec(w.n)
+    for t in range(1, 6):
+        pg = fit.params.cpu().numpy().astype(np.float64)
+        mg = fit.adam_m.cpu().numpy().astype(np.float64)
+        vg = fit.adam_v.cpu().numpy().astype(np.float64)
+        g_ref, loss_ref, g_abs = oracle_grads(pg, w.target, T, with_abs=True)
+        fit.step(1)
+        torch.cuda.synchronize()
+        assert fit.mse()[0] == pytest.approx(loss_ref, rel=1e-5)
+        g_gpu = fit.grads.cpu().numpy().astype(np.float64)
+        tol_g = np.zeros_like(g_ref)
+        for sl in (slice(0, 2), slice(2, 5), slice(5, 8)):
+            s = np.abs(g_ref[:, sl]).max()
+            rel = GRAD_TOL * np.maximum(np.abs(g_ref[:, sl]), 1e-3 * s)
+            err = np.abs(g_gpu[:, sl] - g_ref[:, sl])
+            cond = (err > rel) & (err <= 16 * 2.0 ** -24 * g_abs[:, sl])
+            assert cond.mean() <= 1e-3, f"step {t}: {cond.sum()} elements need the conditioning bound"
+            assert np.all((err <= rel) | cond), f"step {t}: gradient outside tolerance"
+            tol_g[:, sl] = np.maximum(rel, 16 * 2.0 ** -24 * g_abs[:, sl])
+        p_ref, _, _ = oracle.adam(pg, g_ref, mg, vg, t, lr)
+        p_new = fit.params.cpu().numpy().astype(np.float64)
+        close = np.abs(p_new - p_ref) <= 1e-5 * np.maximum(np.abs(p_ref), 1.0) + 1e-3 * lr
+        assert close.mean() > 0.999, f"step {t}: {np.sum(~close)} parameters off the oracle's update"
+        assert np.all(np.abs(p_new - p_ref) <= 2 * lr + 1e-5 * np.maximum(np.abs(p_ref), 1.0))
+    assert int(fit.step_count.item()) == 5
+    fit.close()
+
+
 def test_graph_replay_equals_eager(gi):
     W, H, T, n = 160, 120, 16, 1500
     target = torch.from_numpy(synth.image(W, H, 22, n_blobs=20)).cuda()
