@@ -50,6 +50,21 @@ SMS, FP32_LANES, SFU_LANES, SM_MAX_MHZ = 152, 128, 32, 2070.0
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5 (FMA = 2 flops)
 
 
+def max_over_ranks(torch, x, device):
+    """Maximum of x over the ranks of the default process group (x itself
+    without one): the job's time is its slowest replica's."""
+    if not (torch.distributed.is_available() and torch.distributed.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, units_per_rank, t_max):
+    """Whole-job throughput: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / t_max
+
+
 def env_rank():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
         os.environ.get("LOCAL_RANK", "0"))
@@ -233,13 +248,77 @@ def batched_vs_plain(gi, torch, n_images, steps, stream):
     for f in plain:
         f.close()
     psnr = lambda e: 10 * math.log10(1.0 / e) if e > 0 else float("inf")  # noqa: E731
-    dpsnr = max(abs(psnr(a) - psnr(b)) for a, b in zip(mse_b, mse_p))
+    d = [abs(psnr(a) - psnr(b)) for a, b in zip(mse_b, mse_p)]
+    dpsnr = max(d)
     return {"images": n_images, "steps": steps, "sizes": "uniform over 256x256, 512x384, 768x512, 1024x768",
             "gaussians": int(sum(w.n for w in ws)), "tile": T, "render_split": sp,
             "autotune_ms_per_step": {f"{k[0]}/{k[1]}": v for k, v in tune["ms_per_step"].items()},
             "batched_image_steps_per_s": n_images * steps / t_b, "plain_image_steps_per_s": n_images * steps / t_p,
             "batched_images_fitted_per_s": n_images / t_b, "plain_images_fitted_per_s": n_images / t_p,
-            "speedup": t_p / t_b, "max_abs_dpsnr_db": dpsnr}
+            "speedup": t_p / t_b, "max_abs_dpsnr_db": dpsnr, "mean_abs_dpsnr_db": sum(d) / len(d),
+            "mean_psnr_db_batched": sum(psnr(a) for a in mse_b) / len(mse_b),
+            "mean_psnr_db_plain": sum(psnr(b) for b in mse_p) / len(mse_p)}
+
+
+def long_fit(gi, torch, stream, T, steps):
+    """The full-length fit of the 768x512, 70k-Gaussian workload: `steps`
+    graph-replayed steps back to back (no L2 flush: steady state), timed as
+    one window with CUDA events; PSNR of the first and of the last step's
+    render. The pair capacity leaves room for the Gaussians to grow."""
+    w = synth.workload(WORKLOAD)
+    fit = gi.Fit([torch.from_numpy(w.target).cuda()], [torch.from_numpy(pack(w)).cuda()], tile=T, lr=LR,
+                 capacity_factor=4.0)
+    fit.step(1)
+    torch.cuda.synchronize()
+    psnr = lambda e: 10 * math.log10(1.0 / e) if e > 0 else float("inf")  # noqa: E731
+    p1 = psnr(fit.mse()[0])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    fit.step(steps - 1)
+    e1.record(stream)
+    e1.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    err = gi.device_errors(clear=True)
+    out = {"steps": steps, "iter_s": (steps - 1) / t, "seconds": t, "psnr_db_step1": p1,
+           "psnr_db_final": psnr(fit.mse()[0]), "pairs_final": int(fit.k.item()),
+           "l2": "not flushed between steps (steady state)", "device_errors": int(err)}
+    fit.close()
+    return out
+
+
+def oracle_c0_times(reps=3):
+    """The FP64 oracle on the 256x256, 2k-Gaussian workload (tile 16): median
+    ms of a forward (support rule, binning, render, loss), a forward +
+    backward, and a full fit step (forward + backward + Adam)."""
+    import oracle
+    w = synth.workload("c0_256x256_2k")
+    T = 16
+    p = pack(w).astype(np.float64)
+    lr = np.tile(np.array([LR[0]] * 2 + [LR[1]] * 3 + [LR[2]] * 3), (p.shape[0], 1))
+
+    def fwd():
+        rect, cnt = oracle.rect_rule(w.means, w.chol, w.color, w.W, w.H, T)
+        ids, rg, _ = oracle.bin_tiles(rect, cnt, w.W, w.H, T)
+        oracle.loss(oracle.render(w.means, w.chol, w.color, ids, rg, w.W, w.H, T), w.target)
+
+    def fb():
+        return oracle.forward_backward(w.means, w.chol, w.color, w.target, T)
+
+    def step():
+        r = fb()
+        g = np.concatenate([r["grads"]["means"], r["grads"]["chol"], r["grads"]["color"]], axis=1)
+        oracle.adam(p, g, np.zeros_like(p), np.zeros_like(p), 1, lr)
+
+    res = {}
+    for name, fn in (("forward", fwd), ("forward_backward", fb), ("step", step)):
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            fn()
+            ts.append(time.perf_counter() - t0)
+        res[name] = 1e3 * statistics.median(ts)
+    return {"workload": "c0_256x256_2k (256x256, 2,000 Gaussians, tile 16)", "ms": res,
+            "cores": oracle.num_threads()}
 
 
 def large_image(gi, torch, stream, flush, T=16, reps=20):
@@ -304,6 +383,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the large-image and codec measurements")
     ap.add_argument("--batch-images", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=2000, help="fit steps of the batched vs plain comparison")
+    ap.add_argument("--long-steps", type=int, default=50000, help="steps of the full-length fit (0 = skip)")
     ap.add_argument("--out", default=os.path.join(ROOT, "gpurun_out"))
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
@@ -349,14 +430,8 @@ def main():
             stage += np.array(fit.stage_times())  # waits for this step; the next flush hides launch latency
         barrier()
     step_ms = sum(a.elapsed_time(b) for a, b in ev)
-    t_local = step_ms / 1e3
-    if world > 1:
-        t = torch.tensor([t_local], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    else:
-        t_max = t_local
-    value = world * args.steps / t_max
+    t_max = max_over_ranks(torch, step_ms / 1e3, "cuda")
+    value = job_value(world, args.steps, t_max)
     stage_ms = stage / args.steps
 
     # Render FPS: formation + binning + render (no backward), flushed L2.
@@ -369,6 +444,12 @@ def main():
         evr[i][1].record(stream)
     torch.cuda.synchronize()
     render_ms = sum(a.elapsed_time(b) for a, b in evr) / n_r
+    # The same forward through the per-stage C-ABI calls, launched eagerly.
+    p_r = fit.params.clone()
+    m_r, l_r, c_r = p_r[:, 0:2].contiguous(), p_r[:, 2:5].contiguous(), p_r[:, 5:8].contiguous()
+    rdr = gi.Renderer(w.W, w.H, w.n, T, capacity=fit.capacity)
+    rdr(m_r, l_r, c_r)
+    render_eager_ms = _time(torch, stream, lambda: rdr(m_r, l_r, c_r), n_r, flush)
 
     # Evaluations per render for the current parameters.
     p_now = fit.params.clone()
@@ -396,9 +477,7 @@ def main():
     e2e = {"value": world * n_e / e2e_s if world == 1 else None, "unit": "iter/s",
            "h2d_bytes_per_step": int(host_tgt.numel() * 4), "d2h_bytes_per_step": int(host_loss.numel() * 8)}
     if world > 1:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e["value"] = world * n_e / float(t.item())
+        e2e["value"] = job_value(world, n_e, max_over_ranks(torch, e2e_s, "cuda"))
 
     # Roofline of the dominant kernel (backward or render), FP32-pipe bound.
     names = ["formation", "binning", "render", "backward", "update"]
@@ -422,6 +501,7 @@ def main():
                       "parallelism": f"replica x{world} (independent images)",
                       "l2": "flushed (256 MB write) before every timed step"},
            "render_fps": 1e3 / render_ms, "render_ms": render_ms,
+           "render_fps_modes": {"graph": 1e3 / render_ms, "eager": 1e3 / render_eager_ms},
            "stage_ms": dict(zip(names, [float(x) for x in stage_ms])),
            "pairs": K, "evals_per_render": ev_in, "evals_per_render_padded": ev_all,
            "fwd_evals_per_s": ev_all / (stage_ms[2] * 1e-3), "bwd_evals_per_s": ev_all / (stage_ms[3] * 1e-3),
@@ -431,12 +511,15 @@ def main():
     if rank == 0:
         out["clocks"] = clk.summary()
     if not args.no_batched and rank == 0:
-        out["batched"] = batched_vs_plain(gi, torch, args.batch_images, 20, stream)
+        out["batched"] = batched_vs_plain(gi, torch, args.batch_images, args.batch_steps, stream)
     if not args.no_extra and rank == 0:
         out["large_image"] = large_image(gi, torch, stream, flush)
         out["codec"] = codec_decode(gi, torch, stream, flush)
+    if args.long_steps > 1 and not args.no_extra and rank == 0:
+        out["fit_long"] = long_fit(gi, torch, stream, T, args.long_steps)
     if not args.no_cpu and rank == 0:
         out["cpu_baseline"] = cpu_baseline(w, T)
+        out["cpu_baseline"]["oracle_c0"] = oracle_c0_times()
     fit.close()
     if world > 1:
         torch.distributed.barrier()

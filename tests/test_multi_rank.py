@@ -1,0 +1,69 @@
+"""The benchmark's multi-GPU path on CPU: two gloo ranks (replicas, no data
+collective) agree on the slowest rank's time and the whole-job throughput,
+and the reference arm leaves every rank but 0 without work."""
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+torch = pytest.importorskip("torch")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    sys.path.insert(0, ROOT)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    t = bench.max_over_ranks(torch, 1.0 + 0.5 * rank, "cpu")
+    q.put((rank, t, bench.job_value(world, 10, t)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_agree_on_the_slowest_time():
+    ctx = torch.multiprocessing.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [r[1] for r in res] == [1.5, 1.5]
+    assert all(r[2] == pytest.approx(2 * 10 / 1.5) for r in res)
+
+
+def test_single_process_needs_no_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.max_over_ranks(torch, 2.5, "cpu") == 2.5
+    assert bench.job_value(1, 100, 2.0) == 50.0
+
+
+def test_reference_arm_only_on_rank_zero():
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_replicas_fit_different_images():
+    sys.path.insert(0, ROOT)
+    import synth
+    a = synth.workload("c1_768x512_70k", index=0)
+    b = synth.workload("c1_768x512_70k", index=1)
+    assert a.target.shape == b.target.shape and not (a.target == b.target).all()
+    assert not (a.means == b.means).all()
