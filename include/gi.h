@@ -31,9 +31,10 @@
  *     rx = 3|l1|, ry = 3 sqrt(l2^2 + l3^2)
  *     tx0 = clamp(floor((mx - rx)/T), 0, tw), tx1 = clamp(floor((mx + rx)/T) + 1, 0, tw)
  * (y likewise), tw = ceil(W/T), th = ceil(H/T). A Gaussian whose parameters
- * are non-finite, whose det = (l1 l3)^2 is 0, whose FP32 conic is not finite
- * or whose rectangle is empty is culled (count 0). Pixel i receives Gaussian
- * n iff i's tile lies in n's rectangle.
+ * are non-finite, whose det = (l1 l3)^2 is 0, whose FP32 conic or scaled
+ * inverse Cholesky factor (GI_REC_FLOATS) is not finite, or whose rectangle
+ * is empty is culled (count 0). Pixel i receives Gaussian n iff i's tile
+ * lies in n's rectangle.
  */
 #ifndef GI_H_
 #define GI_H_
@@ -74,9 +75,11 @@ typedef struct {
     int32_t width, height, tile;
 } gi_image;
 
-/* Floats per projected record: (mx, my, A', B', C', c'r, c'g, c'b) where
- * Sigma^-1 = [[A, B], [B, C]] and A' = -A log2(e)/2, B' = -B log2(e),
- * C' = -C log2(e)/2, so exp(-sigma) = exp2(A'dx^2 + B'dx dy + C'dy^2). */
+/* Floats per projected record: (mx, my, m11, m21, m22, c'r, c'g, c'b) where
+ * [[m11, 0], [m21, m22]] = k L^-1, k = sqrt(log2(e)/2), i.e. m11 = k/l1,
+ * m21 = -k l2/(l1 l3), m22 = k/l3. With z1 = m11 dx, z2 = m21 dx + m22 dy:
+ * sigma = 1/2 d^T Sigma^-1 d = (z1^2 + z2^2)/log2(e) and
+ * exp(-sigma) = exp2(-(z1^2 + z2^2)) (Sec. 3.1 with Sigma^-1 = L^-T L^-1). */
 #define GI_REC_FLOATS 8
 
 GI_API int32_t gi_abi_version(void);
@@ -89,7 +92,8 @@ GI_API gi_status gi_device_errors(uint32_t* bits, int32_t clear, gi_stream strea
 
 /* ------------------------------------------------------------------------
  * gi_project -- 2D Gaussian formation (Sec. 3.1, Eq. 1; Sec. 3.2, Eq. 5):
- * Sigma = L L^T, its inverse (the conic) and the support rectangle.
+ * Sigma = L L^T, the scaled inverse Cholesky factor and the support
+ * rectangle.
  *   means [n][2], chol [n][3] = (l1, l2, l3), color [n][3]: device, f32.
  *   rec [n][8] f32 (GI_REC_FLOATS), rect [n][4] i32 (tx0, ty0, tx1, ty1),
  *   cnt [n] i32 = (tx1 - tx0)(ty1 - ty0), 0 when culled (rect = 0).

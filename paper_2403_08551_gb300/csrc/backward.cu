@@ -44,20 +44,22 @@ template <int T>
 __device__ __forceinline__ void pair_sums(const float* __restrict__ G, float4 r0, float4 r1, float dx0, float dyb,
                                           float (&out)[8]) {
     constexpr int NPIX = T * T;
-    const float2 A2 = make_float2(r0.z, r0.z);
+    const float2 M11 = make_float2(r0.z, r0.z), M21 = make_float2(r0.w, r0.w);
     const float2 cr = make_float2(r1.y, r1.y), cg = make_float2(r1.z, r1.z), cb = make_float2(r1.w, r1.w);
     const float2 d0 = make_float2(dx0, dx0 + 1.0f);
-    // dx and dx^2 of the strip's pixel pairs do not depend on the row: kept in
-    // registers for tiles of up to 16 x 16 (two packed FP32 operations fewer
-    // per pixel pair).
+    // dx, dx^2 and z1^2 = (m11 dx)^2 of the strip's pixel pairs do not depend
+    // on the row: kept in registers for tiles of up to 16 x 16, so a pixel
+    // pair costs two packed operations for sigma (z2, then z2^2 + z1^2).
     constexpr bool kHoist = T <= 16;
     constexpr int NH = kHoist ? T / 2 : 1;
-    float2 DX[NH], DX2[NH];
+    float2 DX[NH], DX2[NH], Z1S[NH];
     if (kHoist) {
 #pragma unroll
         for (int i = 0; i < NH; ++i) {
             DX[i] = __fadd2_rn(d0, make_float2(2.0f * i, 2.0f * i));
             DX2[i] = __fmul2_rn(DX[i], DX[i]);
+            const float2 z1 = __fmul2_rn(M11, DX[i]);
+            Z1S[i] = __fmul2_rn(z1, z1);
         }
     }
     float2 gcr = make_float2(0.f, 0.f), gcg = gcr, gcb = gcr;
@@ -68,9 +70,9 @@ __device__ __forceinline__ void pair_sums(const float* __restrict__ G, float4 r0
 #pragma unroll 1
     for (int y = 0; y < T; ++y) {
         const float dy = dyb + (float)y;
-        const float bdy = r0.w * dy, cdy2 = r1.x * dy * dy;
-        const float2 B2 = make_float2(bdy, bdy), C2 = make_float2(cdy2, cdy2);
-        float2 u = make_float2(0.f, 0.f), v = u, q = u;
+        const float z2y = r1.x * dy;
+        const float2 Z2Y = make_float2(z2y, z2y);
+        float2 u = make_float2(0.f, 0.f), v = u, qm = u;
         const float4* Rr = reinterpret_cast<const float4*>(G + y * T);
         const float4* Rg = reinterpret_cast<const float4*>(G + NPIX + y * T);
         const float4* Bb_ = reinterpret_cast<const float4*>(G + 2 * NPIX + y * T);
@@ -83,9 +85,18 @@ __device__ __forceinline__ void pair_sums(const float* __restrict__ G, float4 r0
                 const float2 gg = h ? make_float2(Gg.z, Gg.w) : make_float2(Gg.x, Gg.y);
                 const float2 gb = h ? make_float2(Bb.z, Bb.w) : make_float2(Bb.x, Bb.y);
                 const float xo = (float)(4 * x4 + 2 * h);
-                const float2 dx = kHoist ? DX[kHoist ? 2 * x4 + h : 0] : __fadd2_rn(d0, make_float2(xo, xo));
-                const float2 s = __ffma2_rn(__ffma2_rn(A2, dx, B2), dx, C2);
-                const float2 w = make_float2(ex2(s.x), ex2(s.y));  // exp(-sigma)
+                const int hi = kHoist ? 2 * x4 + h : 0;
+                const float2 dx = kHoist ? DX[hi] : __fadd2_rn(d0, make_float2(xo, xo));
+                const float2 z2 = __ffma2_rn(M21, dx, Z2Y);
+                float2 z1s;
+                if (kHoist) {
+                    z1s = Z1S[hi];
+                } else {
+                    const float2 z1 = __fmul2_rn(M11, dx);
+                    z1s = __fmul2_rn(z1, z1);
+                }
+                const float2 q = __ffma2_rn(z2, z2, z1s);  // sigma log2(e) = |M d|^2
+                const float2 w = make_float2(ex2(-q.x), ex2(-q.y));  // exp(-sigma)
                 gcr = __ffma2_rn(gr, w, gcr);
                 gcg = __ffma2_rn(gg, w, gcg);
                 gcb = __ffma2_rn(gb, w, gcb);
@@ -94,15 +105,15 @@ __device__ __forceinline__ void pair_sums(const float* __restrict__ G, float4 r0
                 u = __fadd2_rn(u, e);
                 if (kHoist) {
                     v = __ffma2_rn(e, dx, v);
-                    q = __ffma2_rn(e, DX2[kHoist ? 2 * x4 + h : 0], q);
+                    qm = __ffma2_rn(e, DX2[hi], qm);
                 } else {
                     const float2 t1 = __fmul2_rn(e, dx);
                     v = __fadd2_rn(v, t1);
-                    q = __ffma2_rn(t1, dx, q);
+                    qm = __ffma2_rn(t1, dx, qm);
                 }
             }
         }
-        const float us = u.x + u.y, vs = v.x + v.y, qs = q.x + q.y;
+        const float us = u.x + u.y, vs = v.x + v.y, qs = qm.x + qm.y;
         kahan_add(S[0], cS[0], vs);
         kahan_add(S[1], cS[1], us * dy);
         kahan_add(S[2], cS[2], qs);
@@ -140,7 +151,7 @@ constexpr size_t backward_smem() { return stage_dl<T>() ? 8 * 2 * tile_floats<T>
 // spans more than two tiles (only tiles with fewer than 32 pairs do) repeats
 // this for the lanes left. Larger tiles read dL/dC from global memory.
 template <int T>
-__global__ void __launch_bounds__(256, T == 16 ? 2 : 3) k_backward(const float4* __restrict__ rec_binned,
+__global__ void __launch_bounds__(256, T <= 16 ? 2 : 3) k_backward(const float4* __restrict__ rec_binned,
                                                   const uint32_t* __restrict__ keys,
                                                   const uint32_t* __restrict__ ids, const int4* __restrict__ rect,
                                                   const int64_t* __restrict__ pair_off,

@@ -3,7 +3,10 @@
 // bounded decoupled look-back) and per-tile ranges.
 //
 // Formation follows Sec. 3.1, Eq. 1 (Sigma = L L^T) and Sec. 3.2, Eq. 5
-// (sigma = 1/2 d^T Sigma^-1 d). The paper does not define the screen support
+// (sigma = 1/2 d^T Sigma^-1 d). With Sigma^-1 = L^-T L^-1, sigma = 1/2 |L^-1 d|^2;
+// the record stores the scaled inverse factor so that the kernels evaluate
+// sigma as a sum of two squares, which stays accurate for needle-shaped
+// Gaussians where the expanded quadratic form cancels catastrophically. The paper does not define the screen support
 // of a Gaussian; the reading implemented here is the tile-granular 3-sigma
 // rectangle, evaluated with correctly rounded FP32 operations only (no fused
 // multiply-add), so that tile lists are bit-identical to the CPU oracle.
@@ -69,7 +72,7 @@ __global__ void __launch_bounds__(kProjBlock) k_project(ParamsIn P, Batch B, flo
         float4 r0 = make_float4(mx, my, 0.f, 0.f), r1 = make_float4(0.f, cr, cg, cb);
         bool ok = isfinite(mx) && isfinite(my) && isfinite(l1) && isfinite(l2) && isfinite(l3) &&
                   isfinite(cr) && isfinite(cg) && isfinite(cb);
-        float ca = 0.f, cbb = 0.f, cc = 0.f;
+        float ca = 0.f, cbb = 0.f, cc = 0.f, m11 = 0.f, m21 = 0.f, m22 = 0.f;
         if (ok) {
             const float s11 = __fmul_rn(l1, l1);
             const float s12 = __fmul_rn(l1, l2);
@@ -82,6 +85,14 @@ __global__ void __launch_bounds__(kProjBlock) k_project(ParamsIn P, Batch B, flo
                 cbb = __fdiv_rn(-s12, det);
                 cc = __fdiv_rn(s11, det);
                 ok = isfinite(det) && isfinite(ca) && isfinite(cbb) && isfinite(cc);
+            }
+            if (ok) {
+                // Scaled inverse Cholesky factor M = sqrt(log2(e)/2) L^-1, so that
+                // sigma log2(e) = |M d|^2 (a sum of squares: no cancellation).
+                m11 = __fdiv_rn(kSqrtHalfLog2e, l1);
+                m22 = __fdiv_rn(kSqrtHalfLog2e, l3);
+                m21 = -__fdiv_rn(__fmul_rn(l2, m11), l3);
+                ok = isfinite(m11) && isfinite(m21) && isfinite(m22);
             }
             if (ok) {
                 const float rx = __fmul_rn(3.0f, fabsf(l1));
@@ -104,10 +115,9 @@ __global__ void __launch_bounds__(kProjBlock) k_project(ParamsIn P, Batch B, flo
         }
         if (ok) {
             c = (r.z - r.x) * (r.w - r.y);
-            const float h = -0.5f * kLog2e;  // negated: exp(-sigma) = exp2(quadratic form)
-            r0.z = ca * h;
-            r0.w = cbb * -kLog2e;
-            r1.x = cc * h;
+            r0.z = m11;
+            r0.w = m21;
+            r1.x = m22;
         }
         rec[2 * (int64_t)g] = r0;
         rec[2 * (int64_t)g + 1] = r1;

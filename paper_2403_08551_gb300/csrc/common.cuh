@@ -1,11 +1,11 @@
 // common.cuh -- shared device/host helpers of libgi (sm_103a).
 //
 // Data layout (all device memory, caller-owned unless noted):
-//   rec[g]        8 x f32 = (mx, my, A', B', C', c'r, c'g, c'b); the conic
-//                 is pre-scaled and negated so that exp(-sigma) =
-//                 exp2(A'dx^2 + B'dx dy + C'dy^2), A' = -A log2(e)/2,
-//                 B' = -B log2(e), C' = -C log2(e)/2 with
-//                 Sigma^-1 = [[A, B], [B, C]].
+//   rec[g]        8 x f32 = (mx, my, m11, m21, m22, c'r, c'g, c'b) with
+//                 [[m11, 0], [m21, m22]] = sqrt(log2(e)/2) L^-1, i.e.
+//                 m11 = k/l1, m21 = -k l2/(l1 l3), m22 = k/l3, k = sqrt(log2(e)/2):
+//                 z1 = m11 dx, z2 = m21 dx + m22 dy and
+//                 exp(-sigma) = exp2(-(z1^2 + z2^2)) (sigma = 1/2 d^T Sigma^-1 d).
 //   rect[g]       int4 (tx0, ty0, tx1, ty1), image-local tile coordinates.
 //   cnt[g]        int32 number of tiles in rect (0 = culled).
 //   pair_off[g]   int64 exclusive prefix of cnt: index of g's first pair in
@@ -23,6 +23,7 @@
 namespace gi {
 
 constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kSqrtHalfLog2e = 0.84932180028801904272f;  // sqrt(log2(e) / 2)
 constexpr int kMaxCapacityLog2 = 30;  // pair indices fit the 30-bit look-back field
 constexpr int64_t kMaxCapacity = (int64_t(1) << kMaxCapacityLog2) - 1;
 

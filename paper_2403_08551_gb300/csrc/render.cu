@@ -12,8 +12,10 @@
 // the SPLIT partial images are then summed in shared memory in a fixed order.
 // Neighbouring pixels of a strip are evaluated as packed FP32 pairs
 // (fma.rn.f32x2), halving the issue slots of the FP32 work.
-// The result is deterministic run to run. exp(-sigma) is evaluated as
-// exp2 on the SFU (MUFU.EX2) with -log2(e) folded into the conic.
+// The result is deterministic run to run. sigma is evaluated as the sum of
+// squares |M d|^2 with M the scaled inverse Cholesky factor of the record
+// (sigma = 1/2 |L^-1 d|^2, Sec. 3.1 and Eq. 5), and exp(-sigma) as exp2 on
+// the SFU (MUFU.EX2).
 #include <algorithm>
 
 #include "kernels.cuh"
@@ -99,20 +101,22 @@ __global__ void __launch_bounds__(Cfg::kThreads) k_render(const float4* __restri
         if (ok) {
 #pragma unroll 1
             for (int k = k0; k < k1; ++k) {
-                const float4 r0 = srec[2 * k];      // mx, my, A', B' (negated, log2 units)
-                const float4 r1 = srec[2 * k + 1];  // C', c'r, c'g, c'b
+                const float4 r0 = srec[2 * k];      // mx, my, m11, m21 (scaled inverse Cholesky factor)
+                const float4 r1 = srec[2 * k + 1];  // m22, c'r, c'g, c'b
                 const float dy = py - r0.y;
-                const float bdy = r0.w * dy;
-                const float cdy2 = r1.x * dy * dy;
+                const float z2y = r1.x * dy;
                 const float dx0 = px0 - r0.x;
-                const float2 A2 = make_float2(r0.z, r0.z), B2 = make_float2(bdy, bdy), C2 = make_float2(cdy2, cdy2);
+                const float2 M11 = make_float2(r0.z, r0.z), M21 = make_float2(r0.w, r0.w);
+                const float2 Z2Y = make_float2(z2y, z2y);
                 const float2 cr = make_float2(r1.y, r1.y), cg = make_float2(r1.z, r1.z), cb = make_float2(r1.w, r1.w);
                 const float2 d0 = make_float2(dx0, dx0 + 1.0f);
 #pragma unroll
                 for (int p = 0; p < NP2; ++p) {
                     const float2 dx = __fadd2_rn(d0, make_float2(2.0f * p, 2.0f * p));
-                    const float2 s = __ffma2_rn(__ffma2_rn(A2, dx, B2), dx, C2);
-                    const float2 w = make_float2(ex2(s.x), ex2(s.y));  // exp(-sigma) of both pixels
+                    const float2 z1 = __fmul2_rn(M11, dx);
+                    const float2 z2 = __ffma2_rn(M21, dx, Z2Y);
+                    const float2 q = __ffma2_rn(z2, z2, __fmul2_rn(z1, z1));  // sigma log2(e)
+                    const float2 w = make_float2(ex2(-q.x), ex2(-q.y));  // exp(-sigma) of both pixels
                     accr[p] = __ffma2_rn(cr, w, accr[p]);
                     accg[p] = __ffma2_rn(cg, w, accg[p]);
                     accb[p] = __ffma2_rn(cb, w, accb[p]);
