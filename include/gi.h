@@ -232,7 +232,7 @@ typedef struct {
     int64_t capacity; /* pair capacity (>= 1), fixed for the context */
     int32_t use_graph; /* 1: capture the step once and replay it */
     int32_t stage_events; /* 1: record CUDA events between the five stages */
-    int32_t render_split; /* warp groups sharing one tile's list in the render: 0 = default;
+    int32_t render_split; /* lane groups sharing one tile's list in the render: 0 = default;
                              tile 8: 2 or 4, tile 16: 4 or 8, tile 32: 1 or 2 */
 } gi_fit_desc;
 

@@ -15,7 +15,7 @@ from . import _lib as L
 __all__ = ["project", "bin_tiles", "render", "render_backward", "vq_decode", "device_errors",
            "GIRender", "rasterize", "Fit", "Bins", "alu_peaks", "tiles", "autotune", "RENDER_SPLITS", "Renderer"]
 
-# Render splits (warp groups sharing one tile's list) available per tile edge.
+# Render splits (lane groups sharing one tile's list) available per tile edge.
 RENDER_SPLITS = {8: (2, 4), 16: (4, 8), 32: (1, 2)}
 
 

@@ -23,20 +23,24 @@
 namespace gi {
 namespace {
 
-template <int T_, int PX_, int SPLIT_>
+// A lane owns a strip of PX pixels in each of ROWS consecutive rows: the
+// x-dependent terms of sigma (dx, z1^2) are computed once per record and
+// shared by the rows. A group of kStrips lanes covers the whole tile; SPLIT
+// groups share the tile's list.
+template <int T_, int PX_, int SPLIT_, int ROWS_>
 struct RCfg {
-    static constexpr int T = T_, PX = PX_, SPLIT = SPLIT_;
+    static constexpr int T = T_, PX = PX_, SPLIT = SPLIT_, ROWS = ROWS_;
     static constexpr int kPix = T * T;
-    static constexpr int kStrips = kPix / PX;
+    static constexpr int kStrips = kPix / (PX * ROWS);
     static constexpr int kStripsPerRow = T / PX;
-    static constexpr int kWarpsPerGroup = kStrips / 32;
-    static constexpr int kWarps = kWarpsPerGroup * SPLIT;
-    static constexpr int kThreads = kWarps * 32;
+    static constexpr int kThreads = kStrips * SPLIT;
+    static constexpr int kWarps = kThreads / 32;
     static constexpr int kStage = 768;  // records per staging batch (24 KB)
     static constexpr int kStageBytes = kStage * 32;
     static constexpr int kPartBytes = SPLIT * 3 * kPix * 4;
     static constexpr int kSmem = kStageBytes > kPartBytes ? kStageBytes : kPartBytes;
-    static_assert(kStrips % 32 == 0, "strips must fill warps");
+    static_assert(kThreads % 32 == 0, "groups must fill warps");
+    static_assert(T % ROWS == 0 && T % PX == 0, "strips must tile the tile");
 };
 
 template <class Cfg>
@@ -62,19 +66,22 @@ __global__ void __launch_bounds__(Cfg::kThreads) k_render(const float4* __restri
     const int2 rg = ranges[t];
     const int L = rg.y - rg.x;
 
+    constexpr int ROWS = Cfg::ROWS;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int split = warp / Cfg::kWarpsPerGroup;
-    const int strip = (warp % Cfg::kWarpsPerGroup) * 32 + lane;
-    const int row = strip / Cfg::kStripsPerRow;
+    const int split = threadIdx.x / Cfg::kStrips;
+    const int strip = threadIdx.x % Cfg::kStrips;
+    const int row = (strip / Cfg::kStripsPerRow) * ROWS;
     const int col0 = (strip % Cfg::kStripsPerRow) * PX;
     const float py = (float)(y0 + row) + 0.5f;
     const float px0 = (float)(x0 + col0) + 0.5f;
 
-    // Packed FP32 pairs: acc[p] holds two neighbouring pixels of the strip.
+    // Packed FP32 pairs: acc[r][p] holds two neighbouring pixels of row r.
     constexpr int NP2 = PX / 2;
-    float2 accr[NP2], accg[NP2], accb[NP2];
+    float2 accr[ROWS][NP2], accg[ROWS][NP2], accb[ROWS][NP2];
 #pragma unroll
-    for (int p = 0; p < NP2; ++p) accr[p] = accg[p] = accb[p] = make_float2(0.f, 0.f);
+    for (int r = 0; r < ROWS; ++r)
+#pragma unroll
+        for (int p = 0; p < NP2; ++p) accr[r][p] = accg[r][p] = accb[r][p] = make_float2(0.f, 0.f);
 
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
@@ -104,22 +111,30 @@ __global__ void __launch_bounds__(Cfg::kThreads) k_render(const float4* __restri
                 const float4 r0 = srec[2 * k];      // mx, my, m11, m21 (scaled inverse Cholesky factor)
                 const float4 r1 = srec[2 * k + 1];  // m22, c'r, c'g, c'b
                 const float dy = py - r0.y;
-                const float z2y = r1.x * dy;
                 const float dx0 = px0 - r0.x;
                 const float2 M11 = make_float2(r0.z, r0.z), M21 = make_float2(r0.w, r0.w);
-                const float2 Z2Y = make_float2(z2y, z2y);
+                float2 Z2Y[ROWS];
+#pragma unroll
+                for (int r = 0; r < ROWS; ++r) {
+                    const float z2y = r1.x * (dy + (float)r);
+                    Z2Y[r] = make_float2(z2y, z2y);
+                }
                 const float2 cr = make_float2(r1.y, r1.y), cg = make_float2(r1.z, r1.z), cb = make_float2(r1.w, r1.w);
                 const float2 d0 = make_float2(dx0, dx0 + 1.0f);
 #pragma unroll
                 for (int p = 0; p < NP2; ++p) {
                     const float2 dx = __fadd2_rn(d0, make_float2(2.0f * p, 2.0f * p));
                     const float2 z1 = __fmul2_rn(M11, dx);
-                    const float2 z2 = __ffma2_rn(M21, dx, Z2Y);
-                    const float2 q = __ffma2_rn(z2, z2, __fmul2_rn(z1, z1));  // sigma log2(e)
-                    const float2 w = make_float2(ex2(-q.x), ex2(-q.y));  // exp(-sigma) of both pixels
-                    accr[p] = __ffma2_rn(cr, w, accr[p]);
-                    accg[p] = __ffma2_rn(cg, w, accg[p]);
-                    accb[p] = __ffma2_rn(cb, w, accb[p]);
+                    const float2 z1s = __fmul2_rn(z1, z1);
+#pragma unroll
+                    for (int r = 0; r < ROWS; ++r) {
+                        const float2 z2 = __ffma2_rn(M21, dx, Z2Y[r]);
+                        const float2 q = __ffma2_rn(z2, z2, z1s);            // sigma log2(e)
+                        const float2 w = make_float2(ex2(-q.x), ex2(-q.y));  // exp(-sigma) of both pixels
+                        accr[r][p] = __ffma2_rn(cr, w, accr[r][p]);
+                        accg[r][p] = __ffma2_rn(cg, w, accg[r][p]);
+                        accb[r][p] = __ffma2_rn(cb, w, accb[r][p]);
+                    }
                 }
             }
         }
@@ -128,14 +143,17 @@ __global__ void __launch_bounds__(Cfg::kThreads) k_render(const float4* __restri
 
     // Partial images of the SPLIT groups -> shared memory, [split][c][pixel].
 #pragma unroll
-    for (int q = 0; q < NP2; ++q) {
-        const int p = row * T + col0 + 2 * q;
-        spart[(split * 3 + 0) * NPIX + p] = accr[q].x;
-        spart[(split * 3 + 0) * NPIX + p + 1] = accr[q].y;
-        spart[(split * 3 + 1) * NPIX + p] = accg[q].x;
-        spart[(split * 3 + 1) * NPIX + p + 1] = accg[q].y;
-        spart[(split * 3 + 2) * NPIX + p] = accb[q].x;
-        spart[(split * 3 + 2) * NPIX + p + 1] = accb[q].y;
+    for (int r = 0; r < ROWS; ++r) {
+#pragma unroll
+        for (int q = 0; q < NP2; ++q) {
+            const int p = (row + r) * T + col0 + 2 * q;
+            spart[(split * 3 + 0) * NPIX + p] = accr[r][q].x;
+            spart[(split * 3 + 0) * NPIX + p + 1] = accr[r][q].y;
+            spart[(split * 3 + 1) * NPIX + p] = accg[r][q].x;
+            spart[(split * 3 + 1) * NPIX + p + 1] = accg[r][q].y;
+            spart[(split * 3 + 2) * NPIX + p] = accb[r][q].x;
+            spart[(split * 3 + 2) * NPIX + p + 1] = accb[r][q].y;
+        }
     }
     __syncthreads();
 
@@ -193,8 +211,15 @@ template <class Cfg>
 cudaError_t launch_cfg(const float4* rec_binned, const int2* ranges, const Batch& B, const float* target,
                        float* out, float* dl_hwc, float* dl_tiled, double* loss_sum, uint32_t* status,
                        cudaStream_t s) {
-    static_assert(Cfg::kSmem <= 48 * 1024, "dynamic shared memory above the default limit");
+    static_assert(Cfg::kSmem <= 96 * 1024, "dynamic shared memory of the render");
     if (B.total_tiles <= 0) return cudaSuccess;
+    static bool attr = false;  // the dynamic window plus the static part may exceed the default 48 KB
+    if (!attr) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(k_render<Cfg>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
     return launch_pdl(k_render<Cfg>, dim3(B.total_tiles), dim3(Cfg::kThreads), Cfg::kSmem, s, rec_binned, ranges, B,
                       target, out, dl_hwc, dl_tiled, loss_sum, status);
 }
@@ -204,33 +229,34 @@ cudaError_t launch_cfg(const float4* rec_binned, const int2* ranges, const Batch
 cudaError_t launch_render(const float4* rec_binned, const int2* ranges, const Batch& B, const float* target,
                           float* out, float* dl_hwc, float* dl_tiled, double* loss_sum, uint32_t* status,
                           cudaStream_t s) {
-    // split: warp groups that share one tile's list (each group covers all
-    // of the tile's pixels); 0 picks the default for the tile edge.
+    // split: lane groups that share one tile's list (each group covers all
+    // of the tile's pixels); 0 picks the default for the tile edge. Tile 16
+    // uses two rows per lane (16 lanes per group), tiles 8 and 32 one.
     const int sp = B.split;
     switch (B.tile) {
         case 8:
             if (sp == 2)
-                return launch_cfg<RCfg<8, 2, 2>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
-                                                 status, s);
+                return launch_cfg<RCfg<8, 2, 2, 1>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
+                                                    status, s);
             if (sp == 0 || sp == 4)
-                return launch_cfg<RCfg<8, 2, 4>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
-                                                 status, s);
+                return launch_cfg<RCfg<8, 2, 4, 1>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
+                                                    status, s);
             return cudaErrorInvalidValue;
         case 16:
             if (sp == 4)
-                return launch_cfg<RCfg<16, 8, 4>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
-                                                  status, s);
+                return launch_cfg<RCfg<16, 8, 4, 2>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
+                                                     status, s);
             if (sp == 0 || sp == 8)
-                return launch_cfg<RCfg<16, 8, 8>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
-                                                  status, s);
+                return launch_cfg<RCfg<16, 8, 8, 2>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
+                                                     status, s);
             return cudaErrorInvalidValue;
         case 32:
             if (sp == 1)
-                return launch_cfg<RCfg<32, 8, 1>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
-                                                  status, s);
+                return launch_cfg<RCfg<32, 8, 1, 1>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
+                                                     status, s);
             if (sp == 0 || sp == 2)
-                return launch_cfg<RCfg<32, 8, 2>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
-                                                  status, s);
+                return launch_cfg<RCfg<32, 8, 2, 1>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
+                                                     status, s);
             return cudaErrorInvalidValue;
         default:
             return cudaErrorInvalidValue;
