@@ -38,8 +38,10 @@ import synth  # noqa: E402
 METRIC = "fit iter/s + render FPS (768×512, 70k Gaussians); batched vs plain at equal PSNR"
 WORKLOAD = "c1_768x512_70k"
 LR = (1e-3, 1e-2, 1e-2)
-FWD_FLOP_PER_EVAL = 11   # 1 FADD + 2 FFMA (quadratic form) + 3 FFMA (accumulate); exp on the SFU
-BWD_FLOP_PER_EVAL = 22   # 1 FADD + 2 FFMA + 3 FFMA + FMUL + 2 FFMA + FMUL + FADD + FMUL + FADD + FFMA
+# sigma = 1/2 |L^-1 d|^2: dx (FADD), z1 = m11 dx (FMUL), z2 = m21 dx + m22 dy (FFMA),
+# z1^2 (FMUL), z1^2 + z2^2 (FFMA) = 7 flop; exp on the SFU.
+FWD_FLOP_PER_EVAL = 13   # sigma 7 + 3 FFMA (accumulate)
+BWD_FLOP_PER_EVAL = 24   # sigma 7 + 3 FFMA (dL/dc') + FMUL + 2 FFMA (<G, c'>) + FMUL (e) + FADD + FMUL + FADD + FFMA (moments)
 # DRAM bytes (read + write) per launch of the ALU-bound kernels at this
 # workload, from one ncu --set full capture of the current kernels
 # (profiles/k_backward_c1_768x512_70k.md, profiles/k_render_c1_768x512_70k.md).
