@@ -241,7 +241,9 @@ typedef struct {
 GI_API gi_status gi_fit_create(const gi_fit_desc* desc, gi_stream stream, gi_fit** out);
 /* Runs `steps` fit steps (graph replays when use_graph). Asynchronous. */
 GI_API gi_status gi_fit_step(gi_fit* fit, int32_t steps, gi_stream stream);
-/* Renders the current parameters into the context's output buffer. */
+/* Renders the current parameters into the context's output buffer
+ * (formation, binning, Eq. 7; no loss, no dL/dC; GI_FIT_LOSS keeps the last
+ * step's value). Replays a captured graph when use_graph. Asynchronous. */
 GI_API gi_status gi_fit_render(gi_fit* fit, gi_stream stream);
 
 /* Device pointers into the context (valid until gi_fit_destroy):

@@ -220,14 +220,23 @@ class Fit:
         dev = targets[0].device
         tgt = torch.cat([_dev(t, torch.float32, "target").reshape(-1) for t in targets])
         prm = torch.cat([_dev(p, torch.float32, "params").reshape(-1, 8) for p in params]).contiguous()
-        if capacity is None:
+        K = None
+        if capacity is None or (render_split == 0 and tile == 16):
             K = 0
             for (W, H), p in zip(self.shapes, params):
                 p = p.contiguous()
                 rec, rect, cnt = project(p[:, 0:2].contiguous(), p[:, 2:5].contiguous(), p[:, 5:8].contiguous(),
                                          W, H, tile)
                 K += bin_tiles(rect, cnt, None, W, H, tile).K
+        if capacity is None:
             capacity = max(4096, int(K * capacity_factor) + 1024)
+        if render_split == 0 and tile == 16:
+            # Short tile lists are rendered faster by fewer lane groups per tile
+            # (measured on GB300: 97 pairs per tile, split 4 is 1.2x faster than
+            # 8; 234 pairs per tile, split 8 is 1.06x faster than 4).
+            n_tiles = sum(tiles(W, H, tile)[0] * tiles(W, H, tile)[1] for W, H in self.shapes)
+            render_split = 8 if K >= 160 * n_tiles else 4
+        self.render_split = int(render_split)
         self.capacity = int(capacity)
         n_img = len(targets)
         self._w = (ctypes.c_int32 * n_img)(*[s[0] for s in self.shapes])

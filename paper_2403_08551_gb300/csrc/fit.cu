@@ -25,6 +25,8 @@ struct gi_fit {
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
+    cudaGraph_t render_graph = nullptr;  // forward only (no loss), for gi_fit_render
+    cudaGraphExec_t render_exec = nullptr;
     void* arena = nullptr;
     // carved from arena
     ImgDesc* d_desc = nullptr;
@@ -57,32 +59,36 @@ cudaError_t mark(gi_fit* f, int i, cudaStream_t s) {
                                                : cudaEventRecord(f->ev[i], s);
 }
 
-cudaError_t enqueue_forward(gi_fit* f, cudaStream_t s) {
+// Formation, binning and render. train: also the loss and the planar dL/dC
+// for the backward, with stage events; otherwise the image only.
+cudaError_t enqueue_forward(gi_fit* f, cudaStream_t s, bool train) {
     ZeroJob zj{};
     zj.p[0] = f->bws.zero;
     zj.n32[0] = f->bws.zero_words;
     zj.p[1] = reinterpret_cast<uint32_t*>(f->ranges);
     zj.n32[1] = (int64_t)f->B.total_tiles * 2;
-    zj.p[2] = reinterpret_cast<uint32_t*>(f->loss);
-    zj.n32[2] = (int64_t)f->nimg * 2;
-    cudaError_t e = mark(f, 0, s);
+    if (train) {  // the render-only pass leaves the last step's loss in place
+        zj.p[2] = reinterpret_cast<uint32_t*>(f->loss);
+        zj.n32[2] = (int64_t)f->nimg * 2;
+    }
+    cudaError_t e = train ? mark(f, 0, s) : cudaSuccess;
     if (e == cudaSuccess)
         e = launch_project(params_aos(f->params), f->B, f->rec, f->rect, f->cnt, f->bws.blk_sum, zj, s, f->bws.cm,
                            f->bws.chunk_sum);
-    if (e == cudaSuccess) e = mark(f, 1, s);
+    if (e == cudaSuccess && train) e = mark(f, 1, s);
     if (e == cudaSuccess)
         e = launch_bin(f->rect, f->cnt, f->rec, f->B, f->capacity, f->bws, true, f->keys, f->ids, f->ranges,
                        f->rec_binned, f->pair_off, f->k_dev, f->k_max, device_status(), s);
-    if (e == cudaSuccess) e = mark(f, 2, s);
+    if (e == cudaSuccess && train) e = mark(f, 2, s);
     if (e == cudaSuccess)
-        e = launch_render(f->rec_binned, f->ranges, f->B, f->targets, f->out, nullptr, f->dl_tiled, f->loss,
-                          device_status(), s);
-    if (e == cudaSuccess) e = mark(f, 3, s);
+        e = launch_render(f->rec_binned, f->ranges, f->B, train ? f->targets : nullptr, f->out, nullptr,
+                          train ? f->dl_tiled : nullptr, train ? f->loss : nullptr, device_status(), s);
+    if (e == cudaSuccess && train) e = mark(f, 3, s);
     return e;
 }
 
 cudaError_t enqueue_step(gi_fit* f, cudaStream_t s) {
-    cudaError_t e = enqueue_forward(f, s);
+    cudaError_t e = enqueue_forward(f, s, true);
     if (e != cudaSuccess) return e;
     e = launch_backward(f->rec_binned, f->keys, f->ids, f->rect, f->pair_off, f->dl_tiled, f->B, f->k_dev,
                         f->capacity, f->partial, s);
@@ -98,6 +104,8 @@ void release(gi_fit* f) {
     if (!f) return;
     if (f->exec) cudaGraphExecDestroy(f->exec);
     if (f->graph) cudaGraphDestroy(f->graph);
+    if (f->render_exec) cudaGraphExecDestroy(f->render_exec);
+    if (f->render_graph) cudaGraphDestroy(f->render_graph);
     if (f->cap_stream) cudaStreamDestroy(f->cap_stream);
     for (cudaEvent_t e : f->ev)
         if (e) cudaEventDestroy(e);
@@ -252,6 +260,14 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
         FIT_TRY(ce);
         FIT_TRY(ee);
         FIT_TRY(cudaGraphInstantiate(&f->exec, f->graph, 0));
+        FIT_TRY(cudaStreamBeginCapture(f->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t re = enqueue_forward(f, f->cap_stream, false);
+        cudaGraph_t rg = nullptr;
+        cudaError_t rende = cudaStreamEndCapture(f->cap_stream, &rg);
+        f->render_graph = rg;
+        FIT_TRY(re);
+        FIT_TRY(rende);
+        FIT_TRY(cudaGraphInstantiate(&f->render_exec, f->render_graph, 0));
     }
 #undef FIT_TRY
     *out = f;
@@ -270,7 +286,8 @@ gi_status gi_fit_step(gi_fit* f, int32_t steps, gi_stream stream) {
 
 gi_status gi_fit_render(gi_fit* f, gi_stream stream) {
     if (!f) return set_error(GI_ERR_INVALID_ARG, "gi_fit_render: NULL fit");
-    cudaError_t e = enqueue_forward(f, reinterpret_cast<cudaStream_t>(stream));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaError_t e = f->render_exec ? cudaGraphLaunch(f->render_exec, s) : enqueue_forward(f, s, false);
     if (e != cudaSuccess) return set_cuda_error(e, "gi_fit_render");
     return GI_OK;
 }

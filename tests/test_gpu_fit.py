@@ -155,6 +155,32 @@ def test_graph_replay_equals_eager(gi):
     b.close()
 
 
+def test_fit_render_is_the_forward_only(gi):
+    """gi_fit_render: the image of the current parameters (same as the
+    per-stage calls with the same render split), graph replay identical to
+    the eager launches, and the last step's loss left in place."""
+    W, H, T, n = 160, 120, 16, 1500
+    target = torch.from_numpy(synth.image(W, H, 23, n_blobs=20)).cuda()
+    p = torch.from_numpy(pack(*synth.init_gaussians(n, W, H, 23))).cuda()
+    a = gi.Fit([target], [p], tile=T, lr=LR, use_graph=True, render_split=8)
+    b = gi.Fit([target], [p], tile=T, lr=LR, use_graph=False, render_split=8)
+    a.step(3)
+    b.step(3)
+    torch.cuda.synchronize()
+    mse = a.mse()[0]
+    a.render()
+    b.render()
+    torch.cuda.synchronize()
+    assert a.mse()[0] == mse
+    assert torch.equal(a.images()[0], b.images()[0])
+    q = a.params
+    ref = gi.rasterize(q[:, 0:2].contiguous(), q[:, 2:5].contiguous(), q[:, 5:8].contiguous(), W, H, T)
+    torch.cuda.synchronize()
+    assert torch.equal(a.images()[0], ref)
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("T,split", [(8, 2), (8, 4), (16, 4), (16, 8), (32, 1), (32, 2)])
 def test_batched_equals_single(gi, T, split):
     """Images fitted together in one launch per stage give bit-identical
