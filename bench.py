@@ -262,11 +262,12 @@ def batched_vs_plain(gi, torch, n_images, steps, stream):
             "mean_psnr_db_plain": sum(psnr(b) for b in mse_p) / len(mse_p)}
 
 
-def long_fit(gi, torch, stream, T, steps):
+def long_fit(gi, torch, stream, T, steps, log_path=None, every=5000):
     """The full-length fit of the 768x512, 70k-Gaussian workload: `steps`
-    graph-replayed steps back to back (no L2 flush: steady state), timed as
-    one window with CUDA events; PSNR of the first and of the last step's
-    render. The pair capacity leaves room for the Gaussians to grow."""
+    graph-replayed steps (no L2 flush: steady state) in chunks of `every`,
+    each timed with CUDA events; PSNR of the first step's render and after
+    every chunk (also written as JSON lines to log_path). The pair capacity
+    leaves room for the Gaussians to grow."""
     w = synth.workload(WORKLOAD)
     fit = gi.Fit([torch.from_numpy(w.target).cuda()], [torch.from_numpy(pack(w)).cuda()], tile=T, lr=LR,
                  capacity_factor=4.0)
@@ -275,14 +276,25 @@ def long_fit(gi, torch, stream, T, steps):
     psnr = lambda e: 10 * math.log10(1.0 / e) if e > 0 else float("inf")  # noqa: E731
     p1 = psnr(fit.mse()[0])
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    fit.step(steps - 1)
-    e1.record(stream)
-    e1.synchronize()
-    t = e0.elapsed_time(e1) / 1e3
+    done, t, traj = 1, 0.0, [[1, p1]]
+    log = open(log_path, "w") if log_path else None
+    while done < steps:
+        n = min(every - (done % every), steps - done)
+        e0.record(stream)
+        fit.step(n)
+        e1.record(stream)
+        e1.synchronize()
+        t += e0.elapsed_time(e1) / 1e3
+        done += n
+        traj.append([done, psnr(fit.mse()[0])])
+        if log:
+            log.write(json.dumps({"step": done, "psnr_db": traj[-1][1], "pairs": int(fit.k.item()),
+                                  "seconds": t}) + "\n")
+    if log:
+        log.close()
     err = gi.device_errors(clear=True)
     out = {"steps": steps, "iter_s": (steps - 1) / t, "seconds": t, "psnr_db_step1": p1,
-           "psnr_db_final": psnr(fit.mse()[0]), "pairs_final": int(fit.k.item()),
+           "psnr_db_final": traj[-1][1], "psnr_db_trajectory": traj, "pairs_final": int(fit.k.item()),
            "l2": "not flushed between steps (steady state)", "device_errors": int(err)}
     fit.close()
     return out
@@ -518,7 +530,8 @@ def main():
         out["large_image"] = large_image(gi, torch, stream, flush)
         out["codec"] = codec_decode(gi, torch, stream, flush)
     if args.long_steps > 1 and not args.no_extra and rank == 0:
-        out["fit_long"] = long_fit(gi, torch, stream, T, args.long_steps)
+        out["fit_long"] = long_fit(gi, torch, stream, T, args.long_steps,
+                                   os.path.join(args.out, "fit_long_psnr.jsonl"))
     if not args.no_cpu and rank == 0:
         out["cpu_baseline"] = cpu_baseline(w, T)
         out["cpu_baseline"]["oracle_c0"] = oracle_c0_times()

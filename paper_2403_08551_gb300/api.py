@@ -292,6 +292,26 @@ class Fit:
         s = self.loss_sum.cpu().tolist()
         return [v / (3.0 * W * H) for v, (W, H) in zip(s, self.shapes)]
 
+    def state_dict(self) -> dict:
+        """Checkpoint of the fit: parameters, Adam moments and the completed
+        step count (copies on the context's device). The pipeline has no
+        random state; everything else is recomputed every step."""
+        torch.cuda.current_stream().synchronize()
+        return {"params": self.params.clone(), "adam_m": self.adam_m.clone(), "adam_v": self.adam_v.clone(),
+                "step": int(self.step_count.item()), "shapes": list(self.shapes), "counts": list(self.counts),
+                "tile": self.tile}
+
+    def load_state_dict(self, sd: dict):
+        """Restores a checkpoint of a fit with the same images, Gaussian
+        counts and tile edge; the next steps continue bit-identically."""
+        if list(sd["shapes"]) != list(self.shapes) or list(sd["counts"]) != list(self.counts) or \
+                sd["tile"] != self.tile:
+            raise ValueError("checkpoint of a different fit (images, Gaussian counts or tile edge)")
+        self.params.copy_(sd["params"])
+        self.adam_m.copy_(sd["adam_m"])
+        self.adam_v.copy_(sd["adam_v"])
+        self.step_count.fill_(int(sd["step"]))
+
     def close(self):
         if getattr(self, "_h_fit", None) is not None:
             L.load().gi_fit_destroy(self._h_fit)

@@ -108,6 +108,7 @@ gi_status gi_device_errors(uint32_t* bits, int32_t clear, gi_stream stream) {
 
 gi_status gi_project(const float* means, const float* chol, const float* color, int32_t n, gi_image img,
                      float* rec, int32_t* rect, int32_t* cnt, gi_stream stream) {
+    NvtxRange nvtx_("gi_project");
     gi_status st = check_image(img, "gi_project");
     if (st != GI_OK) return st;
     GI_REQUIRE(n >= 0, "gi_project: n < 0");
@@ -140,6 +141,7 @@ gi_status gi_bin_tiles(const int32_t* rect, const int32_t* cnt, const float* rec
                        int64_t capacity, void* ws, size_t ws_bytes, uint32_t* keys, uint32_t* ids,
                        int32_t* ranges, float* rec_binned, int64_t* pair_off, int64_t* k_dev,
                        gi_stream stream) {
+    NvtxRange nvtx_("gi_bin_tiles");
     gi_status st = check_image(img, "gi_bin_tiles");
     if (st != GI_OK) return st;
     GI_REQUIRE(n >= 0, "gi_bin_tiles: n < 0");
@@ -166,6 +168,7 @@ gi_status gi_bin_tiles(const int32_t* rect, const int32_t* cnt, const float* rec
 
 gi_status gi_render(const float* rec_binned, const int32_t* ranges, gi_image img, const float* target, float* out,
                     float* dl_dout, double* loss_sum, gi_stream stream) {
+    NvtxRange nvtx_("gi_render");
     gi_status st = check_image(img, "gi_render");
     if (st != GI_OK) return st;
     GI_REQUIRE(rec_binned && ranges && out, "gi_render: NULL pointer");
@@ -199,6 +202,7 @@ gi_status gi_render_backward(const float* rec_binned, const uint32_t* keys, cons
                              const int64_t* pair_off, const int64_t* k_dev, const float* chol, int32_t n,
                              gi_image img, int64_t capacity, const float* dl_dout, void* ws, size_t ws_bytes,
                              float* g_means, float* g_chol, float* g_color, float* g_conic, gi_stream stream) {
+    NvtxRange nvtx_("gi_render_backward");
     gi_status st = check_image(img, "gi_render_backward");
     if (st != GI_OK) return st;
     GI_REQUIRE(n >= 0, "gi_render_backward: n < 0");
@@ -231,6 +235,7 @@ gi_status gi_render_backward(const float* rec_binned, const uint32_t* keys, cons
 
 gi_status gi_vq_decode(const uint16_t* means16, const uint8_t* idx, const float* codebooks, int32_t n,
                        int32_t stages, int32_t cb_size, float* means, float* chol, float* color, gi_stream stream) {
+    NvtxRange nvtx_("gi_vq_decode");
     GI_REQUIRE(n >= 0, "gi_vq_decode: n < 0");
     GI_REQUIRE(stages >= 1 && stages <= 8 && cb_size >= 1 && cb_size <= 256,
                "gi_vq_decode: stages must be 1..8 and cb_size 1..256");

@@ -16,6 +16,7 @@
 //   ranges[t]     int2 [begin, end) of global tile t in the sorted pairs.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "../../include/gi.h"
@@ -168,6 +169,16 @@ __device__ __forceinline__ void flag_error(uint32_t* status, uint32_t bits) {
 // wait, so a kernel launched with launch_pdl may be scheduled while its
 // predecessor drains, and still sees all of the predecessor's results (and
 // no predecessor still reads what it overwrites). A no-op for plain launches.
+// Host-side NVTX range for the lifetime of the object (shows each call and
+// each stage of a fit step on a profiler timeline; free when no tool is
+// attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 // Look-back words: 2 flag bits (aggregate / inclusive prefix) over a 30-bit
 // value; spins on an unpublished word are bounded by kSpinLimit.
 constexpr uint32_t kFlagAgg = 1u << 30;

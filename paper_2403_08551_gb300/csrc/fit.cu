@@ -72,17 +72,23 @@ cudaError_t enqueue_forward(gi_fit* f, cudaStream_t s, bool train) {
         zj.n32[2] = (int64_t)f->nimg * 2;
     }
     cudaError_t e = train ? mark(f, 0, s) : cudaSuccess;
-    if (e == cudaSuccess)
+    if (e == cudaSuccess) {
+        NvtxRange r("gi:formation");
         e = launch_project(params_aos(f->params), f->B, f->rec, f->rect, f->cnt, f->bws.blk_sum, zj, s, f->bws.cm,
                            f->bws.chunk_sum);
+    }
     if (e == cudaSuccess && train) e = mark(f, 1, s);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess) {
+        NvtxRange r("gi:binning");
         e = launch_bin(f->rect, f->cnt, f->rec, f->B, f->capacity, f->bws, true, f->keys, f->ids, f->ranges,
                        f->rec_binned, f->pair_off, f->k_dev, f->k_max, device_status(), s);
+    }
     if (e == cudaSuccess && train) e = mark(f, 2, s);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess) {
+        NvtxRange r("gi:render");
         e = launch_render(f->rec_binned, f->ranges, f->B, train ? f->targets : nullptr, f->out, nullptr,
                           train ? f->dl_tiled : nullptr, train ? f->loss : nullptr, device_status(), s);
+    }
     if (e == cudaSuccess && train) e = mark(f, 3, s);
     return e;
 }
@@ -90,12 +96,17 @@ cudaError_t enqueue_forward(gi_fit* f, cudaStream_t s, bool train) {
 cudaError_t enqueue_step(gi_fit* f, cudaStream_t s) {
     cudaError_t e = enqueue_forward(f, s, true);
     if (e != cudaSuccess) return e;
-    e = launch_backward(f->rec_binned, f->keys, f->ids, f->rect, f->pair_off, f->dl_tiled, f->B, f->k_dev,
-                        f->capacity, f->partial, s);
+    {
+        NvtxRange r("gi:backward");
+        e = launch_backward(f->rec_binned, f->keys, f->ids, f->rect, f->pair_off, f->dl_tiled, f->B, f->k_dev,
+                            f->capacity, f->partial, s);
+    }
     if (e == cudaSuccess) e = mark(f, 4, s);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess) {
+        NvtxRange r("gi:update");
         e = launch_reduce(f->partial, f->pair_off, f->cnt, f->capacity, (int32_t)f->N, params_aos(f->params),
                           nullptr, nullptr, nullptr, nullptr, &f->adam, f->params, f->m, f->v, f->grads, s);
+    }
     if (e == cudaSuccess) e = mark(f, 5, s);
     return e;
 }
@@ -118,6 +129,7 @@ void release(gi_fit* f) {
 extern "C" {
 
 gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
+    NvtxRange nvtx_("gi_fit_create");
     if (!d || !out) return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: NULL argument");
     *out = nullptr;
     if (d->n_images < 1 || !d->widths || !d->heights || !d->counts || !d->targets || !d->params)
@@ -275,6 +287,7 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
 }
 
 gi_status gi_fit_step(gi_fit* f, int32_t steps, gi_stream stream) {
+    NvtxRange nvtx_("gi_fit_step");
     if (!f || steps < 0) return set_error(GI_ERR_INVALID_ARG, "gi_fit_step: bad argument");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     for (int i = 0; i < steps; ++i) {
@@ -285,6 +298,7 @@ gi_status gi_fit_step(gi_fit* f, int32_t steps, gi_stream stream) {
 }
 
 gi_status gi_fit_render(gi_fit* f, gi_stream stream) {
+    NvtxRange nvtx_("gi_fit_render");
     if (!f) return set_error(GI_ERR_INVALID_ARG, "gi_fit_render: NULL fit");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     cudaError_t e = f->render_exec ? cudaGraphLaunch(f->render_exec, s) : enqueue_forward(f, s, false);

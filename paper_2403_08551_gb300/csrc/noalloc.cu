@@ -66,6 +66,7 @@ extern "C" gi_status gi_bin_tiles_noalloc(const int32_t* rect, const int32_t* cn
                                           gi_image img, int64_t capacity, uint32_t* keys, uint32_t* ids,
                                           int32_t* ranges, float* rec_binned, int64_t* pair_off, int64_t* k_dev,
                                           gi_stream stream) {
+    NvtxRange nvtx_("gi_bin_tiles_noalloc");
     if (img.width <= 0 || img.height <= 0 || (img.tile != 8 && img.tile != 16 && img.tile != 32))
         return set_error(GI_ERR_INVALID_ARG, "gi_bin_tiles_noalloc: bad image %dx%d tile %d", img.width,
                          img.height, img.tile);

@@ -155,6 +155,35 @@ def test_graph_replay_equals_eager(gi):
     b.close()
 
 
+def test_checkpoint_resume_is_bit_identical(gi, tmp_path):
+    """A fit saved after 4 steps (torch.save of state_dict) and restored into
+    a fresh context continues exactly like the uninterrupted fit."""
+    W, H, T, n = 160, 120, 16, 1500
+    target = torch.from_numpy(synth.image(W, H, 24, n_blobs=20)).cuda()
+    p = torch.from_numpy(pack(*synth.init_gaussians(n, W, H, 24))).cuda()
+    a = gi.Fit([target], [p], tile=T, lr=LR)
+    a.step(4)
+    path = tmp_path / "fit.pt"
+    torch.save(a.state_dict(), path)
+    a.step(3)
+    b = gi.Fit([target], [p], tile=T, lr=LR)
+    b.load_state_dict(torch.load(path))
+    b.step(3)
+    torch.cuda.synchronize()
+    assert torch.equal(a.params, b.params)
+    assert torch.equal(a.adam_m, b.adam_m) and torch.equal(a.adam_v, b.adam_v)
+    assert int(a.step_count.item()) == int(b.step_count.item()) == 7
+    assert a.mse() == b.mse()
+    with pytest.raises(ValueError):
+        c = gi.Fit([target], [p[:100]], tile=T, lr=LR)
+        try:
+            c.load_state_dict(torch.load(path))
+        finally:
+            c.close()
+    a.close()
+    b.close()
+
+
 def test_fit_render_is_the_forward_only(gi):
     """gi_fit_render: the image of the current parameters (same as the
     per-stage calls with the same render split), graph replay identical to
