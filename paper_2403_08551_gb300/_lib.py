@@ -12,7 +12,9 @@ import os
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libgi.so")
+# GI_LIB_VARIANT=check loads the bounds-checking build (see build.py).
+LIB_PATH = os.path.join(HERE, "_build_check" if os.environ.get("GI_LIB_VARIANT") == "check" else "_build",
+                        "libgi.so")
 
 P = ctypes.c_void_p
 i32, i64, f32, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double

@@ -46,10 +46,23 @@ def _stale(target: str, deps) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
+# Variants: "release" (the product, _build/libgi.so) and "check"
+# (_build_check/libgi.so, compiled with -DGI_CHECK_BOUNDS: extra index
+# checks in the kernels that raise the bounds error bit and skip the access).
+VARIANTS = {"release": (OUT, []), "check": (os.path.join(HERE, "_build_check"), ["-DGI_CHECK_BOUNDS"])}
+
+
+def library_path(variant: str = "release") -> str:
+    return os.path.join(VARIANTS[variant][0], "libgi.so")
+
+
+def build(force: bool = False, verbose: bool = False, extra_flags=None, variant: str = "release") -> str:
+    out_dir, vflags = VARIANTS[variant]
+    LIB = os.path.join(out_dir, "libgi.so")
+    OUT = out_dir
     os.makedirs(OUT, exist_ok=True)
     nvcc = _nvcc()
-    flags = NVCC_FLAGS + list(extra_flags or [])
+    flags = NVCC_FLAGS + vflags + list(extra_flags or [])
     srcs = sources()
     headers = _deps()
     objs = []
@@ -85,4 +98,4 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, variant="check" if "--check" in sys.argv else "release"))

@@ -225,7 +225,7 @@ gi_status gi_render_backward(const float* rec_binned, const uint32_t* keys, cons
     cudaError_t e = launch_pack_dl(dl_dout, B, dl_tiled, s);
     if (e == cudaSuccess)
         e = launch_backward(reinterpret_cast<const float4*>(rec_binned), keys, ids, reinterpret_cast<const int4*>(rect),
-                            pair_off, dl_tiled, B, k_dev, capacity, partial, s);
+                            pair_off, dl_tiled, B, k_dev, capacity, partial, device_status(), s);
     if (e == cudaSuccess)
         e = launch_reduce(partial, pair_off, cnt, capacity, n, params_soa(nullptr, chol, nullptr), g_means, g_chol,
                           g_color, g_conic, nullptr, nullptr, nullptr, nullptr, nullptr, s);

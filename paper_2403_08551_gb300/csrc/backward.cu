@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(256, T <= 16 ? 2 : 3) k_backward(const float4*
                                                   const int64_t* __restrict__ pair_off,
                                                   const float* __restrict__ dl_tiled, Batch B,
                                                   const int64_t* __restrict__ k_dev, int64_t capacity,
-                                                  float4* __restrict__ partial) {
+                                                  float4* __restrict__ partial, uint32_t* __restrict__ status) {
     constexpr int TF = tile_floats<T>();
     extern __shared__ float4 s_dl[];
     pdl_wait();
@@ -168,7 +168,9 @@ __global__ void __launch_bounds__(256, T <= 16 ? 2 : 3) k_backward(const float4*
     for (int task = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; task * 32 < K; task += nwarps) {
         const int k = min(task * 32 + lane, K - 1);
         const float4 r0 = rec_binned[2 * (size_t)k], r1 = rec_binned[2 * (size_t)k + 1];
-        const uint32_t t = keys[k], g = ids[k];
+        uint32_t t = keys[k], g = ids[k];
+        const bool inb = gi_in_bounds(t < (uint32_t)B.total_tiles && g < (uint32_t)B.total_gauss, status);
+        if (!inb) t = g = 0;  // bounds-checking build: the pair is skipped
         const int4 r = rect[g];
         const int64_t po = pair_off[g];
         int tx, ty;
@@ -202,7 +204,7 @@ __global__ void __launch_bounds__(256, T <= 16 ? 2 : 3) k_backward(const float4*
             pair_sums<T>(dl_tiled + (size_t)t * TF, r0, r1, dx0, dyb, o);
             have = true;
         }
-        if (have) {
+        if (have && inb) {
             const int64_t p = po + (int64_t)(ty - r.y) * (r.z - r.x) + (tx - r.x);
             if (p >= 0 && p < capacity) {
                 partial[2 * p] = make_float4(o[0], o[1], o[2], o[3]);
@@ -388,7 +390,7 @@ int sm_count_b() {
 
 cudaError_t launch_backward(const float4* rec_binned, const uint32_t* keys, const uint32_t* ids, const int4* rect,
                             const int64_t* pair_off, const float* dl_tiled, const Batch& B, const int64_t* k_dev,
-                            int64_t capacity, float4* partial, cudaStream_t s) {
+                            int64_t capacity, float4* partial, uint32_t* status, cudaStream_t s) {
     if (capacity <= 0) return cudaSuccess;
     static int nsm = 0;
     if (!nsm) nsm = sm_count_b();
@@ -407,13 +409,13 @@ cudaError_t launch_backward(const float4* rec_binned, const uint32_t* keys, cons
     switch (B.tile) {
         case 8:
             return launch_pdl(k_backward<8>, dim3(blocks), dim3(256), backward_smem<8>(), s, rec_binned, keys, ids,
-                              rect, pair_off, dl_tiled, B, k_dev, capacity, partial);
+                              rect, pair_off, dl_tiled, B, k_dev, capacity, partial, status);
         case 16:
             return launch_pdl(k_backward<16>, dim3(blocks), dim3(256), backward_smem<16>(), s, rec_binned, keys, ids,
-                              rect, pair_off, dl_tiled, B, k_dev, capacity, partial);
+                              rect, pair_off, dl_tiled, B, k_dev, capacity, partial, status);
         case 32:
             return launch_pdl(k_backward<32>, dim3(blocks), dim3(256), 0, s, rec_binned, keys, ids, rect, pair_off,
-                              dl_tiled, B, k_dev, capacity, partial);
+                              dl_tiled, B, k_dev, capacity, partial, status);
         default:
             return cudaErrorInvalidValue;
     }

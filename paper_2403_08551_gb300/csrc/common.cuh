@@ -169,6 +169,20 @@ __device__ __forceinline__ void flag_error(uint32_t* status, uint32_t bits) {
 // wait, so a kernel launched with launch_pdl may be scheduled while its
 // predecessor drains, and still sees all of the predecessor's results (and
 // no predecessor still reads what it overwrites). A no-op for plain launches.
+// Extra index checks of the bounds-checking build (-DGI_CHECK_BOUNDS):
+// gi_in_bounds(cond, status) raises kErrBounds and returns false when cond
+// fails; in the release build it is constant true and compiles away.
+__device__ __forceinline__ bool gi_in_bounds(bool cond, uint32_t* status) {
+#ifdef GI_CHECK_BOUNDS
+    if (!cond) flag_error(status, kErrBounds);
+    return cond;
+#else
+    (void)status;
+    (void)cond;
+    return true;
+#endif
+}
+
 // Host-side NVTX range for the lifetime of the object (shows each call and
 // each stage of a fit step on a profiler timeline; free when no tool is
 // attached).

@@ -99,7 +99,7 @@ cudaError_t enqueue_step(gi_fit* f, cudaStream_t s) {
     {
         NvtxRange r("gi:backward");
         e = launch_backward(f->rec_binned, f->keys, f->ids, f->rect, f->pair_off, f->dl_tiled, f->B, f->k_dev,
-                            f->capacity, f->partial, s);
+                            f->capacity, f->partial, device_status(), s);
     }
     if (e == cudaSuccess) e = mark(f, 4, s);
     if (e == cudaSuccess) {

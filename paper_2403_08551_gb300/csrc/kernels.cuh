@@ -91,7 +91,7 @@ cudaError_t launch_render(const float4* rec_binned, const int2* ranges, const Ba
 cudaError_t launch_backward(const float4* rec_binned, const uint32_t* keys, const uint32_t* ids,
                             const int4* rect, const int64_t* pair_off, const float* dl_tiled,
                             const Batch& B, const int64_t* k_dev, int64_t capacity, float4* partial,
-                            cudaStream_t s);
+                            uint32_t* status, cudaStream_t s);
 cudaError_t launch_pack_dl(const float* dl_hwc, const Batch& B, float* dl_tiled, cudaStream_t s);
 
 struct AdamCfg {

@@ -63,7 +63,8 @@ __global__ void __launch_bounds__(Cfg::kThreads) k_render(const float4* __restri
     const int lt = t - d.tile_base;
     const int tx = lt % d.tw, ty = lt / d.tw;
     const int x0 = tx * T, y0 = ty * T;
-    const int2 rg = ranges[t];
+    int2 rg = ranges[t];
+    if (!gi_in_bounds(rg.x >= 0 && rg.y >= rg.x, status)) rg = make_int2(0, 0);
     const int L = rg.y - rg.x;
 
     constexpr int ROWS = Cfg::ROWS;
