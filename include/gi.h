@@ -279,6 +279,17 @@ GI_API gi_status gi_fit_stage_times(gi_fit* fit, float* ms);
  * SM MHz during the FFMA run, SM count. */
 GI_API gi_status gi_alu_peaks(double* result, gi_stream stream);
 
+/* Self-test of the bounded waits (failure detection without a GPU fault; the
+ * paper has no counterpart). Launches one kernel that waits on an mbarrier
+ * nothing arrives at (the wait of the render's TMA staging) and one that
+ * spins on a device flag nothing sets (the pattern of the look-back scans),
+ * each with limit_ns (1 ns .. 2 s) of global time, and returns their private
+ * status bits in *observed (host pointer): bit 0 = the mbarrier wait gave up,
+ * bit 1 = the spin gave up; bits 2 and 3 would mean a wait ended without its
+ * event (never expected). Synchronises `stream`; allocates nothing; leaves
+ * gi_device_errors() untouched and the context usable. */
+GI_API gi_status gi_selftest_bounded_waits(uint32_t* observed, int64_t limit_ns, gi_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

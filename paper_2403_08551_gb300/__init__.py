@@ -6,8 +6,9 @@ include/gi.h); this package is its Python binding: per-stage calls, an
 autograd Function and multi-image fitting contexts.
 """
 from .api import (RENDER_SPLITS, Bins, Fit, GIRender, Renderer, alu_peaks, autotune, bin_tiles, device_errors, project,
-                  rasterize, render, render_backward, tiles, vq_decode)
+                  rasterize, render, render_backward, selftest_bounded_waits, tiles, vq_decode)
 from ._lib import GIError, load
 
 __all__ = ["RENDER_SPLITS", "Bins", "Fit", "GIRender", "Renderer", "GIError", "alu_peaks", "autotune", "bin_tiles",
-           "device_errors", "load", "project", "rasterize", "render", "render_backward", "tiles", "vq_decode"]
+           "device_errors", "load", "project", "rasterize", "render", "render_backward", "selftest_bounded_waits",
+           "tiles", "vq_decode"]

@@ -48,6 +48,7 @@ SIGNATURES = {
     "gi_fit_destroy": (i32, [P]),
     "gi_fit_stage_times": (i32, [P, P]),
     "gi_alu_peaks": (i32, [P, P]),
+    "gi_selftest_bounded_waits": (i32, [P, i64, P]),
 }
 
 

@@ -13,7 +13,8 @@ import torch
 from . import _lib as L
 
 __all__ = ["project", "bin_tiles", "render", "render_backward", "vq_decode", "device_errors",
-           "GIRender", "rasterize", "Fit", "Bins", "alu_peaks", "tiles", "autotune", "RENDER_SPLITS", "Renderer"]
+           "GIRender", "rasterize", "Fit", "Bins", "alu_peaks", "tiles", "autotune", "RENDER_SPLITS", "Renderer",
+           "selftest_bounded_waits"]
 
 # Render splits (lane groups sharing one tile's list) available per tile edge.
 RENDER_SPLITS = {8: (2, 4), 16: (4, 8), 32: (1, 2)}
@@ -385,6 +386,15 @@ def autotune(targets, params, tiles=(8, 16, 32), splits=None, steps=10, warmup=3
             f.close()
     best = min(times, key=times.get)
     return {"tile": best[0], "render_split": best[1], "ms_per_step": times}
+
+
+def selftest_bounded_waits(limit_ns: int = 2_000_000) -> int:
+    """Runs the bounded-wait self-test (gi_selftest_bounded_waits) and
+    returns its status bits: 3 = both waits gave up after limit_ns."""
+    bits = ctypes.c_uint32(0)
+    L.check(L.load().gi_selftest_bounded_waits(ctypes.byref(bits), int(limit_ns), L.stream_handle()),
+            "gi_selftest_bounded_waits")
+    return int(bits.value)
 
 
 def alu_peaks():

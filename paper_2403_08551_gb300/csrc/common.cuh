@@ -35,6 +35,14 @@ enum : uint32_t {
     kErrBounds = 1u << 2,    // an index check failed
 };
 
+// Look-back words: 2 flag bits (aggregate / inclusive prefix) over a 30-bit
+// value; spins on an unpublished word are bounded by kSpinLimit.
+constexpr uint32_t kFlagAgg = 1u << 30;
+constexpr uint32_t kFlagPre = 2u << 30;
+constexpr uint32_t kValMask = (1u << 30) - 1;
+constexpr uint32_t kSpinLimit = 1u << 20;      // look-back spins (>= 64 ns each after the first 16)
+constexpr uint64_t kWaitLimitNs = 1000000000ull;  // bounded mbarrier waits: 1 s
+
 // Per-image descriptor. Pixels of image b live at pix_base + y*W + x.
 struct ImgDesc {
     int32_t W, H, tw, th;
@@ -125,9 +133,19 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
 }
 
 // Bounded wait on an mbarrier phase; returns false if it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t max_iters = 1u << 24) {
-    uint32_t addr = smem_addr(bar);
-    for (uint32_t it = 0; it < max_iters; ++it) {
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Waits for phase `parity` of the mbarrier; gives up (returns false) once
+// limit_ns of global time have passed, so a copy that never lands cannot
+// hang the kernel.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t limit_ns = kWaitLimitNs) {
+    const uint32_t addr = smem_addr(bar);
+    const uint64_t t0 = globaltimer_ns();
+    for (uint32_t it = 0;; ++it) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -137,8 +155,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
             : "r"(addr), "r"(parity)
             : "memory");
         if (done) return true;
+        if ((it & 15u) == 15u && globaltimer_ns() - t0 > limit_ns) return false;
     }
-    return false;
 }
 
 // 1-D bulk copy global -> shared (TMA unit), completion counted on `bar`.
@@ -193,12 +211,6 @@ struct NvtxRange {
     NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
-// Look-back words: 2 flag bits (aggregate / inclusive prefix) over a 30-bit
-// value; spins on an unpublished word are bounded by kSpinLimit.
-constexpr uint32_t kFlagAgg = 1u << 30;
-constexpr uint32_t kFlagPre = 2u << 30;
-constexpr uint32_t kValMask = (1u << 30) - 1;
-constexpr uint32_t kSpinLimit = 1u << 22;
 
 template <typename Tv>
 __device__ __forceinline__ Tv warp_incl_scan(Tv v) {

@@ -269,6 +269,27 @@ def test_deterministic(gi):
         assert torch.equal(a[k], b[k]), k
 
 
+def test_bounded_waits_give_up_and_report(gi):
+    """Failure detection without a fault: a TMA-style mbarrier wait with no
+    arrival and a spin on a flag nothing sets both stop after their limit and
+    report it in the self-test's own status word; the context stays usable
+    (a render afterwards is correct) and the library's error word is clean."""
+    import time
+    assert gi.device_errors(clear=True) == 0
+    t0 = time.perf_counter()
+    bits = gi.selftest_bounded_waits(2_000_000)  # 2 ms each
+    assert time.perf_counter() - t0 < 30
+    assert bits == 3
+    assert gi.device_errors() == 0
+    W, H, T, n = 96, 64, 16, 300
+    means, chol, color = synth.init_gaussians(n, W, H, 41)
+    out = gi.rasterize(dev(means), dev(chol), dev(color), W, H, T)
+    torch.cuda.synchronize()
+    rect, cnt = oracle.rect_rule(means, chol, color, W, H, T)
+    ids, rg, _ = oracle.bin_tiles(rect, cnt, W, H, T)
+    check_pixels(out, oracle.render(means, chol, color, ids, rg, W, H, T))
+
+
 def test_capacity_overflow_reported(gi):
     W, H, T, n = 128, 128, 16, 500
     means, chol, color = synth.init_gaussians(n, W, H, 14)
