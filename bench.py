@@ -80,13 +80,13 @@ def binning_launches(n, W, H, T):
     """Kernels the fit step's binning launches: 2 for the count-matrix path (at
     most 2048 tiles and 128-Gaussian chunks x tiles <= 2^20; the projection
     writes the count rows), else emit + one onesweep per LSD pass (digits of
-    at most 8 bits) + ranges."""
+    at most 9 bits) + ranges."""
     tiles = ((W + T - 1) // T) * ((H + T - 1) // T)
     chunks = max(1, (n + 127) // 128)
     if tiles <= 2048 and chunks * tiles <= (1 << 20):
         return 2
     bits = max(1, math.ceil(math.log2(max(tiles, 2))))
-    return 2 + (bits + 7) // 8
+    return 2 + (bits + 8) // 9
 
 
 def evals_per_render(ranges, W, H, T):

@@ -169,10 +169,10 @@ __global__ void __launch_bounds__(kProjBlock) k_emit(const int4* __restrict__ re
                                                      int64_t* __restrict__ k_max, uint32_t* __restrict__ hist,
                                                      RadixPlan rp, uint32_t* __restrict__ status) {
     __shared__ int64_t s_warp[32];
-    __shared__ uint32_t s_hist[4 * 256];
+    __shared__ uint32_t s_hist[kMaxPasses * kMaxRadix];
     pdl_wait();
     const int n = B.total_gauss;
-    for (int i = threadIdx.x; i < 4 * 256; i += blockDim.x) s_hist[i] = 0;
+    for (int i = threadIdx.x; i < kMaxPasses * kMaxRadix; i += blockDim.x) s_hist[i] = 0;
     int64_t pre = 0;
     for (int i = threadIdx.x; i < (int)blockIdx.x; i += blockDim.x) pre += blk_sum[i];
     pre = block_sum<int64_t>(pre, s_warp);
@@ -200,23 +200,27 @@ __global__ void __launch_bounds__(kProjBlock) k_emit(const int4* __restrict__ re
                 keys[p] = key;
                 vals[p] = (uint32_t)g;
                 for (int ps = 0; ps < rp.passes; ++ps)
-                    atomicAdd(&s_hist[ps * 256 + ((key >> (ps * rp.dbits)) & dmask)], 1u);
+                    atomicAdd(&s_hist[ps * kMaxRadix + ((key >> (ps * rp.dbits)) & dmask)], 1u);
             }
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < rp.passes * 256; i += blockDim.x) {
+    // Flush into one of kHistReplicas copies, spreading the additions of the
+    // blocks over more addresses; the sort sums the copies.
+    uint32_t* hr = hist + (blockIdx.x % kHistReplicas) * kMaxRadix;
+    for (int i = threadIdx.x; i < rp.passes * kMaxRadix; i += blockDim.x) {
         const uint32_t v = s_hist[i];
-        if (v) atomicAdd(&hist[i], v);
+        if (v) atomicAdd(&hr[(i / kMaxRadix) * kHistReplicas * kMaxRadix + (i % kMaxRadix)], v);
     }
 }
 
 // ---------------------------------------------------------------------------
-// One stable LSD radix pass (onesweep). Each block takes a ticket, ranks its
-// 4096 keys per digit with warp-level multi-split (items ordered by (warp,
-// round, lane) = input order, so the ranking is stable), resolves its
-// per-digit global offset with a decoupled look-back over lower tickets
-// (bounded spin), and scatters.
+// One stable LSD radix pass (onesweep) over digits of up to 9 bits. Each
+// block takes a ticket, ranks its kSortTile keys per digit with warp-level
+// multi-split (items ordered by (warp, round, lane) = input order, so the
+// ranking is stable), resolves its per-digit global offset with a decoupled
+// look-back over lower tickets (bounded spin), and scatters. A thread owns
+// digits threadIdx.x and threadIdx.x + kSortThreads in the per-digit phases.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in, uint32_t* __restrict__ keys_out,
@@ -224,14 +228,18 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     const uint32_t* __restrict__ hist, uint32_t* __restrict__ lookback, uint32_t* __restrict__ ticket,
     uint32_t* __restrict__ status) {
     constexpr int NW = kSortThreads / 32;
-    __shared__ uint32_t s_wc[NW][256];
-    __shared__ uint32_t s_base[256];
+    constexpr int DPT = kMaxRadix / kSortThreads;  // digits per thread in the per-digit phases
+    __shared__ uint32_t s_wc[NW][kMaxRadix];
+    __shared__ uint32_t s_base[kMaxRadix];   // global position of the block's first key of each digit
+    __shared__ uint32_t s_boff[kMaxRadix];   // block-local position of the first key of each digit
     __shared__ uint32_t s_warp[32];
+    __shared__ uint32_t s_tot0;
     __shared__ uint32_t s_ticket;
+    extern __shared__ uint32_t s_stage[];    // [kSortTile] keys, then [kSortTile] values, in digit order
     pdl_wait();
     const int K = (int)min(*k_dev, capacity);
     if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1u);
-    for (int i = threadIdx.x; i < NW * 256; i += kSortThreads) (&s_wc[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < NW * kMaxRadix; i += kSortThreads) (&s_wc[0][0])[i] = 0;
     __syncthreads();
     const int blk = (int)s_ticket;
     const int64_t start = (int64_t)blk * kSortTile;
@@ -252,7 +260,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
         } else {
             key[r] = 0;
             val[r] = 0;
-            dig[r] = 256;
+            dig[r] = kMaxRadix;  // no digit: not ranked, not stored
         }
     }
     uint32_t* wc = s_wc[warp];
@@ -263,7 +271,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
         const uint32_t peers = __match_any_sync(0xffffffffu, dg);
         const int leader = __ffs(peers) - 1;
         uint32_t base = 0;
-        if (lane == leader && dg < 256) {
+        if (lane == leader && dg < kMaxRadix) {
             base = wc[dg];
             wc[dg] = base + __popc(peers);
         }
@@ -273,29 +281,59 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
     }
     __syncthreads();
 
-    const int d = threadIdx.x;  // kSortThreads >= 256 >= radix
-    uint32_t tot = 0;
-    if (d < radix) {
+    // Per digit: exclusive offsets of the warps, the block's total, published
+    // at once (an inclusive prefix for the first block).
+    uint32_t tot[DPT];
 #pragma unroll
-        for (int w = 0; w < NW; ++w) {
-            const uint32_t v = s_wc[w][d];
-            s_wc[w][d] = tot;
-            tot += v;
+    for (int q = 0; q < DPT; ++q) {
+        const int d = threadIdx.x + q * kSortThreads;
+        tot[q] = 0;
+        if (d < radix) {
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                const uint32_t v = s_wc[w][d];
+                s_wc[w][d] = tot[q];
+                tot[q] += v;
+            }
+            st_relaxed_u32(lookback + (size_t)blk * kMaxRadix + d, (blk == 0 ? kFlagPre : kFlagAgg) | tot[q]);
         }
     }
-    // Global digit base: exclusive scan of this pass's histogram.
-    const uint32_t h = d < radix ? hist[d] : 0u;
-    const uint32_t hex = block_incl_scan<uint32_t>(h, s_warp) - h;
-    if (d < radix) {
+    // Global digit bases: exclusive scan of this pass's histogram, digits
+    // [0, kSortThreads) then [kSortThreads, kMaxRadix).
+    uint32_t hex[DPT];
+    {
+        uint32_t carry = 0, lcarry = 0;
+#pragma unroll
+        for (int q = 0; q < DPT; ++q) {
+            const int d = threadIdx.x + q * kSortThreads;
+            uint32_t h = 0;
+            if (d < radix) {
+#pragma unroll
+                for (int rep = 0; rep < kHistReplicas; ++rep) h += hist[rep * kMaxRadix + d];
+            }
+            const uint32_t incl = block_incl_scan<uint32_t>(h, s_warp);  // ends with a barrier
+            hex[q] = carry + incl - h;
+            if (threadIdx.x == kSortThreads - 1) s_tot0 = incl;
+            __syncthreads();
+            carry += s_tot0;
+            __syncthreads();
+            const uint32_t lincl = block_incl_scan<uint32_t>(tot[q], s_warp);
+            if (d < radix) s_boff[d] = lcarry + lincl - tot[q];
+            if (threadIdx.x == kSortThreads - 1) s_tot0 = lincl;
+            __syncthreads();
+            lcarry += s_tot0;
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < DPT; ++q) {
+        const int d = threadIdx.x + q * kSortThreads;
+        if (d >= radix) continue;
         uint32_t excl = 0;
-        uint32_t* mine = lookback + (size_t)blk * 256 + d;
-        if (blk == 0) {
-            st_release_u32(mine, kFlagPre | tot);
-        } else {
-            st_release_u32(mine, kFlagAgg | tot);
-            // Windowed look-back: kWin predecessor words are loaded at once
-            // (independent loads), then consumed nearest first until an
-            // inclusive prefix is found or a word is not published yet.
+        if (blk > 0) {
+            // Windowed look-back: kWin predecessor words loaded at once
+            // (independent loads), consumed nearest first until an inclusive
+            // prefix is found or a word is not published yet.
             int j = blk - 1;
             uint32_t spins = 0;
             bool found = false;
@@ -303,7 +341,7 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
                 uint32_t v[kWin];
 #pragma unroll
                 for (int i = 0; i < kWin; ++i)
-                    v[i] = (j - i >= 0) ? ld_relaxed_u32(lookback + (size_t)(j - i) * 256 + d) : kFlagPre;
+                    v[i] = (j - i >= 0) ? ld_relaxed_u32(lookback + (size_t)(j - i) * kMaxRadix + d) : kFlagPre;
                 int used = 0;
 #pragma unroll
                 for (int i = 0; i < kWin; ++i) {
@@ -323,23 +361,33 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
                     if (spins > 16) __nanosleep(64);
                 }
             }
-            st_release_u32(mine, kFlagPre | ((excl + tot) & kValMask));
+            st_relaxed_u32(lookback + (size_t)blk * kMaxRadix + d, kFlagPre | ((excl + tot[q]) & kValMask));
         }
-        s_base[d] = hex + excl;
+        s_base[d] = hex[q] + excl;
     }
-    __syncthreads();
+    // Stage the block's keys in digit order, then write each digit's run
+    // with consecutive threads (coalesced stores).
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         const uint32_t dg = dig[r];
-        if (dg < 256) {
-            const uint32_t pos = s_base[dg] + s_wc[warp][dg] + lrank[r];
-            if (pos >= (uint32_t)K) {
-                flag_error(status, kErrBounds);
-                continue;
-            }
-            keys_out[pos] = key[r];
-            vals_out[pos] = val[r];
+        if (dg < kMaxRadix) {
+            const uint32_t li = s_boff[dg] + s_wc[warp][dg] + lrank[r];
+            s_stage[li] = key[r];
+            s_stage[kSortTile + li] = val[r];
         }
+    }
+    __syncthreads();
+    const int nvalid = (int)min((int64_t)kSortTile, (int64_t)K - start);
+    for (int i = threadIdx.x; i < nvalid; i += kSortThreads) {
+        const uint32_t kk = s_stage[i];
+        const uint32_t dg = (kk >> shift) & mask;
+        const uint32_t pos = s_base[dg] + ((uint32_t)i - s_boff[dg]);
+        if (pos >= (uint32_t)K) {
+            flag_error(status, kErrBounds);
+            continue;
+        }
+        keys_out[pos] = kk;
+        vals_out[pos] = s_stage[kSortTile + i];
     }
 }
 
@@ -389,7 +437,7 @@ int sm_count() {
 RadixPlan radix_plan(int total_tiles) {
     int bits = 1;
     while (bits < 31 && (int64_t(1) << bits) < (int64_t)total_tiles) ++bits;
-    const int passes = (bits + 7) / 8;
+    const int passes = (bits + kMaxDigitBits - 1) / kMaxDigitBits;
     const int dbits = (bits + passes - 1) / passes;
     return {bits, passes, dbits};
 }
@@ -419,8 +467,9 @@ BinWs bin_ws_layout(void* base, int64_t n, int64_t capacity, int total_tiles) {
         w.vals_tmp = static_cast<uint32_t*>(take(cap * 4));
     }
     const size_t zero_off = off;
-    if (!w.cm_path) w.hist = static_cast<uint32_t*>(take((size_t)rp.passes * 256 * 4));
-    w.lookback = static_cast<uint32_t*>(take(w.cm_path ? (size_t)groups * 4 : (size_t)rp.passes * sblk * 256 * 4));
+    if (!w.cm_path) w.hist = static_cast<uint32_t*>(take((size_t)rp.passes * kHistReplicas * kMaxRadix * 4));
+    w.lookback =
+        static_cast<uint32_t*>(take(w.cm_path ? (size_t)groups * 4 : (size_t)rp.passes * sblk * kMaxRadix * 4));
     w.tickets = static_cast<uint32_t*>(take(16));
     w.zero = b ? reinterpret_cast<uint32_t*>(b + zero_off) : nullptr;
     w.zero_words = (int64_t)((off - zero_off) / 4);
@@ -463,9 +512,17 @@ cudaError_t launch_bin(const int4* rect, const int32_t* cnt, const float4* rec, 
     cudaError_t e = launch_pdl(k_emit, dim3(nblk), dim3(kProjBlock), 0, s, rect, cnt, ws.blk_sum, B, capacity, ka, va,
                                pair_off, k_dev, k_max, ws.hist, rp, status);
     if (e != cudaSuccess) return e;
+    static bool attr = false;  // the staging buffer and the static arrays exceed the default 48 KB window
+    if (!attr) {
+        e = cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortStageBytes);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
     for (int ps = 0; ps < rp.passes; ++ps) {
-        e = launch_pdl(k_onesweep, dim3((unsigned)sblk), dim3(kSortThreads), 0, s, ka, va, kb, vb, k_dev, capacity,
-                       ps * rp.dbits, rp.dbits, ws.hist + ps * 256, ws.lookback + (size_t)ps * sblk * 256,
+        e = launch_pdl(k_onesweep, dim3((unsigned)sblk), dim3(kSortThreads), (size_t)kSortStageBytes, s, ka, va, kb,
+                       vb, k_dev, capacity,
+                       ps * rp.dbits, rp.dbits, ws.hist + ps * kHistReplicas * kMaxRadix,
+                       ws.lookback + (size_t)ps * sblk * kMaxRadix,
                        ws.tickets + ps, status);
         if (e != cudaSuccess) return e;
         std::swap(ka, kb);

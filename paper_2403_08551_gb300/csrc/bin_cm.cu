@@ -226,9 +226,9 @@ __global__ void __launch_bounds__(kCmScanWarps * 32) k_colscan(uint32_t* __restr
         const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
         uint32_t excl = 0;
         if (blk == 0) {
-            if (lane == 0) st_release_u32(lookback, kFlagPre | (tot & kValMask));
+            if (lane == 0) st_relaxed_u32(lookback, kFlagPre | (tot & kValMask));
         } else {
-            if (lane == 0) st_release_u32(lookback + blk, kFlagAgg | (tot & kValMask));
+            if (lane == 0) st_relaxed_u32(lookback + blk, kFlagAgg | (tot & kValMask));
             int j = blk - 1;
             uint32_t spins = 0;
             while (j >= 0) {
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(kCmScanWarps * 32) k_colscan(uint32_t* __restr
                 if (pre) break;
                 j -= 32;
             }
-            if (lane == 0) st_release_u32(lookback + blk, kFlagPre | ((excl + tot) & kValMask));
+            if (lane == 0) st_relaxed_u32(lookback + blk, kFlagPre | ((excl + tot) & kValMask));
         }
         const uint32_t start = excl + incl - col;
         s_start[lane] = start;

@@ -27,14 +27,19 @@ struct ZeroJob {
 struct RadixPlan {
     int bits;    // total key bits
     int passes;  // LSD passes
-    int dbits;   // digit bits per pass (<= 8)
+    int dbits;   // digit bits per pass (<= kMaxDigitBits)
 };
 RadixPlan radix_plan(int total_tiles);
 
 constexpr int kProjBlock = 256;        // Gaussians per projection / emit block
 constexpr int kSortThreads = 256;      // threads per onesweep block
-constexpr int kSortItems = 8;          // keys per thread
+constexpr int kSortItems = 16;         // keys per thread
+constexpr int kMaxDigitBits = 9;       // radix digits of at most 9 bits (512 buckets)
+constexpr int kMaxRadix = 1 << kMaxDigitBits;
+constexpr int kMaxPasses = 4;          // 31-bit keys at most
+constexpr int kHistReplicas = 8;       // copies of each pass's digit histogram (spread the emit's atomics)
 constexpr int kSortTile = kSortThreads * kSortItems;  // keys per onesweep block
+constexpr int kSortStageBytes = kSortTile * 8;          // keys + values staged in digit order
 
 // Count-matrix binning (bin_cm.cu): chunks of kCmChunk Gaussians; used when
 // the batch has at most kCmMaxTiles tiles and chunks x tiles <= kCmMaxCells.
@@ -45,7 +50,7 @@ bool cm_applies(int64_t n, int total_tiles);
 
 // Binning workspace carve-up. [zero, zero + zero_words) holds every buffer
 // that must be zero before a binning pass. Radix path: keys_tmp, vals_tmp,
-// hist, lookback [passes][sort_blocks][256]. Count-matrix path: cm
+// hist [passes][kHistReplicas][kMaxRadix], lookback [passes][sort_blocks][kMaxRadix]. Count-matrix path: cm
 // [chunks][tiles], chunk_sum [chunks], lookback [tile groups].
 struct BinWs {
     bool cm_path;
@@ -56,7 +61,7 @@ struct BinWs {
     uint32_t* chunk_sum;  // [chunks]            (count matrix)
     uint32_t* zero;
     int64_t zero_words;
-    uint32_t* hist;       // [passes][256]       (radix)
+    uint32_t* hist;       // [passes][kHistReplicas][kMaxRadix] (radix)
     uint32_t* lookback;
     uint32_t* tickets;    // [4]
     size_t bytes;

@@ -147,6 +147,7 @@ BIN_CASES = [
     (300, 200, 1000, 8, 23, 6.0),      # 1026 tiles, wide Gaussians: count matrix
     (1400, 700, 3000, 16, 24, 6.0),    # 3872 tiles, wide Gaussians: radix sort
     (96, 96, 129, 32, 25, 1.0),        # 9 tiles, two chunks (one Gaussian in the second)
+    (8192, 8192, 3000, 8, 26, 4.0),    # 1,048,576 tiles: 20-bit keys, three radix passes
 ]
 
 
