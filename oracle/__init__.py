@@ -18,6 +18,10 @@ Parity status per function (pins live in ``tests/test_oracle_*.py``):
                 union additivity, brute force bit-exact)
   backward .... pinned (central finite differences, isotropic closed form)
   adam ........ pinned (closed-form first step, torch.optim.Adam)
+  paper_formation / paper_forward_backward ... pinned (finite differences
+                in theta and the raw Cholesky vector; inverse of atanh init)
+  adan ........ pinned (closed-form first step, constant-gradient steps,
+                reduction to Adam's direction when b2 = 0)
   vq_decode ... pinned (IEEE float32 addition, zero residual codebook)
   rvq_encode .. pinned (exhaustive per-stage argmin)
 """
@@ -222,6 +226,78 @@ def adam(param, grad, m, v, step, lr, betas=ADAM_BETAS, eps=ADAM_EPS):
     mhat = m / (1.0 - b1 ** step)
     vhat = v / (1.0 - b2 ** step)
     return p - lr * mhat / (np.sqrt(vhat) + eps), m, v
+
+
+# ---------------------------------------------------------------------------
+# The paper's own parameterisation and optimiser (App. C.1, Sec. 4.1).
+# ---------------------------------------------------------------------------
+
+def paper_formation(theta, chol_raw, W, H):
+    """Raw parameters -> pixel-space ones (App. C.1): positions pass through
+    tanh into (-1, 1), read as mu = (tanh(theta) + 1) / 2 * (W, H); the
+    Cholesky diagonal gets +0.5 (l1' = l1 + 0.5, l3' = l3 + 0.5). Returns
+    FP32 means and Cholesky vectors (tanh in FP64, each result rounded once)
+    and the FP64 Jacobian d mu / d theta = (1 - tanh^2) / 2 * (W, H)."""
+    th = np.asarray(theta, np.float64)
+    t = np.tanh(th)
+    scale = np.array([W, H], np.float64)
+    means = ((t + 1.0) * 0.5 * scale).astype(np.float32)
+    c = np.asarray(chol_raw, np.float32).copy()
+    c[:, 0] = c[:, 0] + np.float32(0.5)
+    c[:, 2] = c[:, 2] + np.float32(0.5)
+    dmu = (1.0 - t) * (1.0 + t) * 0.5 * scale
+    return means, c, dmu
+
+
+def paper_forward_backward(theta, chol_raw, color, target, T):
+    """forward_backward on the raw parameters of App. C.1: gradients with
+    respect to theta (chained through tanh) and to the raw Cholesky vector
+    (the +0.5 shift has unit derivative)."""
+    H, W, _ = target.shape
+    means, chol, dmu = paper_formation(theta, chol_raw, W, H)
+    r = forward_backward(means, chol, color, target, T)
+    g = r["grads"]
+    r["grads_raw"] = {"theta": g["means"] * dmu, "chol": g["chol"], "color": g["color"],
+                      "abs_theta": g["abs"]["means"] * np.abs(dmu)}
+    return r
+
+
+ADAN_BETAS = (0.98, 0.92, 0.99)  # decay factors of the three averages (Adan's 0.02, 0.08, 0.01)
+
+
+def adan(param, grad, state, step, lr, betas=ADAN_BETAS, eps=ADAM_EPS):
+    """One Adan step (Xie et al. 2022, Adaptive Nesterov momentum), FP64,
+    without weight decay, with bias correction of the three averages.
+    state = (m, v, n, g_prev); on the first step (step == 1) the previous
+    gradient is taken equal to the current one, so the difference is 0.
+      m = b1 m + (1 - b1) g                       (gradient average)
+      v = b2 v + (1 - b2) (g - g_prev)            (gradient-difference average)
+      n = b3 n + (1 - b3) (g + b2 (g - g_prev))^2 (second moment of the
+                                                   Nesterov-corrected gradient)
+      p -= lr (m^ + b2 v^) / (sqrt(n^) + eps),  x^ = x / (1 - b^step)
+    Returns (param, (m, v, n, g))."""
+    b1, b2, b3 = betas
+    p = np.asarray(param, np.float64)
+    g = np.asarray(grad, np.float64)
+    m, v, n, gp = (np.asarray(x, np.float64) for x in state)
+    if step == 1:
+        gp = g
+    d = g - gp
+    m = b1 * m + (1.0 - b1) * g
+    v = b2 * v + (1.0 - b2) * d
+    n = b3 * n + (1.0 - b3) * (g + b2 * d) ** 2
+    mh = m / (1.0 - b1 ** step)
+    vh = v / (1.0 - b2 ** step)
+    nh = n / (1.0 - b3 ** step)
+    return p - lr * (mh + b2 * vh) / (np.sqrt(nh) + eps), (m, v, n, g)
+
+
+def lr_at(lr, step, halve_every):
+    """Learning rate of 1-based step `step`: halved every `halve_every`
+    steps (Sec. 4.1: 1e-3, halved every 20000); 0 = constant."""
+    if not halve_every:
+        return lr
+    return lr * 0.5 ** ((step - 1) // halve_every)
 
 
 def vq_decode(means16, idx, codebooks):
