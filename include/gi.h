@@ -82,6 +82,7 @@ typedef struct {
  * exp(-sigma) = exp2(-(z1^2 + z2^2)) (Sec. 3.1 with Sigma^-1 = L^-T L^-1). */
 #define GI_REC_FLOATS 8
 
+/* ABI version: 2 (gi_fit_desc gained param_mode, optimizer, beta3, lr_halve_every). */
 GI_API int32_t gi_abi_version(void);
 GI_API const char* gi_last_error(void);
 GI_API const char* gi_status_string(int32_t status);
@@ -234,6 +235,18 @@ typedef struct {
     int32_t stage_events; /* 1: record CUDA events between the five stages */
     int32_t render_split; /* lane groups sharing one tile's list in the render: 0 = default;
                              tile 8: 2 or 4, tile 16: 4 or 8, tile 32: 1 or 2 */
+    int32_t param_mode;   /* 0: params are pixel-space (mx, my, l1, l2, l3, c');
+                             1: params are the raw parameters of App. C.1: positions
+                             theta with mu = (tanh(theta) + 1) / 2 * (W, H), Cholesky
+                             diagonal stored without its +0.5 (l1 + 0.5, l2, l3 + 0.5) */
+    int32_t optimizer;    /* 0: Adam (beta1, beta2, eps); 1: Adan (Sec. 4.1; Xie et al. 2022):
+                             beta1, beta2, beta3 decay the averages of the gradient, of its
+                             change and of the squared extrapolated gradient
+                             g + beta2 (g - g_prev) (Adan's 0.02, 0.08, 0.01 are 0.98, 0.92,
+                             0.99 here), bias-corrected, no weight decay */
+    float beta3;          /* Adan only */
+    int32_t lr_halve_every; /* every learning rate halves every this many steps (the paper:
+                               20000); 0 = constant */
 } gi_fit_desc;
 
 /* Allocates the context and copies targets and params (the caller's buffers
@@ -247,7 +260,8 @@ GI_API gi_status gi_fit_step(gi_fit* fit, int32_t steps, gi_stream stream);
 GI_API gi_status gi_fit_render(gi_fit* fit, gi_stream stream);
 
 /* Device pointers into the context (valid until gi_fit_destroy):
- *   GI_FIT_PARAMS [N][8], GI_FIT_ADAM_M [N][8], GI_FIT_ADAM_V [N][8],
+ *   GI_FIT_PARAMS [N][8], GI_FIT_ADAM_M [N][8], GI_FIT_ADAM_V [N][8] (the
+ *   optimiser's first two averages; Adan also GI_FIT_ADAN_N, GI_FIT_ADAN_GPREV),
  *   GI_FIT_GRADS [N][8] (gradients of the last step),
  *   GI_FIT_OUT (images concatenated, HWC f32, the last step's render),
  *   GI_FIT_LOSS [n_images] f64 sums of squared error of the last step,
@@ -263,7 +277,9 @@ enum {
     GI_FIT_LOSS = 5,
     GI_FIT_STEP = 6,
     GI_FIT_K = 7,
-    GI_FIT_TARGET = 8
+    GI_FIT_TARGET = 8,
+    GI_FIT_ADAN_N = 9,     /* [N][8] Adan's third average (NULL pointer for Adam) */
+    GI_FIT_ADAN_GPREV = 10 /* [N][8] Adan's previous gradient (NULL pointer for Adam) */
 };
 GI_API gi_status gi_fit_pointer(gi_fit* fit, int32_t what, void** ptr);
 GI_API gi_status gi_fit_destroy(gi_fit* fit);

@@ -25,7 +25,8 @@ STATUS = {0: "GI_OK", 1: "GI_ERR_INVALID_ARG", 2: "GI_ERR_CUDA", 3: "GI_ERR_CAPA
           4: "GI_ERR_TIMEOUT", 5: "GI_ERR_UNSUPPORTED", 6: "GI_ERR_NO_MEMORY"}
 DEVERR_CAPACITY, DEVERR_TIMEOUT, DEVERR_BOUNDS = 1, 2, 4
 
-FIT_PARAMS, FIT_ADAM_M, FIT_ADAM_V, FIT_GRADS, FIT_OUT, FIT_LOSS, FIT_STEP, FIT_K, FIT_TARGET = range(9)
+(FIT_PARAMS, FIT_ADAM_M, FIT_ADAM_V, FIT_GRADS, FIT_OUT, FIT_LOSS, FIT_STEP, FIT_K, FIT_TARGET, FIT_ADAN_N,
+ FIT_ADAN_GPREV) = range(11)
 
 # Every symbol include/gi.h declares, with (restype, argtypes).
 SIGNATURES = {
@@ -60,7 +61,8 @@ class GIFitDesc(ctypes.Structure):
     _fields_ = [("n_images", i32), ("widths", P), ("heights", P), ("counts", P), ("targets", P),
                 ("params", P), ("tile", i32), ("lr_means", f32), ("lr_chol", f32), ("lr_color", f32),
                 ("beta1", f32), ("beta2", f32), ("eps", f32), ("capacity", i64), ("use_graph", i32),
-                ("stage_events", i32), ("render_split", i32)]
+                ("stage_events", i32), ("render_split", i32), ("param_mode", i32), ("optimizer", i32),
+                ("beta3", f32), ("lr_halve_every", i32)]
 
 
 class GIError(RuntimeError):

@@ -14,7 +14,7 @@ from . import _lib as L
 
 __all__ = ["project", "bin_tiles", "render", "render_backward", "vq_decode", "device_errors",
            "GIRender", "rasterize", "Fit", "Bins", "alu_peaks", "tiles", "autotune", "RENDER_SPLITS", "Renderer",
-           "selftest_bounded_waits"]
+           "selftest_bounded_waits", "paper_to_pixel", "ADAN_BETAS"]
 
 # Render splits (lane groups sharing one tile's list) available per tile edge.
 RENDER_SPLITS = {8: (2, 4), 16: (4, 8), 32: (1, 2)}
@@ -201,6 +201,22 @@ class _DevArray:
                                          "version": 3, "strides": None}
 
 
+# Adan's decay factors of its three averages (Adan's 0.02, 0.08, 0.01).
+ADAN_BETAS = (0.98, 0.92, 0.99)
+
+
+def paper_to_pixel(p, W: int, H: int):
+    """Raw parameters of App. C.1 ([n,8]: theta, Cholesky without the +0.5 on
+    its diagonal, colour) -> pixel-space parameters, as the formation kernel
+    maps them (tanh in FP64, one rounding to FP32)."""
+    q = p.clone()
+    t = torch.tanh(p[:, 0:2].double())
+    q[:, 0:2] = ((t + 1.0) * 0.5 * torch.tensor([W, H], dtype=torch.float64, device=p.device)).float()
+    q[:, 2] = p[:, 2] + 0.5
+    q[:, 4] = p[:, 4] + 0.5
+    return q
+
+
 class Fit:
     """Fitting context over one or more images (Sec. 3.4): each step is
     formation, binning, render + L2 loss, backward and Adam, replayed from a
@@ -212,7 +228,8 @@ class Fit:
     def __init__(self, targets: Sequence[torch.Tensor], params: Sequence[torch.Tensor], tile: int = 16,
                  lr=(1e-3, 1e-2, 1e-2), betas=(0.9, 0.999), eps=1e-8, capacity: Optional[int] = None,
                  capacity_factor: float = 1.5, use_graph: bool = True, stage_events: bool = False,
-                 render_split: int = 0):
+                 render_split: int = 0, param_mode: str = "pixel", optimizer: str = "adam",
+                 lr_halve_every: int = 0):
         lib = L.load()
         assert len(targets) == len(params) and len(targets) >= 1
         self.shapes = [(int(t.shape[1]), int(t.shape[0])) for t in targets]
@@ -221,11 +238,18 @@ class Fit:
         dev = targets[0].device
         tgt = torch.cat([_dev(t, torch.float32, "target").reshape(-1) for t in targets])
         prm = torch.cat([_dev(p, torch.float32, "params").reshape(-1, 8) for p in params]).contiguous()
+        if param_mode not in ("pixel", "paper") or optimizer not in ("adam", "adan"):
+            raise ValueError("param_mode must be 'pixel' or 'paper', optimizer 'adam' or 'adan'")
+        self.param_mode, self.optimizer = param_mode, optimizer
+        if optimizer == "adan" and len(betas) != 3:
+            betas = ADAN_BETAS
         K = None
         if capacity is None or (render_split == 0 and tile == 16):
             K = 0
             for (W, H), p in zip(self.shapes, params):
                 p = p.contiguous()
+                if param_mode == "paper":
+                    p = paper_to_pixel(p, W, H)
                 rec, rect, cnt = project(p[:, 0:2].contiguous(), p[:, 2:5].contiguous(), p[:, 5:8].contiguous(),
                                          W, H, tile)
                 K += bin_tiles(rect, cnt, None, W, H, tile).K
@@ -246,7 +270,9 @@ class Fit:
         desc = L.GIFitDesc(n_img, ctypes.cast(self._w, ctypes.c_void_p), ctypes.cast(self._h, ctypes.c_void_p),
                            ctypes.cast(self._n, ctypes.c_void_p), tgt.data_ptr(), prm.data_ptr(), tile,
                            lr[0], lr[1], lr[2], betas[0], betas[1], eps, self.capacity, int(use_graph),
-                           int(stage_events), int(render_split))
+                           int(stage_events), int(render_split), int(param_mode == "paper"),
+                           int(optimizer == "adan"), float(betas[2]) if optimizer == "adan" else 0.0,
+                           int(lr_halve_every))
         h = ctypes.c_void_p()
         L.check(lib.gi_fit_create(ctypes.byref(desc), L.stream_handle(), ctypes.byref(h)), "gi_fit_create")
         self._h_fit = h
@@ -261,6 +287,9 @@ class Fit:
         self.loss_sum = self._view(L.FIT_LOSS, (n_img,), "<f8")
         self.step_count = self._view(L.FIT_STEP, (1,), "<i4")
         self.k = self._view(L.FIT_K, (1,), "<i8")
+        if optimizer == "adan":
+            self.adan_n = self._view(L.FIT_ADAN_N, (N, 8), "<f4")
+            self.adan_gprev = self._view(L.FIT_ADAN_GPREV, (N, 8), "<f4")
         self.targets = self._view(L.FIT_TARGET, (npix * 3,), "<f4")
 
     def _view(self, what, shape, typestr):
@@ -298,19 +327,28 @@ class Fit:
         step count (copies on the context's device). The pipeline has no
         random state; everything else is recomputed every step."""
         torch.cuda.current_stream().synchronize()
-        return {"params": self.params.clone(), "adam_m": self.adam_m.clone(), "adam_v": self.adam_v.clone(),
-                "step": int(self.step_count.item()), "shapes": list(self.shapes), "counts": list(self.counts),
-                "tile": self.tile}
+        sd = {"params": self.params.clone(), "adam_m": self.adam_m.clone(), "adam_v": self.adam_v.clone(),
+              "step": int(self.step_count.item()), "shapes": list(self.shapes), "counts": list(self.counts),
+              "tile": self.tile, "param_mode": self.param_mode, "optimizer": self.optimizer}
+        if self.optimizer == "adan":
+            sd["adan_n"] = self.adan_n.clone()
+            sd["adan_gprev"] = self.adan_gprev.clone()
+        return sd
 
     def load_state_dict(self, sd: dict):
         """Restores a checkpoint of a fit with the same images, Gaussian
         counts and tile edge; the next steps continue bit-identically."""
         if list(sd["shapes"]) != list(self.shapes) or list(sd["counts"]) != list(self.counts) or \
-                sd["tile"] != self.tile:
-            raise ValueError("checkpoint of a different fit (images, Gaussian counts or tile edge)")
+                sd["tile"] != self.tile or sd.get("param_mode", "pixel") != self.param_mode or \
+                sd.get("optimizer", "adam") != self.optimizer:
+            raise ValueError("checkpoint of a different fit (images, Gaussian counts, tile edge, "
+                             "parameterisation or optimiser)")
         self.params.copy_(sd["params"])
         self.adam_m.copy_(sd["adam_m"])
         self.adam_v.copy_(sd["adam_v"])
+        if self.optimizer == "adan":
+            self.adan_n.copy_(sd["adan_n"])
+            self.adan_gprev.copy_(sd["adan_gprev"])
         self.step_count.fill_(int(sd["step"]))
 
     def close(self):

@@ -76,7 +76,7 @@ using namespace gi;
 
 extern "C" {
 
-int32_t gi_abi_version(void) { return 1; }
+int32_t gi_abi_version(void) { return 2; }
 
 const char* gi_last_error(void) { return t_err; }
 
@@ -228,7 +228,7 @@ gi_status gi_render_backward(const float* rec_binned, const uint32_t* keys, cons
                             pair_off, dl_tiled, B, k_dev, capacity, partial, device_status(), s);
     if (e == cudaSuccess)
         e = launch_reduce(partial, pair_off, cnt, capacity, n, params_soa(nullptr, chol, nullptr), g_means, g_chol,
-                          g_color, g_conic, nullptr, nullptr, nullptr, nullptr, nullptr, s);
+                          g_color, g_conic, nullptr, nullptr, nullptr, nullptr, nullptr, B, s);
     if (e != cudaSuccess) return set_cuda_error(e, "gi_render_backward");
     return GI_OK;
 }

@@ -253,17 +253,26 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
                                                 ParamsIn P, float* __restrict__ g_means, float* __restrict__ g_chol,
                                                 float* __restrict__ g_color, float* __restrict__ g_conic,
                                                 AdamCfg cfg, float* __restrict__ params, float* __restrict__ m,
-                                                float* __restrict__ v, float* __restrict__ grads_aos) {
+                                                float* __restrict__ v, float* __restrict__ grads_aos, Batch B) {
     constexpr int kBatch = 8;
     __shared__ int s_step;
-    __shared__ float s_bc[2];  // lr scale 1/(1 - beta1^t) and 1/sqrt(1 - beta2^t)
+    // Adam: 1/(1 - b1^t), 1/sqrt(1 - b2^t); Adan: 1/(1 - b1^t), 1/(1 - b2^t),
+    // 1/sqrt(1 - b3^t); [3] = learning-rate factor of the halving schedule.
+    __shared__ float s_bc[4];
     pdl_wait();
     if (ADAM) {
         if (threadIdx.x == 0) {
             const int step = *cfg.step + 1;
             s_step = step;
             s_bc[0] = 1.f / (1.f - powf(cfg.beta1, (float)step));
-            s_bc[1] = rsqrtf(1.f - powf(cfg.beta2, (float)step));
+            if (cfg.optimizer == 1) {
+                s_bc[1] = 1.f / (1.f - powf(cfg.beta2, (float)step));
+                s_bc[2] = rsqrtf(1.f - powf(cfg.beta3, (float)step));
+            } else {
+                s_bc[1] = rsqrtf(1.f - powf(cfg.beta2, (float)step));
+                s_bc[2] = 0.f;
+            }
+            s_bc[3] = cfg.lr_halve_every > 0 ? ldexpf(1.f, -((step - 1) / cfg.lr_halve_every)) : 1.f;
         }
         __syncthreads();
     }
@@ -281,8 +290,11 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
             *reinterpret_cast<float4*>(mm) = M4[0]; *reinterpret_cast<float4*>(mm + 4) = M4[1];
             *reinterpret_cast<float4*>(vv) = V4[0]; *reinterpret_cast<float4*>(vv + 4) = V4[1];
         }
-        const float l1 = P.chol[(int64_t)g * P.ls], l2 = P.chol[(int64_t)g * P.ls + 1],
-                    l3 = P.chol[(int64_t)g * P.ls + 2];
+        float l1 = P.chol[(int64_t)g * P.ls], l2 = P.chol[(int64_t)g * P.ls + 1], l3 = P.chol[(int64_t)g * P.ls + 2];
+        if (ADAM && cfg.param_mode == 1) {  // App. C.1: the chain runs through l1 + 0.5, l3 + 0.5
+            l1 += 0.5f;
+            l3 += 0.5f;
+        }
         const int c = cnt[g];
         const int64_t p0 = pair_off[g];
         const int64_t p1 = min(p0 + (int64_t)c, capacity);
@@ -345,18 +357,50 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
             if (g_color) { g_color[3 * g] = gr[5]; g_color[3 * g + 1] = gr[6]; g_color[3 * g + 2] = gr[7]; }
             if (g_conic) { g_conic[3 * g] = gq[0]; g_conic[3 * g + 1] = gq[1]; g_conic[3 * g + 2] = gq[2]; }
         } else {
+            if (cfg.param_mode == 1 && c > 0) {
+                // d mu / d theta = (1 - tanh^2(theta)) / 2 * (W, H)
+                const ImgDesc d = img_desc(B, image_of_gauss(B, g));
+                const float tx = tanhf(pp[0]), ty = tanhf(pp[1]);
+                gr[0] *= (1.f - tx) * (1.f + tx) * 0.5f * (float)d.W;
+                gr[1] *= (1.f - ty) * (1.f + ty) * 0.5f * (float)d.H;
+            }
             if (grads_aos) {
                 float4* go = reinterpret_cast<float4*>(grads_aos) + 2 * (size_t)g;
                 go[0] = make_float4(gr[0], gr[1], gr[2], gr[3]);
                 go[1] = make_float4(gr[4], gr[5], gr[6], gr[7]);
             }
+            if (cfg.optimizer == 1) {
+                // Adan (Xie et al. 2022), no weight decay: m, v, n average the
+                // gradient, its change and the square of the extrapolated
+                // gradient g + b2 (g - g_prev); the first step takes g_prev = g.
+                float nn[8], gp[8];
+                float4* N4 = reinterpret_cast<float4*>(cfg.n) + 2 * (size_t)g;
+                float4* G4 = reinterpret_cast<float4*>(cfg.g_prev) + 2 * (size_t)g;
+                *reinterpret_cast<float4*>(nn) = N4[0]; *reinterpret_cast<float4*>(nn + 4) = N4[1];
+                *reinterpret_cast<float4*>(gp) = G4[0]; *reinterpret_cast<float4*>(gp + 4) = G4[1];
 #pragma unroll
-            for (int s = 0; s < 8; ++s) {
-                const float lr = cfg.lr[s < 2 ? 0 : (s < 5 ? 1 : 2)];
-                mm[s] = cfg.beta1 * mm[s] + (1.f - cfg.beta1) * gr[s];
-                vv[s] = cfg.beta2 * vv[s] + (1.f - cfg.beta2) * gr[s] * gr[s];
-                const float denom = sqrtf(vv[s]) * s_bc[1] + cfg.eps;
-                pp[s] -= (lr * s_bc[0]) * mm[s] / denom;
+                for (int s = 0; s < 8; ++s) {
+                    const float lr = cfg.lr[s < 2 ? 0 : (s < 5 ? 1 : 2)] * s_bc[3];
+                    const float dg = s_step == 1 ? 0.f : gr[s] - gp[s];
+                    mm[s] = cfg.beta1 * mm[s] + (1.f - cfg.beta1) * gr[s];
+                    vv[s] = cfg.beta2 * vv[s] + (1.f - cfg.beta2) * dg;
+                    const float ge = gr[s] + cfg.beta2 * dg;
+                    nn[s] = cfg.beta3 * nn[s] + (1.f - cfg.beta3) * ge * ge;
+                    const float dir = mm[s] * s_bc[0] + cfg.beta2 * (vv[s] * s_bc[1]);
+                    pp[s] -= lr * dir / (sqrtf(nn[s]) * s_bc[2] + cfg.eps);
+                    gp[s] = gr[s];
+                }
+                N4[0] = *reinterpret_cast<float4*>(nn); N4[1] = *reinterpret_cast<float4*>(nn + 4);
+                G4[0] = *reinterpret_cast<float4*>(gp); G4[1] = *reinterpret_cast<float4*>(gp + 4);
+            } else {
+#pragma unroll
+                for (int s = 0; s < 8; ++s) {
+                    const float lr = cfg.lr[s < 2 ? 0 : (s < 5 ? 1 : 2)] * s_bc[3];
+                    mm[s] = cfg.beta1 * mm[s] + (1.f - cfg.beta1) * gr[s];
+                    vv[s] = cfg.beta2 * vv[s] + (1.f - cfg.beta2) * gr[s] * gr[s];
+                    const float denom = sqrtf(vv[s]) * s_bc[1] + cfg.eps;
+                    pp[s] -= (lr * s_bc[0]) * mm[s] / denom;
+                }
             }
             P4[0] = *reinterpret_cast<float4*>(pp); P4[1] = *reinterpret_cast<float4*>(pp + 4);
             M4[0] = *reinterpret_cast<float4*>(mm); M4[1] = *reinterpret_cast<float4*>(mm + 4);
@@ -434,17 +478,17 @@ cudaError_t launch_pack_dl(const float* dl_hwc, const Batch& B, float* dl_tiled,
 cudaError_t launch_reduce(const float4* partial, const int64_t* pair_off, const int32_t* cnt, int64_t capacity,
                           int32_t n, const ParamsIn& P, float* g_means, float* g_chol, float* g_color,
                           float* g_conic, const AdamCfg* adam, float* params, float* m, float* v, float* grads_aos,
-                          cudaStream_t s) {
+                          const Batch& B, cudaStream_t s) {
     const int blocks = std::max(1, (n + kReduceThreads - 1) / kReduceThreads);
     if (adam) {
         return launch_pdl(k_reduce<true>, dim3(blocks), dim3(kReduceThreads), 0, s, partial, pair_off, cnt, capacity, n,
                           P, (float*)nullptr, (float*)nullptr, (float*)nullptr, (float*)nullptr, *adam, params, m, v,
-                          grads_aos);
+                          grads_aos, B);
     }
     AdamCfg none{};
     return launch_pdl(k_reduce<false>, dim3(blocks), dim3(kReduceThreads), 0, s, partial, pair_off, cnt, capacity, n, P,
                       g_means, g_chol, g_color, g_conic, none, (float*)nullptr, (float*)nullptr, (float*)nullptr,
-                      (float*)nullptr);
+                      (float*)nullptr, B);
 }
 
 }  // namespace gi

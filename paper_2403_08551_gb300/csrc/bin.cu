@@ -63,9 +63,17 @@ __global__ void __launch_bounds__(kProjBlock) k_project(ParamsIn P, Batch B, flo
     int c = 0;
     if (g < B.total_gauss) {
         const ImgDesc d = img_desc(B, image_of_gauss(B, g));
-        const float mx = P.means[(int64_t)g * P.ms], my = P.means[(int64_t)g * P.ms + 1];
-        const float l1 = P.chol[(int64_t)g * P.ls], l2 = P.chol[(int64_t)g * P.ls + 1],
-                    l3 = P.chol[(int64_t)g * P.ls + 2];
+        float mx = P.means[(int64_t)g * P.ms], my = P.means[(int64_t)g * P.ms + 1];
+        float l1 = P.chol[(int64_t)g * P.ls], l2 = P.chol[(int64_t)g * P.ls + 1], l3 = P.chol[(int64_t)g * P.ls + 2];
+        if (B.param_mode == 1) {
+            // App. C.1: positions through tanh into (-1, 1), read as
+            // mu = (tanh(theta) + 1) / 2 * (W, H) (tanh in FP64, one rounding
+            // to FP32); +0.5 on the Cholesky diagonal.
+            mx = (float)__dmul_rn(__dmul_rn(__dadd_rn(tanh((double)mx), 1.0), 0.5), (double)d.W);
+            my = (float)__dmul_rn(__dmul_rn(__dadd_rn(tanh((double)my), 1.0), 0.5), (double)d.H);
+            l1 = __fadd_rn(l1, 0.5f);
+            l3 = __fadd_rn(l3, 0.5f);
+        }
         const float cr = P.color[(int64_t)g * P.cs], cg = P.color[(int64_t)g * P.cs + 1],
                     cb = P.color[(int64_t)g * P.cs + 2];
         int4 r = make_int4(0, 0, 0, 0);

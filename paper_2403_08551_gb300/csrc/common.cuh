@@ -60,6 +60,8 @@ struct Batch {
     int32_t total_tiles;  // sum of tw*th
     int32_t total_gauss;  // sum of n
     int32_t split;        // render: warp groups sharing one tile's list (0 = default for the tile edge)
+    int32_t param_mode;   // 0: pixel-space parameters; 1: raw parameters of App. C.1 (tanh positions,
+                          //    Cholesky diagonal + 0.5), formation maps them to pixel space
 };
 
 __device__ __forceinline__ ImgDesc img_desc(const Batch& b, int i) {

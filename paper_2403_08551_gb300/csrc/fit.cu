@@ -105,7 +105,7 @@ cudaError_t enqueue_step(gi_fit* f, cudaStream_t s) {
     if (e == cudaSuccess) {
         NvtxRange r("gi:update");
         e = launch_reduce(f->partial, f->pair_off, f->cnt, f->capacity, (int32_t)f->N, params_aos(f->params),
-                          nullptr, nullptr, nullptr, nullptr, &f->adam, f->params, f->m, f->v, f->grads, s);
+                          nullptr, nullptr, nullptr, nullptr, &f->adam, f->params, f->m, f->v, f->grads, f->B, s);
     }
     if (e == cudaSuccess) e = mark(f, 5, s);
     return e;
@@ -145,6 +145,9 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
     }
     if (d->capacity < 1 || d->capacity > kMaxCapacity)
         return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: capacity outside [1, 2^30)");
+    if ((d->param_mode != 0 && d->param_mode != 1) || (d->optimizer != 0 && d->optimizer != 1) ||
+        d->lr_halve_every < 0 || (d->optimizer == 1 && !(d->beta3 >= 0.f && d->beta3 < 1.f)))
+        return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: bad param_mode, optimizer, beta3 or lr_halve_every");
     if ((reinterpret_cast<uintptr_t>(d->params) & 15) != 0)
         return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: params must be 16-byte aligned");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -199,6 +202,8 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
         up256((size_t)d->n_images * 8),                         // 18 loss
         256,                                                    // 19 step, done
         up256(probe.bytes),                                     // 20 bin ws
+        d->optimizer == 1 ? up256((size_t)N * 32) : 0,          // 21 Adan n
+        d->optimizer == 1 ? up256((size_t)N * 32) : 0,          // 22 Adan g_prev
     };
     size_t total = 0;
     for (size_t x : sz) total += x;
@@ -246,6 +251,13 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
     f->adam.eps = d->eps;
     f->adam.step = f->step;
     f->adam.done = f->done;
+    f->adam.optimizer = d->optimizer;
+    f->adam.beta3 = d->beta3;
+    f->adam.lr_halve_every = d->lr_halve_every;
+    f->adam.n = d->optimizer == 1 ? reinterpret_cast<float*>(at(21)) : nullptr;
+    f->adam.g_prev = d->optimizer == 1 ? reinterpret_cast<float*>(at(22)) : nullptr;
+    f->adam.param_mode = d->param_mode;
+    f->B.param_mode = d->param_mode;
 
 #define FIT_TRY(x)                                      \
     do {                                                \
@@ -318,6 +330,8 @@ gi_status gi_fit_pointer(gi_fit* f, int32_t what, void** ptr) {
         case GI_FIT_STEP: *ptr = f->step; break;
         case GI_FIT_K: *ptr = f->k_dev; break;
         case GI_FIT_TARGET: *ptr = f->targets; break;
+        case GI_FIT_ADAN_N: *ptr = f->adam.n; break;
+        case GI_FIT_ADAN_GPREV: *ptr = f->adam.g_prev; break;
         default: return set_error(GI_ERR_INVALID_ARG, "gi_fit_pointer: unknown field %d", what);
     }
     return GI_OK;

@@ -104,6 +104,12 @@ struct AdamCfg {
     float beta1, beta2, eps;
     int32_t* step;  // device counter (1-based step of the update being made = *step + 1)
     uint32_t* done; // device counter for the last-block step increment
+    int32_t optimizer;       // 0: Adam; 1: Adan (beta1, beta2, beta3 decay m, v, n)
+    float beta3;             // Adan
+    int32_t lr_halve_every;  // every learning rate halves every this many steps; 0 = never
+    float* n;                // Adan: second moment of the extrapolated gradient [N][8]
+    float* g_prev;           // Adan: previous gradient [N][8]
+    int32_t param_mode;      // 1: params are the raw App. C.1 parameters (chain through the formation)
 };
 
 // Reduce partials per Gaussian, chain conic -> Cholesky; then either write
@@ -112,7 +118,8 @@ struct AdamCfg {
 cudaError_t launch_reduce(const float4* partial, const int64_t* pair_off, const int32_t* cnt,
                           int64_t capacity, int32_t n, const ParamsIn& P, float* g_means,
                           float* g_chol, float* g_color, float* g_conic, const AdamCfg* adam,
-                          float* params, float* m, float* v, float* grads_aos, cudaStream_t s);
+                          float* params, float* m, float* v, float* grads_aos, const Batch& B,
+                          cudaStream_t s);
 
 cudaError_t launch_vq_decode(const uint16_t* means16, const uint8_t* idx, const float* cb, int32_t n,
                              int32_t stages, int32_t cb_size, float* means, float* chol, float* color,

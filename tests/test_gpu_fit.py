@@ -140,6 +140,73 @@ def test_full_size_five_steps(gi):
     fit.close()
 
 
+def paper_raw(means, chol, color, W, H):
+    """Raw App. C.1 parameters giving these pixel-space Gaussians:
+    theta = atanh(2 mu / (W, H) - 1), Cholesky diagonal without its +0.5."""
+    u = np.clip(means.astype(np.float64) / [W, H] * 2 - 1, -0.999, 0.999)
+    theta = np.arctanh(u)
+    c = chol.astype(np.float32).copy()
+    c[:, 0] -= 0.5
+    c[:, 2] -= 0.5
+    return theta, c, color
+
+
+def run_paper_adan(gi, W, H, means, chol, color, target, T, steps, lr=1e-3, halve=0):
+    """Fits with the paper's parameterisation and Adan; at every step the
+    oracle runs at the GPU's own raw parameters, so each step's loss and
+    gradients are checked exactly, and the Adan update from the GPU's own
+    state is checked against the oracle's update."""
+    theta, craw, col = paper_raw(means, chol, color, W, H)
+    p0 = np.concatenate([theta, craw, col], axis=1).astype(np.float32)
+    fit = gi.Fit([torch.from_numpy(target).cuda()], [torch.from_numpy(p0).cuda()], tile=T, lr=(lr, lr, lr),
+                 param_mode="paper", optimizer="adan", lr_halve_every=halve)
+    n = p0.shape[0]
+    lrv = np.full((n, 8), lr)
+    for t in range(1, steps + 1):
+        pg = fit.params.cpu().numpy().astype(np.float64)
+        state = tuple(x.cpu().numpy().astype(np.float64) for x in (fit.adam_m, fit.adam_v, fit.adan_n, fit.adan_gprev))
+        r = oracle.paper_forward_backward(pg[:, 0:2], pg[:, 2:5].astype(np.float32), pg[:, 5:8].astype(np.float32),
+                                          target, T)
+        gr = r["grads_raw"]
+        g_ref = np.concatenate([gr["theta"], gr["chol"], gr["color"]], axis=1)
+        g_abs = np.concatenate([gr["abs_theta"], r["grads"]["abs"]["chol"], r["grads"]["abs"]["color"]], axis=1)
+        fit.step(1)
+        torch.cuda.synchronize()
+        assert fit.mse()[0] == pytest.approx(r["loss"], rel=1e-5)
+        g_gpu = fit.grads.cpu().numpy().astype(np.float64)
+        for sl in (slice(0, 2), slice(2, 5), slice(5, 8)):
+            s = np.abs(g_ref[:, sl]).max()
+            rel = GRAD_TOL * np.maximum(np.abs(g_ref[:, sl]), 1e-3 * s)
+            err = np.abs(g_gpu[:, sl] - g_ref[:, sl])
+            cond = (err > rel) & (err <= 16 * 2.0 ** -24 * g_abs[:, sl])
+            assert cond.mean() <= 1e-3, f"step {t}: {cond.sum()} elements need the conditioning bound"
+            assert np.all((err <= rel) | cond), f"step {t}: gradient outside tolerance, worst {(err / rel).max()}"
+        p_ref, _ = oracle.adan(pg, g_ref, state, t, oracle.lr_at(1.0, t, halve) * lrv)
+        p_new = fit.params.cpu().numpy().astype(np.float64)
+        close = np.abs(p_new - p_ref) <= 1e-5 * np.maximum(np.abs(p_ref), 1.0) + 1e-3 * lr
+        assert close.mean() > 0.999, f"step {t}: {np.sum(~close)} parameters off the oracle's Adan update"
+        assert np.all(np.abs(p_new - p_ref) <= 4 * lr + 1e-5 * np.maximum(np.abs(p_ref), 1.0))
+    return fit
+
+
+def test_paper_mode_adan_steps_track_oracle(gi):
+    W, H, T, n = 128, 96, 16, 800
+    target = synth.image(W, H, 25, n_blobs=20)
+    means, chol, color = synth.init_gaussians(n, W, H, 25)
+    fit = run_paper_adan(gi, W, H, means, chol, color, target, T, 5, halve=3)
+    assert int(fit.step_count.item()) == 5
+    fit.close()
+
+
+@pytest.mark.slow
+def test_paper_mode_adan_full_size(gi):
+    """The 768x512, 70k-Gaussian workload with the paper's parameterisation
+    and optimiser, first five steps."""
+    w = synth.workload("c1_768x512_70k")
+    fit = run_paper_adan(gi, w.W, w.H, w.means, w.chol, w.color, w.target, 16, 5)
+    fit.close()
+
+
 def test_graph_replay_equals_eager(gi):
     W, H, T, n = 160, 120, 16, 1500
     target = torch.from_numpy(synth.image(W, H, 22, n_blobs=20)).cuda()
