@@ -20,6 +20,8 @@ Parity status per function (pins live in ``tests/test_oracle_*.py``):
   adam ........ pinned (closed-form first step, torch.optim.Adam)
   paper_formation / paper_forward_backward ... pinned (finite differences
                 in theta and the raw Cholesky vector; inverse of atanh init)
+  rs_to_chol / rs_chain / rs_forward_backward ... pinned (Sigma rebuilt from
+                R S against L L^T; finite differences in theta, s1, s2)
   adan ........ pinned (closed-form first step, constant-gradient steps,
                 reduction to Adam's direction when b2 = 0)
   vq_decode ... pinned (IEEE float32 addition, zero residual codebook)
@@ -259,6 +261,68 @@ def paper_forward_backward(theta, chol_raw, color, target, T):
     g = r["grads"]
     r["grads_raw"] = {"theta": g["means"] * dmu, "chol": g["chol"], "color": g["color"],
                       "abs_theta": g["abs"]["means"] * np.abs(dmu)}
+    return r
+
+
+def rs_to_chol(rs):
+    """Rotation-scaling form (Sec. 3.1, Eq. 2-3): Sigma = (R S)(R S)^T with R
+    the rotation by theta and S = diag(s1, s2); returns the lower-triangular
+    Cholesky vector of the same Sigma (FP64, each entry rounded once to FP32):
+      Sigma11 = c^2 s1^2 + s^2 s2^2, Sigma12 = c s (s1^2 - s2^2),
+      Sigma22 = s^2 s1^2 + c^2 s2^2,
+      l1 = sqrt(Sigma11), l2 = Sigma12 / l1, l3 = |s1 s2| / l1
+    (det Sigma = (s1 s2)^2 = (l1 l3)^2)."""
+    rs = np.asarray(rs, np.float64)
+    th, s1, s2 = rs[:, 0], rs[:, 1], rs[:, 2]
+    c, s = np.cos(th), np.sin(th)
+    S11 = c * c * s1 * s1 + s * s * s2 * s2
+    S12 = c * s * (s1 * s1 - s2 * s2)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        l1 = np.sqrt(S11)
+        l2 = S12 / l1
+        l3 = np.abs(s1 * s2) / l1
+    return np.stack([l1, l2, l3], axis=1).astype(np.float32)
+
+
+def rs_chain(rs, g_sigma):
+    """dL/d(theta, s1, s2) from dL/dSigma = [[g1, g2], [g2, g3]] (Sigma12 and
+    Sigma21 as separate entries, App. A.2's convention), FP64:
+    dL/dx = g1 dSigma11/dx + 2 g2 dSigma12/dx + g3 dSigma22/dx."""
+    rs = np.asarray(rs, np.float64)
+    th, s1, s2 = rs[:, 0], rs[:, 1], rs[:, 2]
+    c, s = np.cos(th), np.sin(th)
+    g1, g2, g3 = (np.asarray(g_sigma, np.float64)[:, i] for i in range(3))
+    d_th = g1 * 2 * c * s * (s2 * s2 - s1 * s1) + 2 * g2 * (c * c - s * s) * (s1 * s1 - s2 * s2) \
+        + g3 * 2 * c * s * (s1 * s1 - s2 * s2)
+    d_s1 = g1 * 2 * c * c * s1 + 2 * g2 * 2 * c * s * s1 + g3 * 2 * s * s * s1
+    d_s2 = g1 * 2 * s * s * s2 - 2 * g2 * 2 * c * s * s2 + g3 * 2 * c * c * s2
+    return np.stack([d_th, d_s1, d_s2], axis=1)
+
+
+def chol_to_sigma_grad(chol, g_chol):
+    """dL/dSigma (entries g1, g2, g3, App. A.2's convention) recovered from
+    dL/dl: the Cholesky chain dL/dl1 = 2 g1 l1 + 2 g2 l2, dL/dl2 = 2 g2 l1 +
+    2 g3 l2, dL/dl3 = 2 g3 l3 solved for (g1, g2, g3)."""
+    l = np.asarray(chol, np.float64)
+    gl = np.asarray(g_chol, np.float64)
+    g3 = gl[:, 2] / (2 * l[:, 2])
+    g2 = (gl[:, 1] - 2 * g3 * l[:, 1]) / (2 * l[:, 0])
+    g1 = (gl[:, 0] - 2 * g2 * l[:, 1]) / (2 * l[:, 0])
+    return np.stack([g1, g2, g3], axis=1)
+
+
+def rs_forward_backward(means, rs, color, target, T, shift=0.0):
+    """forward_backward for the rotation-scaling form (shift = 0.5 adds App.
+    C.1's +0.5 to s1, s2): Sigma's Cholesky vector from rs_to_chol, the
+    usual pass, then dL/dl -> dL/dSigma -> dL/d(theta, s1, s2)."""
+    r_ = np.asarray(rs, np.float64).copy()
+    r_[:, 1] += shift
+    r_[:, 2] += shift
+    chol = rs_to_chol(r_)
+    r = forward_backward(means, chol, color, target, T)
+    gs = chol_to_sigma_grad(chol, r["grads"]["chol"])
+    live = (r["cnt"] > 0)[:, None]
+    r["grads_rs"] = np.where(live, rs_chain(r_, np.nan_to_num(gs)), 0.0)
     return r
 
 

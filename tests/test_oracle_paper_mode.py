@@ -144,3 +144,56 @@ def test_lr_halving_schedule():
     assert oracle.lr_at(1e-3, 20001, 20000) == 5e-4
     assert oracle.lr_at(1e-3, 50000, 20000) == 2.5e-4
     assert oracle.lr_at(1e-3, 50000, 0) == 1e-3
+
+
+# --------------------------------------------------------------------------
+# Rotation-scaling factorisation (Sec. 3.1, Eq. 2-3)
+# --------------------------------------------------------------------------
+
+def test_rs_to_chol_rebuilds_sigma():
+    """L L^T of the returned Cholesky vector equals (R S)(R S)^T built with
+    numpy matrix products, for angles in every quadrant and both orders of
+    the scales."""
+    gen = np.random.default_rng(11)
+    rs = np.stack([gen.uniform(-4, 4, 300), gen.uniform(0.3, 9, 300), gen.uniform(0.3, 9, 300)], axis=1)
+    L = oracle.rs_to_chol(rs).astype(np.float64)
+    for i in range(300):
+        th, s1, s2 = rs[i]
+        R = np.array([[np.cos(th), -np.sin(th)], [np.sin(th), np.cos(th)]])
+        A = R @ np.diag([s1, s2])
+        Lm = np.array([[L[i, 0], 0.0], [L[i, 1], L[i, 2]]])
+        np.testing.assert_allclose(Lm @ Lm.T, A @ A.T, rtol=2e-6, atol=2e-6 * (A @ A.T).max())
+        assert L[i, 0] > 0 and L[i, 2] > 0
+
+
+@pytest.mark.parametrize("shift", [0.0, 0.5])
+def test_rs_gradients_match_finite_differences(shift):
+    """Central differences of the FP64 loss in (theta, s1, s2), support held
+    fixed, against the chained analytic gradients (shift = App. C.1's +0.5
+    on the scales)."""
+    W, H, T, n = 24, 20, 8, 6
+    means, _, col = synth.init_gaussians(n, W, H, 47)
+    gen = np.random.default_rng(47)
+    rs = np.stack([gen.uniform(-1.5, 1.5, n), gen.uniform(1.0, 5.0, n), gen.uniform(1.0, 5.0, n)], axis=1)
+    target = synth.image(W, H, 47, n_blobs=5)
+    r = oracle.rs_forward_backward(means, rs, col, target, T, shift=shift)
+    ids, ranges = r["ids"], r["ranges"]
+
+    def loss_at(x):
+        y = x.copy()
+        y[:, 1:] += shift
+        out = oracle.render(means, oracle.rs_to_chol(y), col, ids, ranges, W, H, T)
+        return oracle.loss(out, target)[0]
+
+    num = np.zeros_like(rs)
+    for idx in np.ndindex(rs.shape):
+        def central(h):
+            a, b = rs.copy(), rs.copy()
+            a[idx] += h
+            b[idx] -= h
+            return (loss_at(a) - loss_at(b)) / (2 * h)
+        # the render rounds the Cholesky vector to FP32: a step of 1e-2 keeps
+        # that rounding far below the signal; Richardson removes the h^2 term
+        h = 1e-2
+        num[idx] = (4 * central(h / 2) - central(h)) / 3
+    np.testing.assert_allclose(r["grads_rs"], num, rtol=3e-4, atol=1e-4 * np.abs(num).max())
