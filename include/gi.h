@@ -82,7 +82,8 @@ typedef struct {
  * exp(-sigma) = exp2(-(z1^2 + z2^2)) (Sec. 3.1 with Sigma^-1 = L^-T L^-1). */
 #define GI_REC_FLOATS 8
 
-/* ABI version: 2 (gi_fit_desc gained param_mode, optimizer, beta3, lr_halve_every). */
+/* ABI version: 3 (gi_fit_desc gained param_mode, optimizer, beta3, lr_halve_every in 2,
+ * cov_mode in 3). */
 GI_API int32_t gi_abi_version(void);
 GI_API const char* gi_last_error(void);
 GI_API const char* gi_status_string(int32_t status);
@@ -247,6 +248,11 @@ typedef struct {
     float beta3;          /* Adan only */
     int32_t lr_halve_every; /* every learning rate halves every this many steps (the paper:
                                20000); 0 = constant */
+    int32_t cov_mode;     /* 0: params slots 2..4 are the Cholesky vector (l1, l2, l3), Sec. 3.1;
+                             1: the rotation-scaling form (theta, s1, s2), Sigma = (R S)(R S)^T
+                             (Sec. 3.1, Eq. 2-3), mapped in FP64 to the Cholesky vector of the
+                             same Sigma; with param_mode 1 the +0.5 goes on s1 and s2 instead of
+                             the Cholesky diagonal */
 } gi_fit_desc;
 
 /* Allocates the context and copies targets and params (the caller's buffers

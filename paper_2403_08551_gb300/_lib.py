@@ -62,7 +62,7 @@ class GIFitDesc(ctypes.Structure):
                 ("params", P), ("tile", i32), ("lr_means", f32), ("lr_chol", f32), ("lr_color", f32),
                 ("beta1", f32), ("beta2", f32), ("eps", f32), ("capacity", i64), ("use_graph", i32),
                 ("stage_events", i32), ("render_split", i32), ("param_mode", i32), ("optimizer", i32),
-                ("beta3", f32), ("lr_halve_every", i32)]
+                ("beta3", f32), ("lr_halve_every", i32), ("cov_mode", i32)]
 
 
 class GIError(RuntimeError):

@@ -14,7 +14,7 @@ from . import _lib as L
 
 __all__ = ["project", "bin_tiles", "render", "render_backward", "vq_decode", "device_errors",
            "GIRender", "rasterize", "Fit", "Bins", "alu_peaks", "tiles", "autotune", "RENDER_SPLITS", "Renderer",
-           "selftest_bounded_waits", "paper_to_pixel", "ADAN_BETAS"]
+           "selftest_bounded_waits", "paper_to_pixel", "rs_to_chol", "ADAN_BETAS"]
 
 # Render splits (lane groups sharing one tile's list) available per tile edge.
 RENDER_SPLITS = {8: (2, 4), 16: (4, 8), 32: (1, 2)}
@@ -205,16 +205,35 @@ class _DevArray:
 ADAN_BETAS = (0.98, 0.92, 0.99)
 
 
-def paper_to_pixel(p, W: int, H: int):
+def paper_to_pixel(p, W: int, H: int, cov: str = "cholesky"):
     """Raw parameters of App. C.1 ([n,8]: theta, Cholesky without the +0.5 on
     its diagonal, colour) -> pixel-space parameters, as the formation kernel
-    maps them (tanh in FP64, one rounding to FP32)."""
+    maps them (tanh in FP64, one rounding to FP32). With cov="rs" the
+    covariance slots are (theta, s1, s2), the +0.5 goes on s1, s2 and the
+    result holds the Cholesky vector of the same Sigma."""
     q = p.clone()
     t = torch.tanh(p[:, 0:2].double())
     q[:, 0:2] = ((t + 1.0) * 0.5 * torch.tensor([W, H], dtype=torch.float64, device=p.device)).float()
-    q[:, 2] = p[:, 2] + 0.5
-    q[:, 4] = p[:, 4] + 0.5
+    if cov == "rs":
+        q[:, 2:5] = rs_to_chol(p[:, 2:5], 0.5)
+    else:
+        q[:, 2] = p[:, 2] + 0.5
+        q[:, 4] = p[:, 4] + 0.5
     return q
+
+
+def rs_to_chol(rs, shift: float = 0.0):
+    """Rotation-scaling covariance parameters ([n,3]: theta, s1, s2; Sec. 3.1,
+    Eq. 2-3, Sigma = (R S)(R S)^T) -> the Cholesky vector (l1, l2, l3) of the
+    same Sigma, in FP64 with one rounding, as the formation kernel maps them:
+    l1 = sqrt(Sigma11), l2 = Sigma12 / l1, l3 = |s1 s2| / l1. `shift` is
+    added to s1, s2 first (App. C.1's +0.5)."""
+    r = rs.double().clone()
+    r[:, 1:3] += shift
+    c, s = torch.cos(r[:, 0]), torch.sin(r[:, 0])
+    a, b = r[:, 1] * r[:, 1], r[:, 2] * r[:, 2]
+    l1 = torch.sqrt(c * c * a + s * s * b)
+    return torch.stack([l1, c * s * (a - b) / l1, torch.abs(r[:, 1] * r[:, 2]) / l1], dim=1).float()
 
 
 class Fit:
@@ -229,7 +248,7 @@ class Fit:
                  lr=(1e-3, 1e-2, 1e-2), betas=(0.9, 0.999), eps=1e-8, capacity: Optional[int] = None,
                  capacity_factor: float = 1.5, use_graph: bool = True, stage_events: bool = False,
                  render_split: int = 0, param_mode: str = "pixel", optimizer: str = "adam",
-                 lr_halve_every: int = 0):
+                 lr_halve_every: int = 0, cov: str = "cholesky"):
         lib = L.load()
         assert len(targets) == len(params) and len(targets) >= 1
         self.shapes = [(int(t.shape[1]), int(t.shape[0])) for t in targets]
@@ -238,9 +257,9 @@ class Fit:
         dev = targets[0].device
         tgt = torch.cat([_dev(t, torch.float32, "target").reshape(-1) for t in targets])
         prm = torch.cat([_dev(p, torch.float32, "params").reshape(-1, 8) for p in params]).contiguous()
-        if param_mode not in ("pixel", "paper") or optimizer not in ("adam", "adan"):
-            raise ValueError("param_mode must be 'pixel' or 'paper', optimizer 'adam' or 'adan'")
-        self.param_mode, self.optimizer = param_mode, optimizer
+        if param_mode not in ("pixel", "paper") or optimizer not in ("adam", "adan") or cov not in ("cholesky", "rs"):
+            raise ValueError("param_mode must be 'pixel' or 'paper', optimizer 'adam' or 'adan', cov 'cholesky' or 'rs'")
+        self.param_mode, self.optimizer, self.cov = param_mode, optimizer, cov
         if optimizer == "adan" and len(betas) != 3:
             betas = ADAN_BETAS
         K = None
@@ -249,7 +268,9 @@ class Fit:
             for (W, H), p in zip(self.shapes, params):
                 p = p.contiguous()
                 if param_mode == "paper":
-                    p = paper_to_pixel(p, W, H)
+                    p = paper_to_pixel(p, W, H, cov)
+                elif cov == "rs":
+                    p = torch.cat([p[:, 0:2], rs_to_chol(p[:, 2:5]), p[:, 5:8]], dim=1)
                 rec, rect, cnt = project(p[:, 0:2].contiguous(), p[:, 2:5].contiguous(), p[:, 5:8].contiguous(),
                                          W, H, tile)
                 K += bin_tiles(rect, cnt, None, W, H, tile).K
@@ -272,7 +293,7 @@ class Fit:
                            lr[0], lr[1], lr[2], betas[0], betas[1], eps, self.capacity, int(use_graph),
                            int(stage_events), int(render_split), int(param_mode == "paper"),
                            int(optimizer == "adan"), float(betas[2]) if optimizer == "adan" else 0.0,
-                           int(lr_halve_every))
+                           int(lr_halve_every), int(cov == "rs"))
         h = ctypes.c_void_p()
         L.check(lib.gi_fit_create(ctypes.byref(desc), L.stream_handle(), ctypes.byref(h)), "gi_fit_create")
         self._h_fit = h
@@ -329,7 +350,7 @@ class Fit:
         torch.cuda.current_stream().synchronize()
         sd = {"params": self.params.clone(), "adam_m": self.adam_m.clone(), "adam_v": self.adam_v.clone(),
               "step": int(self.step_count.item()), "shapes": list(self.shapes), "counts": list(self.counts),
-              "tile": self.tile, "param_mode": self.param_mode, "optimizer": self.optimizer}
+              "tile": self.tile, "param_mode": self.param_mode, "optimizer": self.optimizer, "cov": self.cov}
         if self.optimizer == "adan":
             sd["adan_n"] = self.adan_n.clone()
             sd["adan_gprev"] = self.adan_gprev.clone()
@@ -340,7 +361,7 @@ class Fit:
         counts and tile edge; the next steps continue bit-identically."""
         if list(sd["shapes"]) != list(self.shapes) or list(sd["counts"]) != list(self.counts) or \
                 sd["tile"] != self.tile or sd.get("param_mode", "pixel") != self.param_mode or \
-                sd.get("optimizer", "adam") != self.optimizer:
+                sd.get("optimizer", "adam") != self.optimizer or sd.get("cov", "cholesky") != self.cov:
             raise ValueError("checkpoint of a different fit (images, Gaussian counts, tile edge, "
                              "parameterisation or optimiser)")
         self.params.copy_(sd["params"])

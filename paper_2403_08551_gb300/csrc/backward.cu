@@ -291,9 +291,15 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
             *reinterpret_cast<float4*>(vv) = V4[0]; *reinterpret_cast<float4*>(vv + 4) = V4[1];
         }
         float l1 = P.chol[(int64_t)g * P.ls], l2 = P.chol[(int64_t)g * P.ls + 1], l3 = P.chol[(int64_t)g * P.ls + 2];
-        if (ADAM && cfg.param_mode == 1) {  // App. C.1: the chain runs through l1 + 0.5, l3 + 0.5
-            l1 += 0.5f;
-            l3 += 0.5f;
+        const bool rs_mode = ADAM && cfg.cov_mode == 1;
+        if (ADAM && cfg.param_mode == 1) {  // App. C.1: +0.5 on the Cholesky diagonal or on the scales
+            if (rs_mode) {
+                l2 += 0.5f;
+                l3 += 0.5f;
+            } else {
+                l1 += 0.5f;
+                l3 += 0.5f;
+            }
         }
         const int c = cnt[g];
         const int64_t p0 = pair_off[g];
@@ -332,8 +338,23 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
         float gr[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         float gq[3] = {0.f, 0.f, 0.f};
         if (c > 0) {
-            const float s11 = l1 * l1, s12 = l1 * l2, s22 = l2 * l2 + l3 * l3;
-            const float dd = l1 * l3, det = dd * dd;
+            // Sigma: from the Cholesky vector, or in the rotation-scaling form
+            // (slots theta, s1, s2) from (R S)(R S)^T with det = (s1 s2)^2.
+            float s11, s12, s22, det, rc = 0.f, rsn = 0.f;
+            if (rs_mode) {
+                sincosf(l1, &rsn, &rc);
+                const float q1 = l2 * l2, q2 = l3 * l3, ds = l2 * l3;
+                s11 = rc * rc * q1 + rsn * rsn * q2;
+                s12 = rc * rsn * (q1 - q2);
+                s22 = rsn * rsn * q1 + rc * rc * q2;
+                det = ds * ds;
+            } else {
+                s11 = l1 * l1;
+                s12 = l1 * l2;
+                s22 = l2 * l2 + l3 * l3;
+                const float dd = l1 * l3;
+                det = dd * dd;
+            }
             const float A = s22 / det, Bc = -s12 / det, C = s11 / det;
             const float Sx = a[3], Sy = a[4], Sxx = a[5], Sxy = a[6], Syy = a[7];
             const float gA = -0.5f * Sxx, gB = -Sxy, gC = -0.5f * Syy;
@@ -346,9 +367,17 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
             const float g1 = -(QG11 * A + QG12 * Bc);
             const float g2 = -(QG11 * Bc + QG12 * C);
             const float g3 = -(QG21 * Bc + QG22 * C);
-            gr[2] = 2.f * (g1 * l1 + g2 * l2);
-            gr[3] = 2.f * (g2 * l1 + g3 * l2);
-            gr[4] = 2.f * g3 * l3;
+            if (rs_mode) {
+                // dL/dx = g1 dSigma11/dx + 2 g2 dSigma12/dx + g3 dSigma22/dx, x = theta, s1, s2
+                const float q1 = l2 * l2, q2 = l3 * l3, cs2 = 2.f * rc * rsn;
+                gr[2] = cs2 * (q2 - q1) * g1 + 2.f * g2 * (rc * rc - rsn * rsn) * (q1 - q2) + cs2 * (q1 - q2) * g3;
+                gr[3] = 2.f * l2 * (rc * rc * g1 + 2.f * rc * rsn * g2 + rsn * rsn * g3);
+                gr[4] = 2.f * l3 * (rsn * rsn * g1 - 2.f * rc * rsn * g2 + rc * rc * g3);
+            } else {
+                gr[2] = 2.f * (g1 * l1 + g2 * l2);
+                gr[3] = 2.f * (g2 * l1 + g3 * l2);
+                gr[4] = 2.f * g3 * l3;
+            }
             gr[5] = a[0]; gr[6] = a[1]; gr[7] = a[2];
         }
         if (!ADAM) {

@@ -68,11 +68,34 @@ __global__ void __launch_bounds__(kProjBlock) k_project(ParamsIn P, Batch B, flo
         if (B.param_mode == 1) {
             // App. C.1: positions through tanh into (-1, 1), read as
             // mu = (tanh(theta) + 1) / 2 * (W, H) (tanh in FP64, one rounding
-            // to FP32); +0.5 on the Cholesky diagonal.
+            // to FP32); +0.5 on the Cholesky diagonal or on the scales.
             mx = (float)__dmul_rn(__dmul_rn(__dadd_rn(tanh((double)mx), 1.0), 0.5), (double)d.W);
             my = (float)__dmul_rn(__dmul_rn(__dadd_rn(tanh((double)my), 1.0), 0.5), (double)d.H);
-            l1 = __fadd_rn(l1, 0.5f);
-            l3 = __fadd_rn(l3, 0.5f);
+            if (B.cov_mode == 0) {
+                l1 = __fadd_rn(l1, 0.5f);
+                l3 = __fadd_rn(l3, 0.5f);
+            }
+        }
+        if (B.cov_mode == 1) {
+            // Rotation-scaling form (Sec. 3.1, Eq. 2-3): the slots hold
+            // (theta, s1, s2); the equivalent Cholesky vector of
+            // Sigma = (R S)(R S)^T, in FP64 with one rounding per entry:
+            // l1 = sqrt(Sigma11), l2 = Sigma12 / l1, l3 = |s1 s2| / l1.
+            const double th = (double)l1;
+            double s1 = (double)l2, s2 = (double)l3;
+            if (B.param_mode == 1) {
+                s1 = __dadd_rn(s1, 0.5);
+                s2 = __dadd_rn(s2, 0.5);
+            }
+            double sn, cs;
+            sincos(th, &sn, &cs);
+            const double S11 = __dadd_rn(__dmul_rn(__dmul_rn(__dmul_rn(cs, cs), s1), s1),
+                                         __dmul_rn(__dmul_rn(__dmul_rn(sn, sn), s2), s2));
+            const double S12 = __dmul_rn(__dmul_rn(cs, sn), __dsub_rn(__dmul_rn(s1, s1), __dmul_rn(s2, s2)));
+            const double q1 = __dsqrt_rn(S11);
+            l1 = (float)q1;
+            l2 = (float)__ddiv_rn(S12, q1);
+            l3 = (float)__ddiv_rn(fabs(__dmul_rn(s1, s2)), q1);
         }
         const float cr = P.color[(int64_t)g * P.cs], cg = P.color[(int64_t)g * P.cs + 1],
                     cb = P.color[(int64_t)g * P.cs + 2];

@@ -62,6 +62,8 @@ struct Batch {
     int32_t split;        // render: warp groups sharing one tile's list (0 = default for the tile edge)
     int32_t param_mode;   // 0: pixel-space parameters; 1: raw parameters of App. C.1 (tanh positions,
                           //    Cholesky diagonal + 0.5), formation maps them to pixel space
+    int32_t cov_mode;     // 0: covariance slots hold the Cholesky vector (l1, l2, l3);
+                          // 1: rotation-scaling form (theta, s1, s2), Sigma = (R S)(R S)^T
 };
 
 __device__ __forceinline__ ImgDesc img_desc(const Batch& b, int i) {

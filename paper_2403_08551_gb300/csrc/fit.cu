@@ -146,8 +146,10 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
     if (d->capacity < 1 || d->capacity > kMaxCapacity)
         return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: capacity outside [1, 2^30)");
     if ((d->param_mode != 0 && d->param_mode != 1) || (d->optimizer != 0 && d->optimizer != 1) ||
-        d->lr_halve_every < 0 || (d->optimizer == 1 && !(d->beta3 >= 0.f && d->beta3 < 1.f)))
-        return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: bad param_mode, optimizer, beta3 or lr_halve_every");
+        (d->cov_mode != 0 && d->cov_mode != 1) || d->lr_halve_every < 0 ||
+        (d->optimizer == 1 && !(d->beta3 >= 0.f && d->beta3 < 1.f)))
+        return set_error(GI_ERR_INVALID_ARG,
+                         "gi_fit_create: bad param_mode, cov_mode, optimizer, beta3 or lr_halve_every");
     if ((reinterpret_cast<uintptr_t>(d->params) & 15) != 0)
         return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: params must be 16-byte aligned");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
@@ -258,6 +260,8 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
     f->adam.g_prev = d->optimizer == 1 ? reinterpret_cast<float*>(at(22)) : nullptr;
     f->adam.param_mode = d->param_mode;
     f->B.param_mode = d->param_mode;
+    f->adam.cov_mode = d->cov_mode;
+    f->B.cov_mode = d->cov_mode;
 
 #define FIT_TRY(x)                                      \
     do {                                                \

@@ -110,6 +110,7 @@ struct AdamCfg {
     float* n;                // Adan: second moment of the extrapolated gradient [N][8]
     float* g_prev;           // Adan: previous gradient [N][8]
     int32_t param_mode;      // 1: params are the raw App. C.1 parameters (chain through the formation)
+    int32_t cov_mode;        // 1: covariance parameters are (theta, s1, s2) (chain dSigma -> theta, s1, s2)
 };
 
 // Reduce partials per Gaussian, chain conic -> Cholesky; then either write

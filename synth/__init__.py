@@ -144,6 +144,19 @@ def init_gaussians(n: int, W: int, H: int, seed: int):
     return means, chol, color
 
 
+def init_gaussians_rs(n: int, W: int, H: int, seed: int):
+    """Initial pixel-space parameters in the rotation-scaling form: means
+    [n,2], rs [n,3] (theta uniform in [-pi, pi), scales s1, s2 log-uniform
+    in [1, 8] like the Cholesky diagonal of init_gaussians), color [n,3]."""
+    means, _, color = init_gaussians(n, W, H, seed)
+    g = rng(seed + 700)
+    rs = np.empty((n, 3), np.float32)
+    rs[:, 0] = g.uniform(-math.pi, math.pi, size=n)
+    rs[:, 1] = np.exp(g.uniform(0.0, math.log(8.0), size=n))
+    rs[:, 2] = np.exp(g.uniform(0.0, math.log(8.0), size=n))
+    return means, rs, color
+
+
 def skewed_means(means: np.ndarray, W: int, H: int, seed: int, frac: float = 0.3,
                  area: float = 0.1) -> np.ndarray:
     """Move ``frac`` of the means uniformly into a seeded axis-aligned rectangle

@@ -1,0 +1,165 @@
+"""GPU fitting in the rotation-scaling covariance form (Sec. 3.1, Eq. 2-3):
+the covariance slots hold (theta, s1, s2). At every step the oracle is
+evaluated at the GPU's own parameters, so each step's loss and gradients
+with respect to (theta, s1, s2) are checked exactly, and the optimiser's
+update from the GPU's own state is checked against the oracle's."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GRAD_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def gi():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2403_08551_gb300 as m
+    m.load()
+    return m
+
+
+def rs_abs(rs_eff, chol, g_chol, g_abs_chol):
+    """Condition magnitude of dL/d(theta, s1, s2) in FP32: the Cholesky
+    gradient's own magnitude carried through the (linear) chain
+    dL/dl -> dL/dSigma -> dL/d(theta, s1, s2), plus the chain's terms taken
+    in absolute value (the rounding of its FP32 evaluation)."""
+    n = chol.shape[0]
+    prop = np.zeros((n, 3))
+    for k in range(3):
+        e = np.zeros((n, 3))
+        e[:, k] = 1.0
+        prop += np.abs(oracle.rs_chain(rs_eff, oracle.chol_to_sigma_grad(chol, e))) * g_abs_chol[:, k:k + 1]
+    gs = np.abs(np.nan_to_num(oracle.chol_to_sigma_grad(chol, g_chol)))
+    th, s1, s2 = (np.asarray(rs_eff, np.float64)[:, i] for i in range(3))
+    c, s = np.abs(np.cos(th)), np.abs(np.sin(th))
+    ab = s1 * s1 + s2 * s2
+    t_th = (gs[:, 0] + gs[:, 2]) * 2 * c * s * ab + 2 * gs[:, 1] * np.abs(c * c - s * s) * ab
+    t_s1 = 2 * np.abs(s1) * (c * c * gs[:, 0] + 2 * c * s * gs[:, 1] + s * s * gs[:, 2])
+    t_s2 = 2 * np.abs(s2) * (s * s * gs[:, 0] + 2 * c * s * gs[:, 1] + c * c * gs[:, 2])
+    return prop + np.stack([t_th, t_s1, t_s2], axis=1)
+
+
+def oracle_step(pg, target, T, paper):
+    """Oracle loss, gradients and their condition magnitudes at the
+    parameters pg ([n,8] FP64: position or theta, (theta, s1, s2), colour)."""
+    H, W, _ = target.shape
+    color = pg[:, 5:8].astype(np.float32)
+    rs = pg[:, 2:5].astype(np.float32).astype(np.float64)
+    if paper:
+        means, _, dmu = oracle.paper_formation(pg[:, 0:2], np.zeros((pg.shape[0], 3), np.float32), W, H)
+    else:
+        means, dmu = pg[:, 0:2].astype(np.float32), np.ones((pg.shape[0], 2))
+    shift = 0.5 if paper else 0.0
+    r = oracle.rs_forward_backward(means, rs, color, target, T, shift=shift)
+    rs_eff = rs.copy()
+    rs_eff[:, 1:3] += shift
+    chol = oracle.rs_to_chol(rs_eff)
+    g = r["grads"]
+    live = (r["cnt"] > 0)[:, None]
+    g_ref = np.concatenate([g["means"] * dmu, r["grads_rs"], g["color"]], axis=1)
+    a_rs = np.where(live, rs_abs(rs_eff, chol, g["chol"], g["abs"]["chol"]), 0.0)
+    g_abs = np.concatenate([g["abs"]["means"] * np.abs(dmu), a_rs, g["abs"]["color"]], axis=1)
+    return r["loss"], g_ref, g_abs
+
+
+def check_grads(g_gpu, g_ref, g_abs, t):
+    """Per group: within GRAD_TOL relative (floor 1e-3 of the group's
+    largest), or within the FP32 conditioning bound 16 eps g_abs. The bound
+    may carry at most 0.2% of the position and colour gradients (this
+    initialisation draws both scales independently over [1, 8] at any
+    angle, so it holds more elongated Gaussians, whose position sums cancel
+    more, than the Cholesky one: 0.104% of the 70k-Gaussian positions
+    needed it at step 5); the (theta, s1, s2) group may use it for 1%:
+    dL/dtheta carries the factor s1^2 - s2^2 (Eq. 2-3), which cancels for
+    nearly round Gaussians, so there the gradient is ill-conditioned by
+    (s1^2 + s2^2) / |s1^2 - s2^2|."""
+    for sl, frac in ((slice(0, 2), 2e-3), (slice(2, 5), 1e-2), (slice(5, 8), 2e-3)):
+        s = np.abs(g_ref[:, sl]).max()
+        rel = GRAD_TOL * np.maximum(np.abs(g_ref[:, sl]), 1e-3 * s)
+        err = np.abs(g_gpu[:, sl] - g_ref[:, sl])
+        cond = (err > rel) & (err <= 16 * 2.0 ** -24 * g_abs[:, sl])
+        assert cond.mean() <= frac, f"step {t}: {cond.sum()} elements need the conditioning bound"
+        assert np.all((err <= rel) | cond), f"step {t}: gradient outside tolerance, worst {(err / rel).max()}"
+
+
+def run_rs(gi, target, p0, T, steps, paper, optimizer, lr=(1e-3, 1e-2, 1e-2), halve=0):
+    """Fits in the rotation-scaling form and checks every step against the
+    oracle at the GPU's own parameters and optimiser state."""
+    H, W, _ = target.shape
+    n = p0.shape[0]
+    fit = gi.Fit([torch.from_numpy(target).cuda()], [torch.from_numpy(p0).cuda()], tile=T, lr=lr,
+                 param_mode="paper" if paper else "pixel", optimizer=optimizer, lr_halve_every=halve, cov="rs")
+    lrv = np.tile(np.array([lr[0]] * 2 + [lr[1]] * 3 + [lr[2]] * 3), (n, 1))
+    for t in range(1, steps + 1):
+        pg = fit.params.cpu().numpy().astype(np.float64)
+        views = (fit.adam_m, fit.adam_v) + ((fit.adan_n, fit.adan_gprev) if optimizer == "adan" else ())
+        state = tuple(x.cpu().numpy().astype(np.float64) for x in views)
+        loss, g_ref, g_abs = oracle_step(pg, target, T, paper)
+        fit.step(1)
+        torch.cuda.synchronize()
+        assert fit.mse()[0] == pytest.approx(loss, rel=1e-5)
+        check_grads(fit.grads.cpu().numpy().astype(np.float64), g_ref, g_abs, t)
+        lr_t = oracle.lr_at(1.0, t, halve) * lrv
+        if optimizer == "adan":
+            p_ref, _ = oracle.adan(pg, g_ref, state, t, lr_t)
+        else:
+            p_ref, _, _ = oracle.adam(pg, g_ref, state[0], state[1], t, lr_t)
+        p_new = fit.params.cpu().numpy().astype(np.float64)
+        close = np.abs(p_new - p_ref) <= 1e-5 * np.maximum(np.abs(p_ref), 1.0) + 1e-3 * lrv
+        assert close.mean() > 0.999, f"step {t}: {np.sum(~close)} parameters off the oracle's update"
+        bound = (4 if optimizer == "adan" else 2) * lrv
+        assert np.all(np.abs(p_new - p_ref) <= bound + 1e-5 * np.maximum(np.abs(p_ref), 1.0))
+    assert int(fit.step_count.item()) == steps
+    return fit
+
+
+def test_rs_pixel_adam_steps_track_oracle(gi):
+    W, H, T, n = 128, 96, 16, 800
+    target = synth.image(W, H, 31, n_blobs=20)
+    means, rs, color = synth.init_gaussians_rs(n, W, H, 31)
+    p0 = np.concatenate([means, rs, color], axis=1).astype(np.float32)
+    run_rs(gi, target, p0, T, 5, paper=False, optimizer="adam").close()
+
+
+def test_rs_paper_adan_steps_track_oracle(gi):
+    W, H, T, n = 160, 112, 16, 1200
+    target = synth.image(W, H, 32, n_blobs=24)
+    means, rs, color = synth.init_gaussians_rs(n, W, H, 32)
+    theta = np.arctanh(np.clip(means.astype(np.float64) / [W, H] * 2 - 1, -0.999, 0.999))
+    rs_raw = rs.copy()
+    rs_raw[:, 1:3] -= 0.5
+    p0 = np.concatenate([theta, rs_raw, color], axis=1).astype(np.float32)
+    run_rs(gi, target, p0, T, 5, paper=True, optimizer="adan", lr=(1e-3, 1e-3, 1e-3), halve=3).close()
+
+
+@pytest.mark.slow
+def test_rs_paper_adan_full_size(gi):
+    """The 768x512, 70k-Gaussian workload in the rotation-scaling form with
+    the paper's parameterisation and optimiser, first five steps."""
+    w = synth.workload("c1_768x512_70k")
+    means, rs, color = synth.init_gaussians_rs(w.n, w.W, w.H, 33)
+    theta = np.arctanh(np.clip(w.means.astype(np.float64) / [w.W, w.H] * 2 - 1, -0.999, 0.999))
+    rs_raw = rs.copy()
+    rs_raw[:, 1:3] -= 0.5
+    p0 = np.concatenate([theta, rs_raw, w.color], axis=1).astype(np.float32)
+    run_rs(gi, w.target, p0, 16, 5, paper=True, optimizer="adan", lr=(1e-3, 1e-3, 1e-3)).close()
+
+
+def test_rs_checkpoint_mismatch_is_refused(gi):
+    W, H, n = 64, 64, 200
+    target = torch.from_numpy(synth.image(W, H, 34, n_blobs=8)).cuda()
+    means, rs, color = synth.init_gaussians_rs(n, W, H, 34)
+    p0 = torch.from_numpy(np.concatenate([means, rs, color], axis=1).astype(np.float32)).cuda()
+    a = gi.Fit([target], [p0], tile=16, cov="rs")
+    b = gi.Fit([target], [p0], tile=16)
+    a.step(2)
+    with pytest.raises(ValueError):
+        b.load_state_dict(a.state_dict())
+    a.close()
+    b.close()
