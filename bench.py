@@ -262,23 +262,30 @@ def batched_vs_plain(gi, torch, n_images, steps, stream):
             "mean_psnr_db_plain": sum(psnr(b) for b in mse_p) / len(mse_p)}
 
 
-def long_fit(gi, torch, stream, T, steps, log_path=None, every=5000, paper=False):
+def long_fit(gi, torch, stream, T, steps, log_path=None, every=5000, paper=False, cov="cholesky"):
     """The full-length fit of the 768x512, 70k-Gaussian workload: `steps`
     graph-replayed steps (no L2 flush: steady state) in chunks of `every`,
     each timed with CUDA events; PSNR of the first step's render and after
     every chunk (also written as JSON lines to log_path). The pair capacity
-    leaves room for the Gaussians to grow."""
+    leaves room for the Gaussians to grow. With cov="rs" the covariance is
+    fitted in the rotation-scaling form (Sec. 3.1, Eq. 2-3), starting from
+    angles uniform in [-pi, pi) and scales log-uniform in [1, 8]."""
     w = synth.workload(WORKLOAD)
     if paper:
         # App. C.1 / Sec. 4.1: raw parameters (theta = atanh(2 mu / (W, H) - 1),
-        # Cholesky diagonal without its +0.5), Adan, lr 1e-3 halved every 20000.
+        # Cholesky diagonal or scales without their +0.5), Adan, lr 1e-3
+        # halved every 20000.
         p = pack(w).astype(np.float64)
         p[:, 0:2] = np.arctanh(np.clip(p[:, 0:2] / [w.W, w.H] * 2 - 1, -0.999, 0.999))
-        p[:, 2] -= 0.5
-        p[:, 4] -= 0.5
+        if cov == "rs":
+            p[:, 2:5] = synth.init_gaussians_rs(w.n, w.W, w.H, 0)[1]
+            p[:, 3:5] -= 0.5
+        else:
+            p[:, 2] -= 0.5
+            p[:, 4] -= 0.5
         fit = gi.Fit([torch.from_numpy(w.target).cuda()], [torch.from_numpy(p.astype(np.float32)).cuda()], tile=T,
                      lr=(1e-3, 1e-3, 1e-3), capacity_factor=4.0, param_mode="paper", optimizer="adan",
-                     lr_halve_every=20000)
+                     lr_halve_every=20000, cov=cov)
     else:
         fit = gi.Fit([torch.from_numpy(w.target).cuda()], [torch.from_numpy(pack(w)).cuda()], tile=T, lr=LR,
                      capacity_factor=4.0)
@@ -558,6 +565,9 @@ def main():
                                    os.path.join(args.out, "fit_long_psnr.jsonl"))
         out["fit_long_paper_recipe"] = long_fit(gi, torch, stream, T, args.long_steps,
                                                 os.path.join(args.out, "fit_long_paper_psnr.jsonl"), paper=True)
+        out["fit_long_paper_recipe_rs"] = long_fit(gi, torch, stream, T, args.long_steps,
+                                                   os.path.join(args.out, "fit_long_paper_rs_psnr.jsonl"),
+                                                   paper=True, cov="rs")
     if not args.no_cpu and rank == 0:
         out["cpu_baseline"] = cpu_baseline(w, T)
         out["cpu_baseline"]["oracle_c0"] = oracle_c0_times()

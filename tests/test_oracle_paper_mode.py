@@ -197,3 +197,28 @@ def test_rs_gradients_match_finite_differences(shift):
         h = 1e-2
         num[idx] = (4 * central(h / 2) - central(h)) / 3
     np.testing.assert_allclose(r["grads_rs"], num, rtol=3e-4, atol=1e-4 * np.abs(num).max())
+
+
+def test_rs_special_cases():
+    """Closed forms of Eq. 2-3: theta = 0 gives Sigma = diag(s1^2, s2^2), so
+    L = (|s1|, 0, |s2|); a round Gaussian (s1 = s2) has L = (s, 0, s) at any
+    angle and dL/dtheta = 0; theta and theta + pi give the same Sigma and
+    the same chained gradient."""
+    gen = np.random.default_rng(12)
+    s = np.stack([gen.uniform(0.3, 9, 50), gen.uniform(0.3, 9, 50)], axis=1)
+    L0 = oracle.rs_to_chol(np.stack([np.zeros(50), s[:, 0], s[:, 1]], axis=1))
+    np.testing.assert_array_equal(L0, np.stack([s[:, 0], np.zeros(50), s[:, 1]], axis=1).astype(np.float32))
+    th = gen.uniform(-4, 4, 50)
+    Lr = oracle.rs_to_chol(np.stack([th, s[:, 0], s[:, 0]], axis=1)).astype(np.float64)
+    np.testing.assert_allclose(Lr[:, 0], s[:, 0], rtol=1e-7)
+    np.testing.assert_allclose(Lr[:, 2], s[:, 0], rtol=1e-7)
+    assert np.all(np.abs(Lr[:, 1]) <= 1e-6 * s[:, 0])
+    g_sigma = gen.normal(size=(50, 3))
+    g_round = oracle.rs_chain(np.stack([th, s[:, 0], s[:, 0]], axis=1), g_sigma)
+    np.testing.assert_array_equal(g_round[:, 0], 0.0)
+    rs = np.stack([th, s[:, 0], s[:, 1]], axis=1)
+    rs_pi = rs.copy()
+    rs_pi[:, 0] += np.pi
+    np.testing.assert_allclose(oracle.rs_to_chol(rs_pi), oracle.rs_to_chol(rs), rtol=1e-6, atol=1e-6)
+    np.testing.assert_allclose(oracle.rs_chain(rs_pi, g_sigma), oracle.rs_chain(rs, g_sigma), rtol=1e-9,
+                               atol=1e-9 * np.abs(oracle.rs_chain(rs, g_sigma)).max())
