@@ -26,6 +26,12 @@ Parity status per function (pins live in ``tests/test_oracle_*.py``):
                 reduction to Adam's direction when b2 = 0)
   vq_decode ... pinned (IEEE float32 addition, zero residual codebook)
   rvq_encode .. pinned (exhaustive per-stage argmin)
+  fp16_round / lsq_fake_quant / lsq_ste_grads / rvq_assign_f32 /
+  commitment_loss / ema_codebook_update / codec_forward_backward ... pinned
+                (struct half packing; brute-force nearest grid point;
+                finite differences of the straight-through surrogate;
+                brute-force nearest entry; zero-residual closed form;
+                cluster means at decay 0; identity quantisers)
 """
 from __future__ import annotations
 
@@ -409,3 +415,158 @@ def psnr(out, target):
     o = np.clip(np.asarray(out, np.float64), 0.0, 1.0)
     mse = np.mean((o - np.asarray(target, np.float64)) ** 2)
     return float(10.0 * np.log10(1.0 / mse)) if mse > 0 else float("inf")
+
+
+# ---------------------------------------------------------------------------
+# Codec fine-tuning (Sec. 3.3 attribute quantisation-aware fine-tuning,
+# Sec. 3.4 total loss). Every decision that yields an integer (a half-precision
+# rounding, a quantiser code, an RVQ index) is taken in FP32 with one rounding
+# per operation, the precision the GPU takes it in; sums are FP64.
+# ---------------------------------------------------------------------------
+
+def fp16_round(x):
+    """Positions stored at 16-bit float precision (Sec. 3.3): FP32 -> FP16
+    (round to nearest even) -> FP32."""
+    return np.asarray(x, np.float32).astype(np.float16).astype(np.float32)
+
+
+def lsq_fake_quant(l, gamma, beta, bits):
+    """b-bit asymmetric quantiser of the Cholesky vector (Sec. 3.3, the LSQ+
+    form): x = (l_i - beta_i) / gamma_i, code = round(clamp(x, 0, 2^b - 1))
+    (half to even), l_bar = code * gamma_i + beta_i; gamma, beta are shared
+    by all Gaussians, one pair per component i.
+    l [n,3]; gamma, beta [3]. Returns (l_bar f32 [n,3], x f32 [n,3],
+    code f32 [n,3]); a non-finite x gives a non-finite l_bar and code."""
+    l = np.asarray(l, np.float32)
+    g = np.asarray(gamma, np.float32)
+    b = np.asarray(beta, np.float32)
+    qp = np.float32(2 ** bits - 1)
+    with np.errstate(all="ignore"):
+        x = (l - b) / g
+        xc = np.where(x < 0, np.float32(0), np.where(x > qp, qp, x)).astype(np.float32)
+        q = np.rint(xc).astype(np.float32)
+        lbar = (q * g + b).astype(np.float32)
+    return lbar, x.astype(np.float32), q
+
+
+def lsq_ste_grads(g_lbar, x, q, bits):
+    """Gradients of the quantiser with the straight-through estimator
+    (d round(x)/dx taken as 1, the LSQ+ convention): inside the clamp range
+    dl_bar/dl = 1, dl_bar/dgamma = code - x, dl_bar/dbeta = 0; below it
+    l_bar = beta (0, 0, 1); above it l_bar = (2^b - 1) gamma + beta
+    (0, 2^b - 1, 1). Returns (dL/dl [n,3], dL/dgamma [3], dL/dbeta [3]),
+    FP64; a non-finite x contributes nothing."""
+    g = np.asarray(g_lbar, np.float64)
+    x = np.asarray(x, np.float64)
+    q = np.asarray(q, np.float64)
+    qp = float(2 ** bits - 1)
+    inside = (x >= 0) & (x <= qp)
+    below = x < 0
+    above = x > qp
+    g_l = np.where(inside, g, 0.0)
+    g_gamma = np.where(inside, g * (q - np.where(inside, x, 0.0)), np.where(above, g * qp, 0.0)).sum(axis=0)
+    g_beta = np.where(below | above, g, 0.0).sum(axis=0)
+    return g_l, g_gamma, g_beta
+
+
+def rvq_assign_f32(c, codebooks):
+    """Greedy residual VQ of the colour coefficients (Sec. 3.3, Eq. 10) with
+    FP32 decisions: r^0 = c'; stage m takes the entry j minimising
+    ((C_j0 - r_0)^2 + (C_j1 - r_1)^2) + (C_j2 - r_2)^2 (each operation
+    rounded to FP32), scanning j upward and moving only on a strictly smaller
+    distance (lowest index on ties; a NaN distance never wins, so an
+    all-NaN stage picks 0); r^m = r^{m-1} - C^m[i^m] in FP32.
+    c [n,3], codebooks [M][B][3]. Returns (idx [M][n] int64, c_hat f32 [n,3]
+    = sum over stages of the chosen entries in FP64 rounded once,
+    r_in f32 [M][n][3] = the residual each stage quantised)."""
+    c = np.asarray(c, np.float32)
+    cb = np.asarray(codebooks, np.float32)
+    M, Bn = cb.shape[0], cb.shape[1]
+    n = c.shape[0]
+    r = c.copy()
+    idx = np.zeros((M, n), np.int64)
+    r_in = np.zeros((M, n, 3), np.float32)
+    with np.errstate(all="ignore"):
+        for m in range(M):
+            r_in[m] = r
+            best = np.zeros(n, np.int64)
+            bd = None
+            for j in range(Bn):
+                e = (cb[m, j][None, :] - r).astype(np.float32)
+                d = ((e[:, 0] * e[:, 0] + e[:, 1] * e[:, 1]) + e[:, 2] * e[:, 2]).astype(np.float32)
+                if bd is None:
+                    bd = d
+                    continue
+                take = d < bd
+                best = np.where(take, j, best)
+                bd = np.where(take, d, bd)
+            idx[m] = best
+            r = (r - cb[m][best]).astype(np.float32)
+    chat = np.zeros((n, 3), np.float64)
+    for m in range(M):
+        chat = chat + cb[m][idx[m]].astype(np.float64)
+    return idx, chat.astype(np.float32), r_in
+
+
+def commitment_loss(r_in, codebooks, idx):
+    """Commitment loss (Sec. 3.3, Eq. 11): L_c = 1/(N B) sum over stages m
+    and Gaussians n of || r_n^{m-1} - C^m[i_n^m] ||^2, r^{m-1} = c' minus the
+    first m-1 stages' entries (the stop-gradient operand). FP64."""
+    r_in = np.asarray(r_in, np.float64)
+    cb = np.asarray(codebooks, np.float32).astype(np.float64)
+    M, Bn = cb.shape[0], cb.shape[1]
+    n = r_in.shape[1]
+    if n == 0:
+        return 0.0
+    tot = 0.0
+    for m in range(M):
+        tot += float(((r_in[m] - cb[m][np.asarray(idx[m])]) ** 2).sum())
+    return tot / (n * Bn)
+
+
+def ema_codebook_update(count, total, idx, r_in, decay, eps):
+    """Exponential-moving-average codebook update (Sec. 3.4): per stage m and
+    entry j, with n_j Gaussians assigned and s_j the sum of their residuals
+    r^{m-1}: count_j <- d count_j + (1 - d) n_j, total_j <- d total_j +
+    (1 - d) s_j; the count is Laplace-smoothed, N_j = (count_j + eps) /
+    (sum count + B eps) * sum count, and C_j = total_j / N_j.
+    count [M][B], total [M][B][3], idx [M][n], r_in [M][n][3]. Returns
+    (count, total, codebooks), FP64."""
+    count = np.asarray(count, np.float64).copy()
+    total = np.asarray(total, np.float64).copy()
+    r_in = np.asarray(r_in, np.float64)
+    M, Bn = count.shape
+    cb = np.zeros((M, Bn, 3))
+    for m in range(M):
+        n_j = np.bincount(np.asarray(idx[m]), minlength=Bn).astype(np.float64)
+        s_j = np.zeros((Bn, 3))
+        np.add.at(s_j, np.asarray(idx[m]), r_in[m])
+        count[m] = decay * count[m] + (1.0 - decay) * n_j
+        total[m] = decay * total[m] + (1.0 - decay) * s_j
+        tot = count[m].sum()
+        smoothed = (count[m] + eps) / (tot + Bn * eps) * tot
+        with np.errstate(all="ignore"):
+            cb[m] = total[m] / smoothed[:, None]
+    return count, total, cb
+
+
+def codec_forward_backward(means, chol, color, gamma, beta, codebooks, bits, target, T):
+    """One fine-tuning pass (Sec. 3.3): the render sees FP16 positions, the
+    quantised Cholesky vector and the RVQ colour; gradients pass straight
+    through the FP16 rounding and the RVQ (dL/dc' = dL/dc_hat) and through
+    the quantiser as lsq_ste_grads. means, chol are the pixel-space values
+    the quantisers act on. Returns forward_backward's dict plus "codec":
+    means16, chol_q, codes (uint8 [n,3]), x, idx, color_q, r_in, commit (L_c)
+    and grads {means, chol, color, gamma, beta}."""
+    mq = fp16_round(means)
+    lbar, x, q = lsq_fake_quant(chol, gamma, beta, bits)
+    idx, chat, r_in = rvq_assign_f32(color, codebooks)
+    r = forward_backward(mq, lbar, chat, target, T)
+    g = r["grads"]
+    g_l, g_gamma, g_beta = lsq_ste_grads(g["chol"], x, q, bits)
+    codes = np.where(np.isfinite(q), q, 0).astype(np.uint8)
+    r["codec"] = {"means16": mq, "chol_q": lbar, "codes": codes, "x": x, "idx": idx, "color_q": chat,
+                  "r_in": r_in, "commit": commitment_loss(r_in, codebooks, idx),
+                  "grads": {"means": g["means"], "chol": g_l, "color": g["color"], "gamma": g_gamma,
+                            "beta": g_beta}}
+    return r
