@@ -82,8 +82,8 @@ typedef struct {
  * exp(-sigma) = exp2(-(z1^2 + z2^2)) (Sec. 3.1 with Sigma^-1 = L^-T L^-1). */
 #define GI_REC_FLOATS 8
 
-/* ABI version: 3 (gi_fit_desc gained param_mode, optimizer, beta3, lr_halve_every in 2,
- * cov_mode in 3). */
+/* ABI version: 4 (gi_fit_desc gained param_mode, optimizer, beta3, lr_halve_every in 2,
+ * cov_mode in 3, the codec fine-tuning fields in 4). */
 GI_API int32_t gi_abi_version(void);
 GI_API const char* gi_last_error(void);
 GI_API const char* gi_status_string(int32_t status);
@@ -253,6 +253,24 @@ typedef struct {
                              (Sec. 3.1, Eq. 2-3), mapped in FP64 to the Cholesky vector of the
                              same Sigma; with param_mode 1 the +0.5 goes on s1 and s2 instead of
                              the Cholesky diagonal */
+    /* Attribute quantisation-aware fine-tuning (Sec. 3.3-3.4), one image only,
+       Cholesky form only. Each step renders FP16 positions, the b-bit quantised
+       Cholesky vector l_bar_i = round(clamp((l_i - beta_i)/gamma_i, 0, 2^b - 1))
+       gamma_i + beta_i (half to even; l is the pixel-space vector, after App.
+       C.1's +0.5 in param_mode 1) and the greedy M-stage RVQ colour (FP32
+       distances, lowest index on ties); gradients pass straight through the
+       FP16 rounding and the RVQ and through the quantiser inside its range;
+       gamma, beta take the optimiser's step at lr_chol; the codebooks follow
+       an exponential moving average of the residuals assigned to each entry
+       (count and sum start at 1 and the initial entry). */
+    int32_t codec_bits;       /* b in [1, 8]; 0 = off (the fields below are then ignored) */
+    int32_t codec_stages;     /* M in [1, 4] */
+    int32_t codec_size;       /* B in [1, 16] */
+    const float* codebooks;   /* device [M][B][3] initial colour codebooks (copied) */
+    float lsq_gamma[3];       /* initial gamma_i (> 0) */
+    float lsq_beta[3];        /* initial beta_i */
+    float ema_decay;          /* in [0, 1) */
+    float ema_eps;            /* Laplace smoothing of the counts (>= 0) */
 } gi_fit_desc;
 
 /* Allocates the context and copies targets and params (the caller's buffers
@@ -285,7 +303,15 @@ enum {
     GI_FIT_K = 7,
     GI_FIT_TARGET = 8,
     GI_FIT_ADAN_N = 9,     /* [N][8] Adan's third average (NULL pointer for Adam) */
-    GI_FIT_ADAN_GPREV = 10 /* [N][8] Adan's previous gradient (NULL pointer for Adam) */
+    GI_FIT_ADAN_GPREV = 10, /* [N][8] Adan's previous gradient (NULL pointer for Adam) */
+    /* codec fine-tuning (NULL pointers when codec_bits == 0): */
+    GI_FIT_CODEC_GB = 11,    /* f32 [5][6]: gamma[3], beta[3]; then the optimiser's m, v, n, g_prev */
+    GI_FIT_CODEBOOKS = 12,   /* f32 [M][B][3] current codebooks */
+    GI_FIT_EMA_COUNT = 13,   /* f64 [M][B] EMA counts */
+    GI_FIT_EMA_TOTAL = 14,   /* f64 [M][B][3] EMA residual sums */
+    GI_FIT_CODES = 15,       /* u8 [N][4] quantiser codes of the last step (4th byte 0) */
+    GI_FIT_RVQ_IDX = 16,     /* u8 [M][N] RVQ indices of the last step */
+    GI_FIT_CODEC_OUT = 17    /* f64 [7] last step: L_c, dL/dgamma[3], dL/dbeta[3] */
 };
 GI_API gi_status gi_fit_pointer(gi_fit* fit, int32_t what, void** ptr);
 GI_API gi_status gi_fit_destroy(gi_fit* fit);

@@ -26,7 +26,8 @@ STATUS = {0: "GI_OK", 1: "GI_ERR_INVALID_ARG", 2: "GI_ERR_CUDA", 3: "GI_ERR_CAPA
 DEVERR_CAPACITY, DEVERR_TIMEOUT, DEVERR_BOUNDS = 1, 2, 4
 
 (FIT_PARAMS, FIT_ADAM_M, FIT_ADAM_V, FIT_GRADS, FIT_OUT, FIT_LOSS, FIT_STEP, FIT_K, FIT_TARGET, FIT_ADAN_N,
- FIT_ADAN_GPREV) = range(11)
+ FIT_ADAN_GPREV, FIT_CODEC_GB, FIT_CODEBOOKS, FIT_EMA_COUNT, FIT_EMA_TOTAL, FIT_CODES, FIT_RVQ_IDX,
+ FIT_CODEC_OUT) = range(18)
 
 # Every symbol include/gi.h declares, with (restype, argtypes).
 SIGNATURES = {
@@ -62,7 +63,9 @@ class GIFitDesc(ctypes.Structure):
                 ("params", P), ("tile", i32), ("lr_means", f32), ("lr_chol", f32), ("lr_color", f32),
                 ("beta1", f32), ("beta2", f32), ("eps", f32), ("capacity", i64), ("use_graph", i32),
                 ("stage_events", i32), ("render_split", i32), ("param_mode", i32), ("optimizer", i32),
-                ("beta3", f32), ("lr_halve_every", i32), ("cov_mode", i32)]
+                ("beta3", f32), ("lr_halve_every", i32), ("cov_mode", i32), ("codec_bits", i32),
+                ("codec_stages", i32), ("codec_size", i32), ("codebooks", P), ("lsq_gamma", f32 * 3),
+                ("lsq_beta", f32 * 3), ("ema_decay", f32), ("ema_eps", f32)]
 
 
 class GIError(RuntimeError):

@@ -14,7 +14,7 @@ from . import _lib as L
 
 __all__ = ["project", "bin_tiles", "render", "render_backward", "vq_decode", "device_errors",
            "GIRender", "rasterize", "Fit", "Bins", "alu_peaks", "tiles", "autotune", "RENDER_SPLITS", "Renderer",
-           "selftest_bounded_waits", "paper_to_pixel", "rs_to_chol", "ADAN_BETAS"]
+           "selftest_bounded_waits", "paper_to_pixel", "rs_to_chol", "codec_init", "ADAN_BETAS"]
 
 # Render splits (lane groups sharing one tile's list) available per tile edge.
 RENDER_SPLITS = {8: (2, 4), 16: (4, 8), 32: (1, 2)}
@@ -203,6 +203,46 @@ class _DevArray:
 
 # Adan's decay factors of its three averages (Adan's 0.02, 0.08, 0.01).
 ADAN_BETAS = (0.98, 0.92, 0.99)
+CODEC_EMA_DECAY = 0.99  # codebook EMA decay (the paper gives none; the common VQ-VAE value)
+CODEC_EMA_EPS = 1e-5    # Laplace smoothing of the EMA counts
+
+
+def codec_init(params, bits: int = 6, stages: int = 2, size: int = 8, iters: int = 5, seed: int = 0,
+               param_mode: str = "pixel") -> dict:
+    """Starting point of the codec fine-tuning (Sec. 3.3-3.4, the paper's b = 6,
+    M = 2, B = 8, five K-means iterations), computed on the host once:
+    gamma_i, beta_i span the fitted Cholesky components (beta = min,
+    gamma = (max - min) / (2^b - 1)); each RVQ stage's codebook is K-means
+    (Lloyd, FP64, centroids started at `size` distinct Gaussians drawn with
+    `seed`, an empty cluster keeps its centroid) on the residual left by
+    the stages before it. params [n,8] as the fit holds them."""
+    import numpy as np
+    p = params.detach().cpu().numpy().astype(np.float64).reshape(-1, 8)
+    l = p[:, 2:5].copy()
+    if param_mode == "paper":
+        l[:, 0] += 0.5
+        l[:, 2] += 0.5
+    qp = 2 ** bits - 1
+    lo, hi = l.min(axis=0), l.max(axis=0)
+    gamma = np.where(hi > lo, (hi - lo) / qp, 1.0)
+    r = p[:, 5:8].copy()
+    gen = np.random.default_rng(seed)
+    cbs = np.zeros((stages, size, 3))
+    for m in range(stages):
+        cent = r[gen.permutation(r.shape[0])[:size]].copy()
+        if cent.shape[0] < size:
+            cent = np.concatenate([cent, np.zeros((size - cent.shape[0], 3))])
+        for _ in range(iters):
+            a = np.argmin(((r[:, None, :] - cent[None]) ** 2).sum(-1), axis=1)
+            for j in range(size):
+                sel = a == j
+                if sel.any():
+                    cent[j] = r[sel].mean(axis=0)
+        a = np.argmin(((r[:, None, :] - cent[None]) ** 2).sum(-1), axis=1)
+        r = r - cent[a]
+        cbs[m] = cent
+    return {"bits": bits, "codebooks": torch.from_numpy(cbs.astype(np.float32)).to(params.device),
+            "gamma": gamma.astype(np.float32).tolist(), "beta": lo.astype(np.float32).tolist()}
 
 
 def paper_to_pixel(p, W: int, H: int, cov: str = "cholesky"):
@@ -248,7 +288,7 @@ class Fit:
                  lr=(1e-3, 1e-2, 1e-2), betas=(0.9, 0.999), eps=1e-8, capacity: Optional[int] = None,
                  capacity_factor: float = 1.5, use_graph: bool = True, stage_events: bool = False,
                  render_split: int = 0, param_mode: str = "pixel", optimizer: str = "adam",
-                 lr_halve_every: int = 0, cov: str = "cholesky"):
+                 lr_halve_every: int = 0, cov: str = "cholesky", codec: Optional[dict] = None):
         lib = L.load()
         assert len(targets) == len(params) and len(targets) >= 1
         self.shapes = [(int(t.shape[1]), int(t.shape[0])) for t in targets]
@@ -294,6 +334,18 @@ class Fit:
                            int(stage_events), int(render_split), int(param_mode == "paper"),
                            int(optimizer == "adan"), float(betas[2]) if optimizer == "adan" else 0.0,
                            int(lr_halve_every), int(cov == "rs"))
+        self.codec = None
+        if codec is not None:
+            cb = _dev(codec["codebooks"], torch.float32, "codebooks").contiguous()
+            M, Bn = int(cb.shape[0]), int(cb.shape[1])
+            desc.codec_bits, desc.codec_stages, desc.codec_size = int(codec.get("bits", 6)), M, Bn
+            desc.codebooks = cb.data_ptr()
+            desc.lsq_gamma[:] = [float(x) for x in codec["gamma"]]
+            desc.lsq_beta[:] = [float(x) for x in codec["beta"]]
+            desc.ema_decay = float(codec.get("ema_decay", CODEC_EMA_DECAY))
+            desc.ema_eps = float(codec.get("ema_eps", CODEC_EMA_EPS))
+            self.codec = {"bits": desc.codec_bits, "stages": M, "size": Bn, "ema_decay": desc.ema_decay,
+                          "ema_eps": desc.ema_eps}
         h = ctypes.c_void_p()
         L.check(lib.gi_fit_create(ctypes.byref(desc), L.stream_handle(), ctypes.byref(h)), "gi_fit_create")
         self._h_fit = h
@@ -312,6 +364,15 @@ class Fit:
             self.adan_n = self._view(L.FIT_ADAN_N, (N, 8), "<f4")
             self.adan_gprev = self._view(L.FIT_ADAN_GPREV, (N, 8), "<f4")
         self.targets = self._view(L.FIT_TARGET, (npix * 3,), "<f4")
+        if self.codec is not None:
+            M, Bn = self.codec["stages"], self.codec["size"]
+            self.codec_gb = self._view(L.FIT_CODEC_GB, (5, 6), "<f4")  # gamma, beta; then m, v, n, g_prev
+            self.codebooks = self._view(L.FIT_CODEBOOKS, (M, Bn, 3), "<f4")
+            self.ema_count = self._view(L.FIT_EMA_COUNT, (M, Bn), "<f8")
+            self.ema_total = self._view(L.FIT_EMA_TOTAL, (M, Bn, 3), "<f8")
+            self.codes = self._view(L.FIT_CODES, (N, 4), "|u1")
+            self.rvq_idx = self._view(L.FIT_RVQ_IDX, (M, N), "|u1")
+            self.codec_out = self._view(L.FIT_CODEC_OUT, (7,), "<f8")
 
     def _view(self, what, shape, typestr):
         p = ctypes.c_void_p()
@@ -354,6 +415,10 @@ class Fit:
         if self.optimizer == "adan":
             sd["adan_n"] = self.adan_n.clone()
             sd["adan_gprev"] = self.adan_gprev.clone()
+        if self.codec is not None:
+            sd["codec"] = dict(self.codec)
+            for k in ("codec_gb", "codebooks", "ema_count", "ema_total"):
+                sd[k] = getattr(self, k).clone()
         return sd
 
     def load_state_dict(self, sd: dict):
@@ -361,7 +426,8 @@ class Fit:
         counts and tile edge; the next steps continue bit-identically."""
         if list(sd["shapes"]) != list(self.shapes) or list(sd["counts"]) != list(self.counts) or \
                 sd["tile"] != self.tile or sd.get("param_mode", "pixel") != self.param_mode or \
-                sd.get("optimizer", "adam") != self.optimizer or sd.get("cov", "cholesky") != self.cov:
+                sd.get("optimizer", "adam") != self.optimizer or sd.get("cov", "cholesky") != self.cov or \
+                sd.get("codec") != self.codec:
             raise ValueError("checkpoint of a different fit (images, Gaussian counts, tile edge, "
                              "parameterisation or optimiser)")
         self.params.copy_(sd["params"])
@@ -370,6 +436,9 @@ class Fit:
         if self.optimizer == "adan":
             self.adan_n.copy_(sd["adan_n"])
             self.adan_gprev.copy_(sd["adan_gprev"])
+        if self.codec is not None:
+            for k in ("codec_gb", "codebooks", "ema_count", "ema_total"):
+                getattr(self, k).copy_(sd[k])
         self.step_count.fill_(int(sd["step"]))
 
     def close(self):

@@ -241,12 +241,64 @@ __global__ void k_pack_dl(const float* __restrict__ dl, Batch B, float* __restri
 
 constexpr int kReduceThreads = 128;
 
+// Codec sums, stage 1 (Sec. 3.3-3.4): per block, dL/dgamma, dL/dbeta, the
+// commitment term and, per RVQ stage and codebook entry, the count and the
+// residual sum of the Gaussians assigned to it. Warp sums by butterfly, then
+// the block's warps in order: a fixed summation order, so the totals do not
+// depend on scheduling. Row v of Q.part holds value v of every block.
+__device__ void codec_block_partials(const CodecCfg& Q, const float (&gb)[6], const int (&jj)[kCodecMaxStages],
+                                     const float (&rr)[kCodecMaxStages][3], float commit) {
+    constexpr int kWarps = kReduceThreads / 32;
+    __shared__ float s_cv[kWarps][kCodecMaxVals];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nv = codec_nvals(Q);
+#pragma unroll
+    for (int v = 0; v < 6; ++v) {
+        const float w = warp_sum(gb[v]);
+        if (lane == 0) s_cv[warp][v] = w;
+    }
+    {
+        const float w = warp_sum(commit);
+        if (lane == 0) s_cv[warp][nv - 1] = w;
+    }
+#pragma unroll
+    for (int m = 0; m < kCodecMaxStages; ++m) {
+        if (m < Q.stages) {
+            for (int j = 0; j < Q.size; ++j) {
+                const bool mine = jj[m] == j;
+                const unsigned mask = __ballot_sync(0xffffffffu, mine);
+                float c0 = 0.f, c1 = 0.f, c2 = 0.f;
+                if (mask) {  // warp-uniform
+                    c0 = warp_sum(mine ? rr[m][0] : 0.f);
+                    c1 = warp_sum(mine ? rr[m][1] : 0.f);
+                    c2 = warp_sum(mine ? rr[m][2] : 0.f);
+                }
+                if (lane == 0) {
+                    float* o = &s_cv[warp][6 + (m * Q.size + j) * 4];
+                    o[0] = (float)__popc(mask);
+                    o[1] = c0;
+                    o[2] = c1;
+                    o[3] = c2;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const int nb = gridDim.x;
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+        double acc = 0.0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) acc += (double)s_cv[w][v];
+        Q.part[(size_t)v * nb + blockIdx.x] = acc;
+    }
+}
+
 // One thread per Gaussian. Every load that does not depend on another is
 // issued first (parameters, Adam state, Cholesky vector, pair offset), then
 // up to eight pair-partial rows at once, so the thread waits for about two
 // memory round trips. Per slot the partials are summed in emission order,
 // Kahan-compensated.
-template <bool ADAM>
+template <bool ADAM, bool CODEC = false>
 __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restrict__ partial,
                                                 const int64_t* __restrict__ pair_off,
                                                 const int32_t* __restrict__ cnt, int64_t capacity, int n,
@@ -277,6 +329,12 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
         __syncthreads();
     }
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    // codec fine-tuning: this Gaussian's dL/dgamma, dL/dbeta terms, RVQ indices,
+    // stage residuals and commitment term (zero when off or g >= n)
+    float cv_gb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int cv_j[kCodecMaxStages] = {-1, -1, -1, -1};
+    float cv_r[kCodecMaxStages][3] = {};
+    float cv_commit = 0.f;
     if (g < n) {
         float pp[8], mm[8], vv[8];
         float4* P4 = nullptr;
@@ -300,6 +358,14 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
                 l1 += 0.5f;
                 l3 += 0.5f;
             }
+        }
+        constexpr bool codec = ADAM && CODEC;
+        float cx[3] = {0.f, 0.f, 0.f}, cq[3] = {0.f, 0.f, 0.f};
+        if constexpr (codec) {  // the render saw the quantised Cholesky vector (Sec. 3.3)
+            const CodecCfg& Q = B.codec;
+            l1 = lsq_quant(l1, Q.gb[0], Q.gb[3], Q.qp, cx[0], cq[0]);
+            l2 = lsq_quant(l2, Q.gb[1], Q.gb[4], Q.qp, cx[1], cq[1]);
+            l3 = lsq_quant(l3, Q.gb[2], Q.gb[5], Q.qp, cx[2], cq[2]);
         }
         const int c = cnt[g];
         const int64_t p0 = pair_off[g];
@@ -386,6 +452,37 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
             if (g_color) { g_color[3 * g] = gr[5]; g_color[3 * g + 1] = gr[6]; g_color[3 * g + 2] = gr[7]; }
             if (g_conic) { g_conic[3 * g] = gq[0]; g_conic[3 * g + 1] = gq[1]; g_conic[3 * g + 2] = gq[2]; }
         } else {
+            if constexpr (codec) {
+                // Straight-through gradients (Sec. 3.3): FP16 positions and RVQ
+                // colour pass dL/d(quantised) unchanged; the quantiser passes it
+                // inside its range and feeds gamma, beta (the LSQ+ convention).
+                const float qp = B.codec.qp;
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const float gi = gr[2 + i];
+                    const bool inside = cx[i] >= 0.f && cx[i] <= qp, outside = cx[i] < 0.f || cx[i] > qp;
+                    cv_gb[i] = inside ? gi * (cq[i] - cx[i]) : (cx[i] > qp ? gi * qp : 0.f);
+                    cv_gb[3 + i] = outside ? gi : 0.f;
+                    gr[2 + i] = inside ? gi : 0.f;
+                }
+                // RVQ residuals each stage quantised, for the EMA codebook update
+                // and the commitment loss (Eq. 11).
+                const CodecCfg& Q = B.codec;
+                float r0 = pp[5], r1 = pp[6], r2 = pp[7];
+#pragma unroll
+                for (int mm_ = 0; mm_ < kCodecMaxStages; ++mm_) {
+                    if (mm_ < Q.stages) {
+                        const int j = Q.idx[(size_t)mm_ * B.total_gauss + g];
+                        const float* e = Q.codebooks + ((size_t)mm_ * Q.size + j) * 3;
+                        cv_j[mm_] = j;
+                        cv_r[mm_][0] = r0; cv_r[mm_][1] = r1; cv_r[mm_][2] = r2;
+                        r0 = __fsub_rn(r0, e[0]);
+                        r1 = __fsub_rn(r1, e[1]);
+                        r2 = __fsub_rn(r2, e[2]);
+                        cv_commit += r0 * r0 + r1 * r1 + r2 * r2;
+                    }
+                }
+            }
             if (cfg.param_mode == 1 && c > 0) {
                 // d mu / d theta = (1 - tanh^2(theta)) / 2 * (W, H)
                 const ImgDesc d = img_desc(B, image_of_gauss(B, g));
@@ -436,6 +533,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
             V4[0] = *reinterpret_cast<float4*>(vv); V4[1] = *reinterpret_cast<float4*>(vv + 4);
         }
     }
+    if (ADAM && CODEC) codec_block_partials(B.codec, cv_gb, cv_j, cv_r, cv_commit);
     if (ADAM) {
         // The last block to finish advances the step counter (every block has
         // read it by then).
@@ -449,6 +547,85 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
                 __threadfence();
             }
         }
+    }
+}
+
+// Codec sums, stage 2: block v adds row v of the per-block partials in a
+// fixed order (thread t takes blocks t, t + 256, ...; then a fixed tree), so
+// the result is reproducible. The last block to finish applies the sums:
+// the optimiser step of gamma, beta (the same optimiser and bias
+// corrections as the Gaussians, the Cholesky learning rate), the EMA
+// codebook update (Sec. 3.4) and the commitment loss L_c (Eq. 11).
+constexpr int kCodecSumThreads = 256;
+
+__global__ void __launch_bounds__(kCodecSumThreads) k_codec_update(CodecCfg Q, AdamCfg cfg, int nblocks, int n) {
+    double* tot = Q.tot;
+    unsigned* ticket = Q.ticket;
+    __shared__ double s_w[32];
+    __shared__ bool s_last;
+    pdl_wait();
+    const int v = blockIdx.x;
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) acc += Q.part[(size_t)v * nblocks + b];
+    acc = block_sum<double>(acc, s_w);
+    if (threadIdx.x == 0) {
+        tot[v] = acc;
+        __threadfence();
+        s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const int nv = codec_nvals(Q);
+    const int t = threadIdx.x;
+    if (t < 6) {
+        const float gr = (float)__ldcg(tot + t);
+        Q.out[1 + t] = __ldcg(tot + t);
+        const int step = *cfg.step;  // already advanced by the reduction
+        const float lr = cfg.lr[1] * (cfg.lr_halve_every > 0 ? ldexpf(1.f, -((step - 1) / cfg.lr_halve_every)) : 1.f);
+        float* p = Q.gb;
+        float& m = p[6 + t];
+        float& vv = p[12 + t];
+        if (cfg.optimizer == 1) {
+            float& nn = p[18 + t];
+            float& gp = p[24 + t];
+            const float dg = step == 1 ? 0.f : gr - gp;
+            m = cfg.beta1 * m + (1.f - cfg.beta1) * gr;
+            vv = cfg.beta2 * vv + (1.f - cfg.beta2) * dg;
+            const float ge = gr + cfg.beta2 * dg;
+            nn = cfg.beta3 * nn + (1.f - cfg.beta3) * ge * ge;
+            const float b1 = 1.f / (1.f - powf(cfg.beta1, (float)step)), b2 = 1.f / (1.f - powf(cfg.beta2, (float)step));
+            const float b3 = rsqrtf(1.f - powf(cfg.beta3, (float)step));
+            p[t] -= lr * (m * b1 + cfg.beta2 * (vv * b2)) / (sqrtf(nn) * b3 + cfg.eps);
+            gp = gr;
+        } else {
+            m = cfg.beta1 * m + (1.f - cfg.beta1) * gr;
+            vv = cfg.beta2 * vv + (1.f - cfg.beta2) * gr * gr;
+            const float b1 = 1.f / (1.f - powf(cfg.beta1, (float)step)), b2 = rsqrtf(1.f - powf(cfg.beta2, (float)step));
+            p[t] -= (lr * b1) * m / (sqrtf(vv) * b2 + cfg.eps);
+        }
+    } else if (t >= 32 && t < 32 + Q.stages) {
+        const int st = t - 32;
+        const double d = (double)Q.decay, e = (double)Q.eps;
+        double sum = 0.0;
+        for (int j = 0; j < Q.size; ++j) {
+            const int base = 6 + (st * Q.size + j) * 4;
+            double& c = Q.ema_count[st * Q.size + j];
+            c = d * c + (1.0 - d) * __ldcg(tot + base);
+            for (int k = 0; k < 3; ++k) {
+                double& s = Q.ema_total[(st * Q.size + j) * 3 + k];
+                s = d * s + (1.0 - d) * __ldcg(tot + base + 1 + k);
+            }
+            sum += c;
+        }
+        for (int j = 0; j < Q.size; ++j) {
+            const double sm = (Q.ema_count[st * Q.size + j] + e) / (sum + Q.size * e) * sum;
+            for (int k = 0; k < 3; ++k)
+                Q.codebooks[(st * Q.size + j) * 3 + k] = (float)(Q.ema_total[(st * Q.size + j) * 3 + k] / sm);
+        }
+    } else if (t == 64) {
+        Q.out[0] = n > 0 ? __ldcg(tot + nv - 1) / ((double)n * Q.size) : 0.0;
+        *ticket = 0u;
     }
 }
 
@@ -510,9 +687,13 @@ cudaError_t launch_reduce(const float4* partial, const int64_t* pair_off, const 
                           const Batch& B, cudaStream_t s) {
     const int blocks = std::max(1, (n + kReduceThreads - 1) / kReduceThreads);
     if (adam) {
-        return launch_pdl(k_reduce<true>, dim3(blocks), dim3(kReduceThreads), 0, s, partial, pair_off, cnt, capacity, n,
-                          P, (float*)nullptr, (float*)nullptr, (float*)nullptr, (float*)nullptr, *adam, params, m, v,
-                          grads_aos, B);
+        const bool codec = B.codec.bits > 0;
+        cudaError_t e = launch_pdl(codec ? k_reduce<true, true> : k_reduce<true, false>, dim3(blocks),
+                                   dim3(kReduceThreads), 0, s, partial, pair_off, cnt, capacity, n, P, (float*)nullptr,
+                                   (float*)nullptr, (float*)nullptr, (float*)nullptr, *adam, params, m, v, grads_aos, B);
+        if (e != cudaSuccess || B.codec.bits == 0) return e;
+        const int nv = 6 + B.codec.stages * B.codec.size * 4 + 1;
+        return launch_pdl(k_codec_update, dim3(nv), dim3(kCodecSumThreads), 0, s, B.codec, *adam, blocks, n);
     }
     AdamCfg none{};
     return launch_pdl(k_reduce<false>, dim3(blocks), dim3(kReduceThreads), 0, s, partial, pair_off, cnt, capacity, n, P,

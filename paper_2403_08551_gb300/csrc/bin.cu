@@ -13,6 +13,8 @@
 // Binning keeps ascending Gaussian index inside each tile (the sort is
 // stable over keys emitted in Gaussian order), which fixes the summation
 // order of Eq. 7 and makes the forward render reproducible.
+#include <cuda_fp16.h>
+
 #include <algorithm>
 
 #include "kernels.cuh"
@@ -97,8 +99,38 @@ __global__ void __launch_bounds__(kProjBlock) k_project(ParamsIn P, Batch B, flo
             l2 = (float)__ddiv_rn(S12, q1);
             l3 = (float)__ddiv_rn(fabs(__dmul_rn(s1, s2)), q1);
         }
-        const float cr = P.color[(int64_t)g * P.cs], cg = P.color[(int64_t)g * P.cs + 1],
-                    cb = P.color[(int64_t)g * P.cs + 2];
+        float cr = P.color[(int64_t)g * P.cs], cg = P.color[(int64_t)g * P.cs + 1],
+              cb = P.color[(int64_t)g * P.cs + 2];
+        if (B.codec.bits > 0) {
+            // Codec fine-tuning (Sec. 3.3): FP16 positions, b-bit Cholesky
+            // vector, greedy RVQ colour; the codes are the encoded stream.
+            const CodecCfg& Q = B.codec;
+            mx = __half2float(__float2half_rn(mx));
+            my = __half2float(__float2half_rn(my));
+            float x, q0, q1, q2;
+            l1 = lsq_quant(l1, Q.gb[0], Q.gb[3], Q.qp, x, q0);
+            l2 = lsq_quant(l2, Q.gb[1], Q.gb[4], Q.qp, x, q1);
+            l3 = lsq_quant(l3, Q.gb[2], Q.gb[5], Q.qp, x, q2);
+            auto code8 = [](float q) { return (unsigned char)(q >= 0.f && q <= 255.f ? (int)q : 0); };
+            Q.codes[g] = make_uchar4(code8(q0), code8(q1), code8(q2), 0);
+            float r0 = cr, r1 = cg, r2 = cb;
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+            for (int m = 0; m < Q.stages; ++m) {
+                const float* cbk = Q.codebooks + (size_t)m * Q.size * 3;
+                const int j = rvq_pick(cbk, Q.size, r0, r1, r2);
+                Q.idx[(size_t)m * B.total_gauss + g] = (uint8_t)j;
+                const float e0 = cbk[3 * j], e1 = cbk[3 * j + 1], e2 = cbk[3 * j + 2];
+                r0 = __fsub_rn(r0, e0);
+                r1 = __fsub_rn(r1, e1);
+                r2 = __fsub_rn(r2, e2);
+                s0 = __dadd_rn(s0, (double)e0);
+                s1 = __dadd_rn(s1, (double)e1);
+                s2 = __dadd_rn(s2, (double)e2);
+            }
+            cr = (float)s0;
+            cg = (float)s1;
+            cb = (float)s2;
+        }
         int4 r = make_int4(0, 0, 0, 0);
         float4 r0 = make_float4(mx, my, 0.f, 0.f), r1 = make_float4(0.f, cr, cg, cb);
         bool ok = isfinite(mx) && isfinite(my) && isfinite(l1) && isfinite(l2) && isfinite(l3) &&

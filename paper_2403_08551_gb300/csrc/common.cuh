@@ -51,6 +51,30 @@ struct ImgDesc {
     int64_t pix_base;    // first pixel index
 };
 
+// Codec fine-tuning state (Sec. 3.3): the render sees FP16 positions, the
+// b-bit quantised Cholesky vector and the RVQ colour; bits == 0 is off.
+constexpr int kCodecMaxStages = 4;
+constexpr int kCodecMaxSize = 16;
+constexpr int kCodecMaxVals = 6 + kCodecMaxStages * kCodecMaxSize * 4 + 1;
+struct CodecCfg {
+    int32_t bits;          // b (1..8); 0: no codec
+    int32_t stages, size;  // M, B
+    float qp;              // 2^b - 1
+    float decay, eps;      // EMA decay and Laplace smoothing of the codebook update
+    float* gb;             // [6] gamma[3], beta[3]; followed by the optimiser state [4][6]
+    float* codebooks;      // [M][B][3]
+    double* ema_count;     // [M][B]
+    double* ema_total;     // [M][B][3]
+    uchar4* codes;         // [N] quantiser codes (x, y, z; w = 0)
+    uint8_t* idx;          // [M][N] RVQ indices
+    double* part;          // [nvals][blocks of the reduction] per-block partial sums
+    double* tot;           // [nvals] their totals
+    unsigned* ticket;      // last-block election of the update kernel (0 between launches)
+    double* out;           // [7]: commitment loss L_c, dL/dgamma[3], dL/dbeta[3]
+};
+
+__device__ __forceinline__ int codec_nvals(const CodecCfg& c) { return 6 + c.stages * c.size * 4 + 1; }
+
 // Either a single image (by value) or nimg > 1 images in device memory.
 struct Batch {
     ImgDesc one;
@@ -64,7 +88,39 @@ struct Batch {
                           //    Cholesky diagonal + 0.5), formation maps them to pixel space
     int32_t cov_mode;     // 0: covariance slots hold the Cholesky vector (l1, l2, l3);
                           // 1: rotation-scaling form (theta, s1, s2), Sigma = (R S)(R S)^T
+    CodecCfg codec;       // quantisation-aware fine-tuning (fit contexts only)
 };
+
+// b-bit asymmetric quantiser of one Cholesky component (Sec. 3.3, LSQ+ form):
+// x = (l - beta) / gamma, code = round(clamp(x, 0, qp)) half to even,
+// l_bar = code * gamma + beta, every operation rounded once (no contraction).
+__device__ __forceinline__ float lsq_quant(float l, float gamma, float beta, float qp, float& x, float& code) {
+    x = __fdiv_rn(__fsub_rn(l, beta), gamma);
+    const float xc = x < 0.f ? 0.f : (x > qp ? qp : x);
+    code = rintf(xc);
+    return __fadd_rn(__fmul_rn(code, gamma), beta);
+}
+
+// One greedy RVQ stage (Sec. 3.3, Eq. 10): the entry of cb [size][3] nearest to
+// r, distances ((e0^2 + e1^2) + e2^2) in FP32 with one rounding per operation,
+// scanning upward and moving only on a strictly smaller distance.
+__device__ __forceinline__ float rvq_dist(const float* __restrict__ e, float r0, float r1, float r2) {
+    const float e0 = __fsub_rn(e[0], r0), e1 = __fsub_rn(e[1], r1), e2 = __fsub_rn(e[2], r2);
+    return __fadd_rn(__fadd_rn(__fmul_rn(e0, e0), __fmul_rn(e1, e1)), __fmul_rn(e2, e2));
+}
+
+__device__ __forceinline__ int rvq_pick(const float* __restrict__ cb, int size, float r0, float r1, float r2) {
+    int best = 0;
+    float bd = rvq_dist(cb, r0, r1, r2);
+    for (int j = 1; j < size; ++j) {
+        const float d = rvq_dist(cb + 3 * j, r0, r1, r2);
+        if (d < bd) {
+            bd = d;
+            best = j;
+        }
+    }
+    return best;
+}
 
 __device__ __forceinline__ ImgDesc img_desc(const Batch& b, int i) {
     return b.nimg == 1 ? b.one : b.many[i];

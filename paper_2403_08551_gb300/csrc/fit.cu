@@ -152,6 +152,19 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
                          "gi_fit_create: bad param_mode, cov_mode, optimizer, beta3 or lr_halve_every");
     if ((reinterpret_cast<uintptr_t>(d->params) & 15) != 0)
         return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: params must be 16-byte aligned");
+    const bool codec = d->codec_bits != 0;
+    if (codec) {
+        if (d->codec_bits < 1 || d->codec_bits > 8 || d->codec_stages < 1 || d->codec_stages > kCodecMaxStages ||
+            d->codec_size < 1 || d->codec_size > kCodecMaxSize || !d->codebooks)
+            return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: codec needs bits in [1, 8], stages in [1, %d], "
+                                                 "size in [1, %d] and codebooks", kCodecMaxStages, kCodecMaxSize);
+        if (d->n_images != 1 || d->cov_mode != 0)
+            return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: codec fine-tuning takes one image in Cholesky form");
+        if (!(d->ema_decay >= 0.f && d->ema_decay < 1.f) || !(d->ema_eps >= 0.f) ||
+            !(d->lsq_gamma[0] > 0.f && d->lsq_gamma[1] > 0.f && d->lsq_gamma[2] > 0.f))
+            return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: codec needs ema_decay in [0, 1), ema_eps >= 0 and "
+                                                 "gamma > 0");
+    }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
     std::vector<ImgDesc> desc(d->n_images);
@@ -206,6 +219,14 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
         up256(probe.bytes),                                     // 20 bin ws
         d->optimizer == 1 ? up256((size_t)N * 32) : 0,          // 21 Adan n
         d->optimizer == 1 ? up256((size_t)N * 32) : 0,          // 22 Adan g_prev
+        codec ? (size_t)256 : 0,                                // 23 gamma, beta + optimiser state
+        codec ? up256((size_t)d->codec_stages * d->codec_size * 12) : 0,  // 24 codebooks
+        codec ? up256((size_t)d->codec_stages * d->codec_size * 8) : 0,   // 25 EMA count
+        codec ? up256((size_t)d->codec_stages * d->codec_size * 24) : 0,  // 26 EMA total
+        codec ? up256((size_t)N * 4) : 0,                                 // 27 quantiser codes
+        codec ? up256((size_t)N * d->codec_stages) : 0,                   // 28 RVQ indices
+        codec ? up256((size_t)kCodecMaxVals * 8 * ((N + 127) / 128)) : 0,  // 29 per-block partials
+        codec ? up256((size_t)kCodecMaxVals * 8) + 256 : 0,               // 30 totals, ticket, out
     };
     size_t total = 0;
     for (size_t x : sz) total += x;
@@ -262,6 +283,41 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
     f->B.param_mode = d->param_mode;
     f->adam.cov_mode = d->cov_mode;
     f->B.cov_mode = d->cov_mode;
+    std::vector<float> gb_init(30, 0.f);
+    std::vector<float> cb_host;
+    std::vector<double> ema_c, ema_t;
+    if (codec) {
+        CodecCfg& Q = f->B.codec;
+        Q.bits = d->codec_bits;
+        Q.stages = d->codec_stages;
+        Q.size = d->codec_size;
+        Q.qp = (float)((1 << d->codec_bits) - 1);
+        Q.decay = d->ema_decay;
+        Q.eps = d->ema_eps;
+        Q.gb = reinterpret_cast<float*>(at(23));
+        Q.codebooks = reinterpret_cast<float*>(at(24));
+        Q.ema_count = reinterpret_cast<double*>(at(25));
+        Q.ema_total = reinterpret_cast<double*>(at(26));
+        Q.codes = reinterpret_cast<uchar4*>(at(27));
+        Q.idx = reinterpret_cast<uint8_t*>(at(28));
+        Q.part = reinterpret_cast<double*>(at(29));
+        Q.tot = reinterpret_cast<double*>(at(30));
+        Q.ticket = reinterpret_cast<unsigned*>(at(30) + up256((size_t)kCodecMaxVals * 8));
+        Q.out = reinterpret_cast<double*>(at(30) + up256((size_t)kCodecMaxVals * 8) + 64);
+        for (int i = 0; i < 3; ++i) {
+            gb_init[i] = d->lsq_gamma[i];
+            gb_init[3 + i] = d->lsq_beta[i];
+        }
+        const size_t ncb = (size_t)Q.stages * Q.size;
+        cb_host.resize(ncb * 3);
+        if (cudaMemcpy(cb_host.data(), d->codebooks, ncb * 12, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            release(f);
+            return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: codebooks is not a readable device buffer");
+        }
+        ema_c.assign(ncb, 1.0);  // one pseudo-count per entry, whose sum is the entry itself
+        ema_t.resize(ncb * 3);
+        for (size_t i = 0; i < ncb * 3; ++i) ema_t[i] = (double)cb_host[i];
+    }
 
 #define FIT_TRY(x)                                      \
     do {                                                \
@@ -275,6 +331,13 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
     FIT_TRY(cudaMemcpyAsync(f->d_desc, desc.data(), sizeof(ImgDesc) * desc.size(), cudaMemcpyHostToDevice, s));
     FIT_TRY(cudaMemcpyAsync(f->params, d->params, (size_t)gauss * 32, cudaMemcpyDeviceToDevice, s));
     FIT_TRY(cudaMemcpyAsync(f->targets, d->targets, (size_t)pix * 12, cudaMemcpyDeviceToDevice, s));
+    if (codec) {
+        const CodecCfg& Q = f->B.codec;
+        FIT_TRY(cudaMemcpyAsync(Q.gb, gb_init.data(), 30 * sizeof(float), cudaMemcpyHostToDevice, s));
+        FIT_TRY(cudaMemcpyAsync(Q.codebooks, cb_host.data(), cb_host.size() * 4, cudaMemcpyHostToDevice, s));
+        FIT_TRY(cudaMemcpyAsync(Q.ema_count, ema_c.data(), ema_c.size() * 8, cudaMemcpyHostToDevice, s));
+        FIT_TRY(cudaMemcpyAsync(Q.ema_total, ema_t.data(), ema_t.size() * 8, cudaMemcpyHostToDevice, s));
+    }
     FIT_TRY(cudaStreamSynchronize(s));
     FIT_TRY(cudaStreamCreateWithFlags(&f->cap_stream, cudaStreamNonBlocking));
     if (f->stage_events)
@@ -336,6 +399,13 @@ gi_status gi_fit_pointer(gi_fit* f, int32_t what, void** ptr) {
         case GI_FIT_TARGET: *ptr = f->targets; break;
         case GI_FIT_ADAN_N: *ptr = f->adam.n; break;
         case GI_FIT_ADAN_GPREV: *ptr = f->adam.g_prev; break;
+        case GI_FIT_CODEC_GB: *ptr = f->B.codec.gb; break;
+        case GI_FIT_CODEBOOKS: *ptr = f->B.codec.codebooks; break;
+        case GI_FIT_EMA_COUNT: *ptr = f->B.codec.ema_count; break;
+        case GI_FIT_EMA_TOTAL: *ptr = f->B.codec.ema_total; break;
+        case GI_FIT_CODES: *ptr = f->B.codec.codes; break;
+        case GI_FIT_RVQ_IDX: *ptr = f->B.codec.idx; break;
+        case GI_FIT_CODEC_OUT: *ptr = f->B.codec.out; break;
         default: return set_error(GI_ERR_INVALID_ARG, "gi_fit_pointer: unknown field %d", what);
     }
     return GI_OK;
