@@ -262,7 +262,7 @@ def batched_vs_plain(gi, torch, n_images, steps, stream):
             "mean_psnr_db_plain": sum(psnr(b) for b in mse_p) / len(mse_p)}
 
 
-def long_fit(gi, torch, stream, T, steps, log_path=None, every=5000, paper=False, cov="cholesky"):
+def long_fit(gi, torch, stream, T, steps, log_path=None, every=5000, paper=False, cov="cholesky", keep=False):
     """The full-length fit of the 768x512, 70k-Gaussian workload: `steps`
     graph-replayed steps (no L2 flush: steady state) in chunks of `every`,
     each timed with CUDA events; PSNR of the first step's render and after
@@ -314,6 +314,63 @@ def long_fit(gi, torch, stream, T, steps, log_path=None, every=5000, paper=False
     out = {"steps": steps, "iter_s": (steps - 1) / t, "seconds": t, "psnr_db_step1": p1,
            "psnr_db_final": traj[-1][1], "psnr_db_trajectory": traj, "pairs_final": int(fit.k.item()),
            "l2": "not flushed between steps (steady state)", "device_errors": int(err)}
+    kept = fit.params.clone() if keep else None
+    fit.close()
+    return (out, kept) if keep else out
+
+
+def codec_finetune(gi, torch, stream, T, params, steps=10000, every=2500, bits=6, stages=2, size=8):
+    """Attribute quantisation-aware fine-tuning (Sec. 3.3-3.4) of the
+    Gaussians a 50k-step fit with the paper's recipe ended at: b = 6 bits for
+    the Cholesky vector, 2-stage RVQ with 8-entry codebooks for the colour,
+    FP16 positions (K-means and quantiser ranges set on the host), Adan at
+    that fit's final learning rate (2.5e-4, after two halvings). Reports the
+    PSNR of the unquantised fit, of the quantised render before fine-tuning
+    (step 1's forward), after `steps` steps, the step rate and the size of
+    the encoded stream."""
+    w = synth.workload(WORKLOAD)
+    psnr = lambda e: 10 * math.log10(1.0 / e) if e > 0 else float("inf")  # noqa: E731
+    lr = 2.5e-4
+    plain = gi.Fit([torch.from_numpy(w.target).cuda()], [params], tile=T, lr=(lr, lr, lr), capacity_factor=4.0,
+                   param_mode="paper", optimizer="adan", use_graph=False)
+    plain.render()
+    torch.cuda.synchronize()
+    img = plain.images()[0]
+    ref = torch.from_numpy(w.target).cuda()
+    p_plain = psnr(float(((img.clamp(0, 1) - ref) ** 2).mean()))
+    plain.close()
+    spec = gi.codec_init(params, bits=bits, stages=stages, size=size, param_mode="paper")
+    fit = gi.Fit([ref], [params], tile=T, lr=(lr, lr, lr), capacity_factor=4.0, param_mode="paper",
+                 optimizer="adan", codec=spec)
+    fit.step(1)
+    torch.cuda.synchronize()
+    p1 = psnr(fit.mse()[0])
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    done, t, traj = 1, 0.0, [[1, p1]]
+    while done < steps:
+        n = min(every, steps - done)
+        e0.record(stream)
+        fit.step(n)
+        e1.record(stream)
+        e1.synchronize()
+        t += e0.elapsed_time(e1) / 1e3
+        done += n
+        traj.append([done, psnr(fit.mse()[0])])
+    fit.render()
+    torch.cuda.synchronize()
+    img = fit.images()[0]
+    p_final = psnr(float(((img.clamp(0, 1) - ref) ** 2).mean()))
+    err = gi.device_errors(clear=True)
+    n = w.n
+    bits_total = n * (2 * 16 + 3 * bits + stages * math.ceil(math.log2(size))) + 6 * 32 + stages * size * 3 * 32
+    out = {"steps": steps, "iter_s": (steps - 1) / t, "psnr_db_unquantised": p_plain,
+           "psnr_db_quantised_before": p1, "psnr_db_trajectory": traj, "psnr_db_final_render": p_final,
+           "commitment_loss": float(fit.codec_out[0].item()), "bits": bits_total,
+           "bpp": bits_total / (w.W * w.H), "config": {"bits": bits, "stages": stages, "size": size, "lr": lr,
+                                                       "ema_decay": fit.codec["ema_decay"]},
+           "psnr_note": "training-loss PSNR of the step's render (unclamped) in the trajectory; the "
+                        "unquantised and final figures are PSNR of the clamped render",
+           "device_errors": int(err)}
     fit.close()
     return out
 
@@ -563,8 +620,10 @@ def main():
     if args.long_steps > 1 and not args.no_extra and rank == 0:
         out["fit_long"] = long_fit(gi, torch, stream, T, args.long_steps,
                                    os.path.join(args.out, "fit_long_psnr.jsonl"))
-        out["fit_long_paper_recipe"] = long_fit(gi, torch, stream, T, args.long_steps,
-                                                os.path.join(args.out, "fit_long_paper_psnr.jsonl"), paper=True)
+        out["fit_long_paper_recipe"], fitted = long_fit(gi, torch, stream, T, args.long_steps,
+                                                        os.path.join(args.out, "fit_long_paper_psnr.jsonl"),
+                                                        paper=True, keep=True)
+        out["codec_finetune"] = codec_finetune(gi, torch, stream, T, fitted)
         out["fit_long_paper_recipe_rs"] = long_fit(gi, torch, stream, T, args.long_steps,
                                                    os.path.join(args.out, "fit_long_paper_rs_psnr.jsonl"),
                                                    paper=True, cov="rs")
