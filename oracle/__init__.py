@@ -26,6 +26,11 @@ Parity status per function (pins live in ``tests/test_oracle_*.py``):
                 reduction to Adam's direction when b2 = 0)
   vq_decode ... pinned (IEEE float32 addition, zero residual codebook)
   rvq_encode .. pinned (exhaustive per-stage argmin)
+  sigmoid_opacity / opacity_forward_backward / blend_render /
+  blend_backward / blend_forward_backward ... pinned (per-pixel brute force
+                over all Gaussians; closed forms of one and two Gaussians;
+                the accumulated sum as the small-opacity limit; central
+                finite differences in every parameter, opacity included)
   fp16_round / lsq_fake_quant / lsq_ste_grads / rvq_assign_f32 /
   commitment_loss / ema_codebook_update / codec_forward_backward ... pinned
                 (struct half packing; brute-force nearest grid point;
@@ -94,6 +99,11 @@ def _load():
             lib.gio_loss.restype = ctypes.c_double
             lib.gio_backward.argtypes = [P, P, P, P, P, i64, i32, i32, i32, P, P, P, P, P, P]
             lib.gio_backward.restype = None
+            d = ctypes.c_double
+            lib.gio_render_blend.argtypes = [P, P, P, P, P, P, i32, i32, i32, d, d, d, P, P, P, P]
+            lib.gio_render_blend.restype = None
+            lib.gio_backward_blend.argtypes = [P, P, P, P, P, P, i64, i32, i32, i32, d, d, P, P, P, P, P, P, P, P]
+            lib.gio_backward_blend.restype = None
             lib.gio_num_threads.restype = ctypes.c_int
             lib.gio_set_num_threads.argtypes = [ctypes.c_int]
             _lib = lib
@@ -570,3 +580,93 @@ def codec_forward_backward(means, chol, color, gamma, beta, codebooks, bits, tar
                   "grads": {"means": g["means"], "chol": g_l, "color": g["color"], "gamma": g_gamma,
                             "beta": g_beta}}
     return r
+
+
+# ---------------------------------------------------------------------------
+# The ablations of Table 3: colour and opacity kept apart ("w/o M", 9
+# parameters, Sec. 3.1's basic 2D Gaussian) and sorted alpha-blending in
+# place of the accumulated sum ("w/o AR", Eq. 3-4).
+# ---------------------------------------------------------------------------
+
+BLEND_THRESHOLDS = (1.0 / 255.0, 0.99, 1e-4)  # alpha skip, alpha clamp, transmittance stop (3D GS)
+
+
+def sigmoid_opacity(logit):
+    """Opacity o = 1 / (1 + exp(-logit)) in FP64, rounded once to FP32 (the
+    activation 3D GS applies to its opacity; the paper names none)."""
+    z = np.asarray(logit, np.float64)
+    return (1.0 / (1.0 + np.exp(-z))).astype(np.float32)
+
+
+def opacity_forward_backward(means, chol, color, logit, target, T):
+    """Accumulated summation with separate colour and opacity (Eq. 5,
+    C_i = sum c_n o_n exp(-sigma_n)): the plain pass on c' = c o (one FP32
+    rounding), then dL/dc = dL/dc' o and dL/dlogit = (dL/dc' . c) o (1 - o)."""
+    o = sigmoid_opacity(logit)
+    c = np.asarray(color, np.float32)
+    cp = (c * o[:, None]).astype(np.float32)
+    r = forward_backward(means, chol, cp, target, T)
+    g = r["grads"]
+    o64 = o.astype(np.float64)
+    r["grads_opacity"] = {"color": g["color"] * o64[:, None],
+                          "logit": (g["color"] * c.astype(np.float64)).sum(axis=1) * o64 * (1.0 - o64),
+                          "abs_color": g["abs"]["color"] * o64[:, None],
+                          "abs_logit": (g["abs"]["color"] * np.abs(c)).sum(axis=1) * o64 * (1.0 - o64)}
+    return r
+
+
+def blend_render(means, chol, color, opac, ids, ranges, W, H, T, thresholds=BLEND_THRESHOLDS):
+    """Sorted alpha-blending (Eq. 3-4) over the binned lists, front to back in
+    ascending g with 3D GS's thresholds (gi_oracle.c). Returns (out [H,W,3]
+    FP64, t_final [H,W], n_last [H,W] int32, ambiguous [H,W] bool)."""
+    means, chol, color, opac = _f32(means), _f32(chol), _f32(color), _f32(opac)
+    ids = np.ascontiguousarray(ids, np.uint32)
+    if ids.size == 0:
+        ids = np.zeros(1, np.uint32)
+    ranges = np.ascontiguousarray(ranges, np.int32)
+    out = np.zeros((H, W, 3), np.float64)
+    tf = np.zeros((H, W), np.float64)
+    nl = np.zeros((H, W), np.int32)
+    amb = np.zeros((H, W), np.uint8)
+    a_min, a_max, t_min = thresholds
+    _load().gio_render_blend(_p(means), _p(chol), _p(color), _p(opac), _p(ids), _p(ranges), W, H, T,
+                             a_min, a_max, t_min, _p(out), _p(tf), _p(nl), _p(amb))
+    return out, tf, nl, amb.astype(bool)
+
+
+def blend_backward(means, chol, color, opac, ids, ranges, W, H, T, out, n_last, dldc, thresholds=BLEND_THRESHOLDS):
+    """Analytic gradients of blend_render (gi_oracle.c): dict of FP64 means
+    [n,2], chol [n,3], color [n,3], opac [n] (dL/do) and abs [n,9]."""
+    means, chol, color, opac = _f32(means), _f32(chol), _f32(color), _f32(opac)
+    ids = np.ascontiguousarray(ids, np.uint32)
+    if ids.size == 0:
+        ids = np.zeros(1, np.uint32)
+    ranges = np.ascontiguousarray(ranges, np.int32)
+    out = np.ascontiguousarray(out, np.float64)
+    n_last = np.ascontiguousarray(n_last, np.int32)
+    dldc = np.ascontiguousarray(dldc, np.float64)
+    n = means.shape[0]
+    gm = np.zeros((n, 2)); gl = np.zeros((n, 3)); gc = np.zeros((n, 3)); go = np.zeros(n); ga = np.zeros((n, 9))
+    a_min, a_max, _ = thresholds
+    _load().gio_backward_blend(_p(means), _p(chol), _p(color), _p(opac), _p(ids), _p(ranges), n, W, H, T,
+                               a_min, a_max, _p(out), _p(n_last), _p(dldc), _p(gm), _p(gl), _p(gc), _p(go), _p(ga))
+    return {"means": gm, "chol": gl, "color": gc, "opac": go, "abs": ga}
+
+
+def blend_forward_backward(means, chol, color, logit, target, T, thresholds=BLEND_THRESHOLDS):
+    """One alpha-blending pass with opacity o = sigmoid_opacity(logit): the
+    support rule and binning of the accumulated form (3-sigma rect, ascending
+    g per tile), blend_render, the L2 loss, blend_backward, and
+    dL/dlogit = dL/do o (1 - o)."""
+    H, W, _ = target.shape
+    o = sigmoid_opacity(logit)
+    rect, cnt = rect_rule(means, chol, color, W, H, T)
+    ids, ranges, pair_off = bin_tiles(rect, cnt, W, H, T)
+    out, tf, nl, amb = blend_render(means, chol, color, o, ids, ranges, W, H, T, thresholds)
+    L, d = loss(out, target)
+    g = blend_backward(means, chol, color, o, ids, ranges, W, H, T, out, nl, d, thresholds)
+    o64 = o.astype(np.float64)
+    g["logit"] = g["opac"] * o64 * (1.0 - o64)
+    g["abs_logit"] = g["abs"][:, 8] * o64 * (1.0 - o64)
+    return dict(rect=rect, cnt=cnt, ids=ids, ranges=ranges, out=out, t_final=tf, n_last=nl, ambiguous=amb,
+                loss=L, dldc=d, grads=g, opac=o)
