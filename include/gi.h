@@ -82,8 +82,8 @@ typedef struct {
  * exp(-sigma) = exp2(-(z1^2 + z2^2)) (Sec. 3.1 with Sigma^-1 = L^-T L^-1). */
 #define GI_REC_FLOATS 8
 
-/* ABI version: 4 (gi_fit_desc gained param_mode, optimizer, beta3, lr_halve_every in 2,
- * cov_mode in 3, the codec fine-tuning fields in 4). */
+/* ABI version: 5 (gi_fit_desc gained param_mode, optimizer, beta3, lr_halve_every in 2,
+ * cov_mode in 3, the codec fine-tuning fields in 4, opacity_mode and opacity_logits in 5). */
 GI_API int32_t gi_abi_version(void);
 GI_API const char* gi_last_error(void);
 GI_API const char* gi_status_string(int32_t status);
@@ -271,6 +271,16 @@ typedef struct {
     float lsq_beta[3];        /* initial beta_i */
     float ema_decay;          /* in [0, 1) */
     float ema_eps;            /* Laplace smoothing of the counts (>= 0) */
+    /* Table 3's ablations: the basic 2D Gaussian of Sec. 3.1 with colour c and a
+       separate opacity o = sigmoid(logit) (9 parameters, "w/o M"). params then
+       hold c in slots 5..7 and the logits live beside them.
+       1: accumulated summation of c o exp(-sigma) (Eq. 5);
+       2: sorted alpha-blending (Eq. 3-4, "w/o AR"): per pixel, front to back in
+          ascending Gaussian index, alpha = min(0.99, o exp(-sigma)) skipped below
+          1/255, stopping before T (1 - alpha) < 1e-4 (3D GS's thresholds);
+          tile 16 only. The logits take the optimiser's step at lr_color. */
+    int32_t opacity_mode;     /* 0 (merged c', the paper's form), 1 or 2; codec needs 0 */
+    const float* opacity_logits; /* device [sum counts] initial logits (copied); NULL = 0 */
 } gi_fit_desc;
 
 /* Allocates the context and copies targets and params (the caller's buffers
@@ -311,7 +321,11 @@ enum {
     GI_FIT_EMA_TOTAL = 14,   /* f64 [M][B][3] EMA residual sums */
     GI_FIT_CODES = 15,       /* u8 [N][4] quantiser codes of the last step (4th byte 0) */
     GI_FIT_RVQ_IDX = 16,     /* u8 [M][N] RVQ indices of the last step */
-    GI_FIT_CODEC_OUT = 17    /* f64 [7] last step: L_c, dL/dgamma[3], dL/dbeta[3] */
+    GI_FIT_CODEC_OUT = 17,   /* f64 [7] last step: L_c, dL/dgamma[3], dL/dbeta[3] */
+    /* separate opacity (NULL pointers when opacity_mode == 0): */
+    GI_FIT_OPACITY = 18,     /* f32 [7][N]: logit, o of the last formation, optimiser m, v, n,
+                                g_prev, dL/dlogit of the last step */
+    GI_FIT_N_LAST = 19       /* i32 [pixels] alpha-blending: list entries each pixel walked */
 };
 GI_API gi_status gi_fit_pointer(gi_fit* fit, int32_t what, void** ptr);
 GI_API gi_status gi_fit_destroy(gi_fit* fit);

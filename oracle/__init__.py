@@ -100,9 +100,9 @@ def _load():
             lib.gio_backward.argtypes = [P, P, P, P, P, i64, i32, i32, i32, P, P, P, P, P, P]
             lib.gio_backward.restype = None
             d = ctypes.c_double
-            lib.gio_render_blend.argtypes = [P, P, P, P, P, P, i32, i32, i32, d, d, d, P, P, P, P]
+            lib.gio_render_blend.argtypes = [P, P, P, P, P, P, i32, i32, i32, d, d, d, d, P, P, P, P]
             lib.gio_render_blend.restype = None
-            lib.gio_backward_blend.argtypes = [P, P, P, P, P, P, i64, i32, i32, i32, d, d, P, P, P, P, P, P, P, P]
+            lib.gio_backward_blend.argtypes = [P, P, P, P, P, P, i64, i32, i32, i32, d, d] + [P] * 10
             lib.gio_backward_blend.restype = None
             lib.gio_num_threads.restype = ctypes.c_int
             lib.gio_set_num_threads.argtypes = [ctypes.c_int]
@@ -589,6 +589,10 @@ def codec_forward_backward(means, chol, color, gamma, beta, codebooks, bits, tar
 # ---------------------------------------------------------------------------
 
 BLEND_THRESHOLDS = (1.0 / 255.0, 0.99, 1e-4)  # alpha skip, alpha clamp, transmittance stop (3D GS)
+# A decision within this relative distance of its threshold is flagged: an
+# FP32 evaluation (alpha to a few 1e-7, the transmittance, a product of up to a
+# few hundred factors, to about 2e-5) may take it the other way.
+BLEND_AMBIGUITY = 3e-5
 
 
 def sigmoid_opacity(logit):
@@ -615,7 +619,7 @@ def opacity_forward_backward(means, chol, color, logit, target, T):
     return r
 
 
-def blend_render(means, chol, color, opac, ids, ranges, W, H, T, thresholds=BLEND_THRESHOLDS):
+def blend_render(means, chol, color, opac, ids, ranges, W, H, T, thresholds=BLEND_THRESHOLDS, amb=BLEND_AMBIGUITY):
     """Sorted alpha-blending (Eq. 3-4) over the binned lists, front to back in
     ascending g with 3D GS's thresholds (gi_oracle.c). Returns (out [H,W,3]
     FP64, t_final [H,W], n_last [H,W] int32, ambiguous [H,W] bool)."""
@@ -627,16 +631,18 @@ def blend_render(means, chol, color, opac, ids, ranges, W, H, T, thresholds=BLEN
     out = np.zeros((H, W, 3), np.float64)
     tf = np.zeros((H, W), np.float64)
     nl = np.zeros((H, W), np.int32)
-    amb = np.zeros((H, W), np.uint8)
+    flags = np.zeros((H, W), np.uint8)
     a_min, a_max, t_min = thresholds
     _load().gio_render_blend(_p(means), _p(chol), _p(color), _p(opac), _p(ids), _p(ranges), W, H, T,
-                             a_min, a_max, t_min, _p(out), _p(tf), _p(nl), _p(amb))
-    return out, tf, nl, amb.astype(bool)
+                             a_min, a_max, t_min, amb, _p(out), _p(tf), _p(nl), _p(flags))
+    return out, tf, nl, flags.astype(bool)
 
 
-def blend_backward(means, chol, color, opac, ids, ranges, W, H, T, out, n_last, dldc, thresholds=BLEND_THRESHOLDS):
+def blend_backward(means, chol, color, opac, ids, ranges, W, H, T, out, n_last, dldc, thresholds=BLEND_THRESHOLDS,
+                   ambiguous=None):
     """Analytic gradients of blend_render (gi_oracle.c): dict of FP64 means
-    [n,2], chol [n,3], color [n,3], opac [n] (dL/do) and abs [n,9]."""
+    [n,2], chol [n,3], color [n,3], opac [n] (dL/do), abs [n,9] and
+    abs_ambiguous [n,9] (magnitudes over the flagged pixels)."""
     means, chol, color, opac = _f32(means), _f32(chol), _f32(color), _f32(opac)
     ids = np.ascontiguousarray(ids, np.uint32)
     if ids.size == 0:
@@ -647,10 +653,13 @@ def blend_backward(means, chol, color, opac, ids, ranges, W, H, T, out, n_last, 
     dldc = np.ascontiguousarray(dldc, np.float64)
     n = means.shape[0]
     gm = np.zeros((n, 2)); gl = np.zeros((n, 3)); gc = np.zeros((n, 3)); go = np.zeros(n); ga = np.zeros((n, 9))
+    gaa = np.zeros((n, 9))
+    amb = np.ascontiguousarray(np.zeros((H, W), np.uint8) if ambiguous is None else ambiguous, np.uint8)
     a_min, a_max, _ = thresholds
     _load().gio_backward_blend(_p(means), _p(chol), _p(color), _p(opac), _p(ids), _p(ranges), n, W, H, T,
-                               a_min, a_max, _p(out), _p(n_last), _p(dldc), _p(gm), _p(gl), _p(gc), _p(go), _p(ga))
-    return {"means": gm, "chol": gl, "color": gc, "opac": go, "abs": ga}
+                               a_min, a_max, _p(out), _p(n_last), _p(amb), _p(dldc), _p(gm), _p(gl), _p(gc), _p(go),
+                               _p(ga), _p(gaa))
+    return {"means": gm, "chol": gl, "color": gc, "opac": go, "abs": ga, "abs_ambiguous": gaa}
 
 
 def blend_forward_backward(means, chol, color, logit, target, T, thresholds=BLEND_THRESHOLDS):
@@ -664,9 +673,10 @@ def blend_forward_backward(means, chol, color, logit, target, T, thresholds=BLEN
     ids, ranges, pair_off = bin_tiles(rect, cnt, W, H, T)
     out, tf, nl, amb = blend_render(means, chol, color, o, ids, ranges, W, H, T, thresholds)
     L, d = loss(out, target)
-    g = blend_backward(means, chol, color, o, ids, ranges, W, H, T, out, nl, d, thresholds)
+    g = blend_backward(means, chol, color, o, ids, ranges, W, H, T, out, nl, d, thresholds, amb)
     o64 = o.astype(np.float64)
     g["logit"] = g["opac"] * o64 * (1.0 - o64)
     g["abs_logit"] = g["abs"][:, 8] * o64 * (1.0 - o64)
+    g["abs_ambiguous_logit"] = g["abs_ambiguous"][:, 8] * o64 * (1.0 - o64)
     return dict(rect=rect, cnt=cnt, ids=ids, ranges=ranges, out=out, t_final=tf, n_last=nl, ambiguous=amb,
                 loss=L, dldc=d, grads=g, opac=o)

@@ -392,15 +392,14 @@ void gio_backward(const float* means, const float* chol, const float* color,
  * out [H][W][3] FP64; t_final [H][W] the final T; n_last [H][W] the list
  * position (from the tile's first entry) just past the last Gaussian that
  * contributed; ambiguous [H][W] = 1 where some decision lay within a relative
- * 1e-4 of its threshold (there an FP32 evaluation may decide otherwise).
+ * amb of its threshold (there an FP32 evaluation may decide otherwise).
  */
 void gio_render_blend(const float* means, const float* chol, const float* color, const float* opac,
                       const uint32_t* ids, const int32_t* ranges, int32_t W, int32_t H, int32_t T,
-                      double a_min, double a_max, double t_min, double* out, double* t_final,
+                      double a_min, double a_max, double t_min, double amb, double* out, double* t_final,
                       int32_t* n_last, uint8_t* ambiguous) {
     const int32_t tw = (W + T - 1) / T, th = (H + T - 1) / T;
     const int64_t T_img = (int64_t)tw * th;
-    const double amb = 1e-4;
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t t = 0; t < T_img; ++t) {
         const int32_t tx = (int32_t)(t % tw), ty = (int32_t)(t / tw);
@@ -451,63 +450,100 @@ void gio_render_blend(const float* means, const float* chol, const float* color,
  * dL/dsigma_n = -dL/dalpha_n alpha_n, chained to mu and the Cholesky vector
  * as in gio_backward. Gradients are summed per Gaussian over all pixels
  * (serial: the sums are in a fixed order). g_opac is dL/do; g_abs [n][9] the
- * condition magnitudes (means 2, chol 3, colour 3, opacity 1).
+ * condition magnitudes (means 2, chol 3, colour 3, opacity 1); g_abs_amb [n][9]
+ * the same magnitudes over the pixels flagged in ambiguous only, where the
+ * walk is continued to the end of the list and skipped Gaussians count as
+ * contributing (a bound on what a decision taken the other way can change).
  */
+static void blend_abs_terms(double* s, double ea, double dx, double dy, double dla_abs, double w,
+                            const double* gabs_at) {
+    s[0] += ea * fabs(dx);
+    s[1] += ea * fabs(dy);
+    s[2] += ea * 0.5 * dx * dx;
+    s[3] += ea * 0.5 * fabs(dx * dy);
+    s[4] += ea * 0.5 * dy * dy;
+    s[5] += gabs_at[0];
+    s[6] += gabs_at[1];
+    s[7] += gabs_at[2];
+    s[8] += dla_abs * w;
+}
+
+static void chain_abs(const double* am, double A, double B, double C, double l1, double l2, double l3, int live,
+                      double* ab) {
+    ab[0] = fabs(A) * am[0] + fabs(B) * am[1];
+    ab[1] = fabs(B) * am[0] + fabs(C) * am[1];
+    const double k11a = A * A * l1 + A * B * l2, k12a = 2.0 * A * B * l1 + (A * C + B * B) * l2,
+                 k22a = B * B * l1 + B * C * l2;
+    const double k11b = A * B * l1 + B * B * l2, k12b = (A * C + B * B) * l1 + 2.0 * B * C * l2,
+                 k22b = B * C * l1 + C * C * l2;
+    ab[2] = live ? 2.0 * (fabs(k11a) * am[2] + fabs(k12a) * am[3] + fabs(k22a) * am[4]) : 0.0;
+    ab[3] = live ? 2.0 * (fabs(k11b) * am[2] + fabs(k12b) * am[3] + fabs(k22b) * am[4]) : 0.0;
+    ab[4] = live ? 2.0 * fabs(l3) * (B * B * am[2] + 2.0 * fabs(B * C) * am[3] + C * C * am[4]) : 0.0;
+    ab[5] = am[5];
+    ab[6] = am[6];
+    ab[7] = am[7];
+    ab[8] = am[8];
+}
+
 void gio_backward_blend(const float* means, const float* chol, const float* color, const float* opac,
                         const uint32_t* ids, const int32_t* ranges, int64_t n, int32_t W, int32_t H,
                         int32_t T, double a_min, double a_max, const double* out, const int32_t* n_last,
-                        const double* dldc, double* g_means, double* g_chol, double* g_color,
-                        double* g_opac, double* g_abs) {
+                        const uint8_t* ambiguous, const double* dldc, double* g_means, double* g_chol,
+                        double* g_color, double* g_opac, double* g_abs, double* g_abs_amb) {
     const int32_t tw = (W + T - 1) / T, th = (H + T - 1) / T;
     const int64_t T_img = (int64_t)tw * th;
-    /* per Gaussian: sums e d (2), e/2 d d^T (3), colour (3), opacity (1) and
-     * their absolute counterparts */
-    double* acc = (double*)calloc((size_t)(n > 0 ? n : 1) * 18, sizeof(double));
+    /* per Gaussian: [0..8] sums e d (2), e/2 d d^T (3), colour (3), opacity (1);
+     * [9..17] their absolute counterparts; [18..26] those over ambiguous pixels */
+    double* acc = (double*)calloc((size_t)(n > 0 ? n : 1) * 27, sizeof(double));
     for (int64_t t = 0; t < T_img; ++t) {
         const int32_t tx = (int32_t)(t % tw), ty = (int32_t)(t / tw);
-        const int32_t b = ranges[2 * t];
+        const int32_t b = ranges[2 * t], e_end = ranges[2 * t + 1];
         for (int32_t y = ty * T; y < (ty + 1) * T && y < H; ++y) {
             for (int32_t x = tx * T; x < (tx + 1) * T && x < W; ++x) {
                 const int64_t pix = (int64_t)y * W + x;
                 const double* G = dldc + 3 * pix;
                 const double* Cf = out + 3 * pix;
+                const int amb = ambiguous && ambiguous[pix];
                 double P[3] = {0.0, 0.0, 0.0}, Tr = 1.0;
                 const double px = x + 0.5, py = y + 0.5;
-                for (int32_t k = b; k < b + n_last[pix]; ++k) {
+                for (int32_t k = b; k < (amb ? e_end : b + n_last[pix]); ++k) {
+                    const int walked = k < b + n_last[pix];
                     const int64_t g = ids[k];
                     double A, B, C;
                     conic64(chol, g, &A, &B, &C);
                     const double dx = px - means[2 * g], dy = py - means[2 * g + 1];
                     const double w = weight64(A, B, C, dx, dy);
                     double a = (double)opac[g] * w;
-                    if (a < a_min) continue;
+                    const int skipped = a < a_min;
+                    if (skipped && !amb) continue;
                     const int clamped = a > a_max;
                     if (clamped) a = a_max;
                     const double cc[3] = {color[3 * g], color[3 * g + 1], color[3 * g + 2]};
-                    double dla = 0.0, dla_abs = 0.0;
-                    double* s = acc + 18 * g;
+                    double dla = 0.0, dla_abs = 0.0, gat[3];
+                    double* s = acc + 27 * g;
                     for (int ch = 0; ch < 3; ++ch) {
-                        P[ch] += cc[ch] * a * Tr;
-                        const double S = Cf[ch] - P[ch];
+                        const double Pn = P[ch] + cc[ch] * a * Tr;
+                        const double S = Cf[ch] - Pn;
                         dla += G[ch] * (cc[ch] * Tr - S / (1.0 - a));
-                        dla_abs += fabs(G[ch]) * (fabs(cc[ch]) * Tr + (fabs(Cf[ch]) + fabs(P[ch])) / (1.0 - a));
-                        s[5 + ch] += G[ch] * a * Tr;
-                        s[14 + ch] += fabs(G[ch] * a * Tr);
+                        dla_abs += fabs(G[ch]) * (fabs(cc[ch]) * Tr + (fabs(Cf[ch]) + fabs(Pn)) / (1.0 - a));
+                        gat[ch] = fabs(G[ch] * a * Tr);
+                        if (walked && !skipped) {
+                            P[ch] = Pn;
+                            s[5 + ch] += G[ch] * a * Tr;
+                        }
                     }
+                    const double ea = clamped ? 0.0 : dla_abs * a; /* magnitude of dL/dsigma */
+                    if (amb) blend_abs_terms(s + 18, ea, dx, dy, clamped ? 0.0 : dla_abs, w, gat);
+                    if (!walked || skipped) continue;
+                    blend_abs_terms(s + 9, ea, dx, dy, clamped ? 0.0 : dla_abs, w, gat);
                     if (!clamped) {
-                        const double e = -dla * a, ea = dla_abs * a; /* dL/dsigma and its magnitude */
+                        const double e = -dla * a; /* dL/dsigma */
                         s[0] += e * -(A * dx + B * dy);
                         s[1] += e * -(B * dx + C * dy);
                         s[2] += e * 0.5 * dx * dx;
                         s[3] += e * 0.5 * dx * dy;
                         s[4] += e * 0.5 * dy * dy;
                         s[8] += dla * w;
-                        s[9] += ea * fabs(dx);
-                        s[10] += ea * fabs(dy);
-                        s[11] += ea * 0.5 * dx * dx;
-                        s[12] += ea * 0.5 * fabs(dx * dy);
-                        s[13] += ea * 0.5 * dy * dy;
-                        s[17] += dla_abs * w;
                     }
                     Tr *= 1.0 - a;
                 }
@@ -515,7 +551,7 @@ void gio_backward_blend(const float* means, const float* chol, const float* colo
         }
     }
     for (int64_t g = 0; g < n; ++g) {
-        const double* s = acc + 18 * g;
+        const double* s = acc + 27 * g;
         double A, B, C;
         conic64(chol, g, &A, &B, &C);
         const double l1 = chol[3 * g], l2 = chol[3 * g + 1], l3 = chol[3 * g + 2];
@@ -523,7 +559,7 @@ void gio_backward_blend(const float* means, const float* chol, const float* colo
         const double QG11 = A * gq11 + B * gq12, QG12 = A * gq12 + B * gq22;
         const double QG21 = B * gq11 + C * gq12, QG22 = B * gq12 + C * gq22;
         const double g1 = -(QG11 * A + QG12 * B), g2 = -(QG11 * B + QG12 * C), g3 = -(QG21 * B + QG22 * C);
-        const int live = s[14] + s[15] + s[16] + s[9] + s[10] > 0.0;
+        const int live = s[14] + s[15] + s[16] + s[9] + s[10] + s[18] + s[19] + s[23] > 0.0;
         g_means[2 * g] = s[0];
         g_means[2 * g + 1] = s[1];
         g_chol[3 * g] = live ? 2.0 * g1 * l1 + 2.0 * g2 * l2 : 0.0;
@@ -533,23 +569,8 @@ void gio_backward_blend(const float* means, const float* chol, const float* colo
         g_color[3 * g + 1] = s[6];
         g_color[3 * g + 2] = s[7];
         g_opac[g] = s[8];
-        if (g_abs) {
-            double* ab = g_abs + 9 * g;
-            const double am0 = s[9], am1 = s[10], am2 = s[11], am3 = s[12], am4 = s[13];
-            ab[0] = fabs(A) * am0 + fabs(B) * am1;
-            ab[1] = fabs(B) * am0 + fabs(C) * am1;
-            const double k11a = A * A * l1 + A * B * l2, k12a = 2.0 * A * B * l1 + (A * C + B * B) * l2,
-                         k22a = B * B * l1 + B * C * l2;
-            const double k11b = A * B * l1 + B * B * l2, k12b = (A * C + B * B) * l1 + 2.0 * B * C * l2,
-                         k22b = B * C * l1 + C * C * l2;
-            ab[2] = live ? 2.0 * (fabs(k11a) * am2 + fabs(k12a) * am3 + fabs(k22a) * am4) : 0.0;
-            ab[3] = live ? 2.0 * (fabs(k11b) * am2 + fabs(k12b) * am3 + fabs(k22b) * am4) : 0.0;
-            ab[4] = live ? 2.0 * fabs(l3) * (B * B * am2 + 2.0 * fabs(B * C) * am3 + C * C * am4) : 0.0;
-            ab[5] = s[14];
-            ab[6] = s[15];
-            ab[7] = s[16];
-            ab[8] = s[17];
-        }
+        if (g_abs) chain_abs(s + 9, A, B, C, l1, l2, l3, live, g_abs + 9 * g);
+        if (g_abs_amb) chain_abs(s + 18, A, B, C, l1, l2, l3, live, g_abs_amb + 9 * g);
     }
     free(acc);
 }

@@ -27,7 +27,7 @@ DEVERR_CAPACITY, DEVERR_TIMEOUT, DEVERR_BOUNDS = 1, 2, 4
 
 (FIT_PARAMS, FIT_ADAM_M, FIT_ADAM_V, FIT_GRADS, FIT_OUT, FIT_LOSS, FIT_STEP, FIT_K, FIT_TARGET, FIT_ADAN_N,
  FIT_ADAN_GPREV, FIT_CODEC_GB, FIT_CODEBOOKS, FIT_EMA_COUNT, FIT_EMA_TOTAL, FIT_CODES, FIT_RVQ_IDX,
- FIT_CODEC_OUT) = range(18)
+ FIT_CODEC_OUT, FIT_OPACITY, FIT_N_LAST) = range(20)
 
 # Every symbol include/gi.h declares, with (restype, argtypes).
 SIGNATURES = {
@@ -65,7 +65,8 @@ class GIFitDesc(ctypes.Structure):
                 ("stage_events", i32), ("render_split", i32), ("param_mode", i32), ("optimizer", i32),
                 ("beta3", f32), ("lr_halve_every", i32), ("cov_mode", i32), ("codec_bits", i32),
                 ("codec_stages", i32), ("codec_size", i32), ("codebooks", P), ("lsq_gamma", f32 * 3),
-                ("lsq_beta", f32 * 3), ("ema_decay", f32), ("ema_eps", f32)]
+                ("lsq_beta", f32 * 3), ("ema_decay", f32), ("ema_eps", f32), ("opacity_mode", i32),
+                ("opacity_logits", P)]
 
 
 class GIError(RuntimeError):

@@ -203,6 +203,9 @@ class _DevArray:
 
 # Adan's decay factors of its three averages (Adan's 0.02, 0.08, 0.01).
 ADAN_BETAS = (0.98, 0.92, 0.99)
+# Table 3's forms: merged colour c' (the paper's), separate opacity with
+# accumulated summation ("w/o M"), separate opacity with alpha-blending ("w/o AR").
+OPACITY_MODES = {"merged": 0, "separate": 1, "blend": 2}
 CODEC_EMA_DECAY = 0.99  # codebook EMA decay (the paper gives none; the common VQ-VAE value)
 CODEC_EMA_EPS = 1e-5    # Laplace smoothing of the EMA counts
 
@@ -288,7 +291,8 @@ class Fit:
                  lr=(1e-3, 1e-2, 1e-2), betas=(0.9, 0.999), eps=1e-8, capacity: Optional[int] = None,
                  capacity_factor: float = 1.5, use_graph: bool = True, stage_events: bool = False,
                  render_split: int = 0, param_mode: str = "pixel", optimizer: str = "adam",
-                 lr_halve_every: int = 0, cov: str = "cholesky", codec: Optional[dict] = None):
+                 lr_halve_every: int = 0, cov: str = "cholesky", codec: Optional[dict] = None,
+                 opacity: str = "merged", opacity_logits: Optional[Sequence[torch.Tensor]] = None):
         lib = L.load()
         assert len(targets) == len(params) and len(targets) >= 1
         self.shapes = [(int(t.shape[1]), int(t.shape[0])) for t in targets]
@@ -334,6 +338,15 @@ class Fit:
                            int(stage_events), int(render_split), int(param_mode == "paper"),
                            int(optimizer == "adan"), float(betas[2]) if optimizer == "adan" else 0.0,
                            int(lr_halve_every), int(cov == "rs"))
+        if opacity not in OPACITY_MODES:
+            raise ValueError(f"opacity must be one of {tuple(OPACITY_MODES)}")
+        self.opacity_mode = opacity
+        desc.opacity_mode = OPACITY_MODES[opacity]
+        if opacity != "merged" and opacity_logits is not None:
+            lg = torch.cat([_dev(x, torch.float32, "opacity_logits").reshape(-1) for x in opacity_logits]).contiguous()
+            assert lg.numel() == sum(self.counts)
+            self._logits_init = lg
+            desc.opacity_logits = lg.data_ptr()
         self.codec = None
         if codec is not None:
             cb = _dev(codec["codebooks"], torch.float32, "codebooks").contiguous()
@@ -373,6 +386,15 @@ class Fit:
             self.codes = self._view(L.FIT_CODES, (N, 4), "|u1")
             self.rvq_idx = self._view(L.FIT_RVQ_IDX, (M, N), "|u1")
             self.codec_out = self._view(L.FIT_CODEC_OUT, (7,), "<f8")
+        if self.opacity_mode != "merged":
+            base = ctypes.c_void_p()
+            L.check(L.load().gi_fit_pointer(self._h_fit, L.FIT_OPACITY, ctypes.byref(base)), "gi_fit_pointer")
+            row = (N * 4 + 255) // 256 * 256
+            rows = [torch.as_tensor(_DevArray(base.value + i * row, (N,), "<f4"), device=self.device) for i in range(7)]
+            (self.opacity_logit, self.opacity, self.opacity_m, self.opacity_v, self.opacity_n, self.opacity_gprev,
+             self.opacity_grad) = rows
+            if self.opacity_mode == "blend":
+                self.n_last = self._view(L.FIT_N_LAST, (npix,), "<i4")
 
     def _view(self, what, shape, typestr):
         p = ctypes.c_void_p()
@@ -415,6 +437,10 @@ class Fit:
         if self.optimizer == "adan":
             sd["adan_n"] = self.adan_n.clone()
             sd["adan_gprev"] = self.adan_gprev.clone()
+        sd["opacity"] = self.opacity_mode
+        if self.opacity_mode != "merged":
+            for k in ("opacity_logit", "opacity_m", "opacity_v", "opacity_n", "opacity_gprev"):
+                sd[k] = getattr(self, k).clone()
         if self.codec is not None:
             sd["codec"] = dict(self.codec)
             for k in ("codec_gb", "codebooks", "ema_count", "ema_total"):
@@ -427,7 +453,7 @@ class Fit:
         if list(sd["shapes"]) != list(self.shapes) or list(sd["counts"]) != list(self.counts) or \
                 sd["tile"] != self.tile or sd.get("param_mode", "pixel") != self.param_mode or \
                 sd.get("optimizer", "adam") != self.optimizer or sd.get("cov", "cholesky") != self.cov or \
-                sd.get("codec") != self.codec:
+                sd.get("codec") != self.codec or sd.get("opacity", "merged") != self.opacity_mode:
             raise ValueError("checkpoint of a different fit (images, Gaussian counts, tile edge, "
                              "parameterisation or optimiser)")
         self.params.copy_(sd["params"])
@@ -438,6 +464,9 @@ class Fit:
             self.adan_gprev.copy_(sd["adan_gprev"])
         if self.codec is not None:
             for k in ("codec_gb", "codebooks", "ema_count", "ema_total"):
+                getattr(self, k).copy_(sd[k])
+        if self.opacity_mode != "merged":
+            for k in ("opacity_logit", "opacity_m", "opacity_v", "opacity_n", "opacity_gprev"):
                 getattr(self, k).copy_(sd[k])
         self.step_count.fill_(int(sd["step"]))
 

@@ -298,7 +298,25 @@ __device__ void codec_block_partials(const CodecCfg& Q, const float (&gb)[6], co
 // up to eight pair-partial rows at once, so the thread waits for about two
 // memory round trips. Per slot the partials are summed in emission order,
 // Kahan-compensated.
-template <bool ADAM, bool CODEC = false>
+// The optimiser step of one scalar parameter (Adam, or Adan without weight
+// decay), with the block's bias corrections s_bc and step count.
+__device__ __forceinline__ float opt_step(const AdamCfg& cfg, const float* s_bc, int step, float lr, float gr, float p,
+                                          float& m, float& v, float* n, float* gp) {
+    if (cfg.optimizer == 1) {
+        const float dg = step == 1 ? 0.f : gr - *gp;
+        m = cfg.beta1 * m + (1.f - cfg.beta1) * gr;
+        v = cfg.beta2 * v + (1.f - cfg.beta2) * dg;
+        const float ge = gr + cfg.beta2 * dg;
+        *n = cfg.beta3 * *n + (1.f - cfg.beta3) * ge * ge;
+        *gp = gr;
+        return p - lr * (m * s_bc[0] + cfg.beta2 * (v * s_bc[1])) / (sqrtf(*n) * s_bc[2] + cfg.eps);
+    }
+    m = cfg.beta1 * m + (1.f - cfg.beta1) * gr;
+    v = cfg.beta2 * v + (1.f - cfg.beta2) * gr * gr;
+    return p - (lr * s_bc[0]) * m / (sqrtf(v) * s_bc[1] + cfg.eps);
+}
+
+template <bool ADAM, bool CODEC = false, int OPAC = 0>
 __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restrict__ partial,
                                                 const int64_t* __restrict__ pair_off,
                                                 const int32_t* __restrict__ cnt, int64_t capacity, int n,
@@ -482,6 +500,31 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
                         cv_commit += r0 * r0 + r1 * r1 + r2 * r2;
                     }
                 }
+            }
+            float g_logit = 0.f;
+            if constexpr (OPAC > 0) {
+                // Separate opacity o = sigmoid(logit): accumulated summation
+                // rendered c' = c o, so dL/dc = dL/dc' o and dL/do = dL/dc' . c;
+                // alpha-blending summed dL/do per pair (ninth sum).
+                const float o = B.opac.o[g];
+                float dldo;
+                if constexpr (OPAC == 1) {
+                    dldo = gr[5] * pp[5] + gr[6] * pp[6] + gr[7] * pp[7];
+                    gr[5] *= o;
+                    gr[6] *= o;
+                    gr[7] *= o;
+                } else {
+                    float s = 0.f, cs = 0.f;
+                    for (int64_t q = p0; q < p1; ++q) kahan_add(s, cs, B.opac.partial[q]);
+                    dldo = s - cs;
+                }
+                g_logit = c > 0 ? dldo * o * (1.f - o) : 0.f;
+                B.opac.grad[g] = g_logit;
+                float lm = B.opac.m[g], lv = B.opac.v[g];
+                B.opac.logit[g] = opt_step(cfg, s_bc, s_step, cfg.lr[2] * s_bc[3], g_logit, B.opac.logit[g], lm, lv,
+                                           B.opac.n + g, B.opac.gp + g);
+                B.opac.m[g] = lm;
+                B.opac.v[g] = lv;
             }
             if (cfg.param_mode == 1 && c > 0) {
                 // d mu / d theta = (1 - tanh^2(theta)) / 2 * (W, H)
@@ -688,9 +731,12 @@ cudaError_t launch_reduce(const float4* partial, const int64_t* pair_off, const 
     const int blocks = std::max(1, (n + kReduceThreads - 1) / kReduceThreads);
     if (adam) {
         const bool codec = B.codec.bits > 0;
-        cudaError_t e = launch_pdl(codec ? k_reduce<true, true> : k_reduce<true, false>, dim3(blocks),
-                                   dim3(kReduceThreads), 0, s, partial, pair_off, cnt, capacity, n, P, (float*)nullptr,
-                                   (float*)nullptr, (float*)nullptr, (float*)nullptr, *adam, params, m, v, grads_aos, B);
+        auto kern = codec ? k_reduce<true, true, 0>
+                          : (B.opac.mode == 1 ? k_reduce<true, false, 1>
+                                              : (B.opac.mode == 2 ? k_reduce<true, false, 2> : k_reduce<true, false, 0>));
+        cudaError_t e = launch_pdl(kern, dim3(blocks), dim3(kReduceThreads), 0, s, partial, pair_off, cnt, capacity, n,
+                                   P, (float*)nullptr, (float*)nullptr, (float*)nullptr, (float*)nullptr, *adam, params,
+                                   m, v, grads_aos, B);
         if (e != cudaSuccess || B.codec.bits == 0) return e;
         const int nv = 6 + B.codec.stages * B.codec.size * 4 + 1;
         return launch_pdl(k_codec_update, dim3(nv), dim3(kCodecSumThreads), 0, s, B.codec, *adam, blocks, n);

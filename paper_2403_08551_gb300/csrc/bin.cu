@@ -101,6 +101,18 @@ __global__ void __launch_bounds__(kProjBlock) k_project(ParamsIn P, Batch B, flo
         }
         float cr = P.color[(int64_t)g * P.cs], cg = P.color[(int64_t)g * P.cs + 1],
               cb = P.color[(int64_t)g * P.cs + 2];
+        if (B.opac.mode > 0) {
+            // Separate opacity o = sigmoid(logit) (FP64, one rounding). With
+            // accumulated summation the record carries c' = c o (Eq. 5); the
+            // blending render reads o itself and the record keeps c.
+            const float o = (float)__ddiv_rn(1.0, __dadd_rn(1.0, exp(-(double)B.opac.logit[g])));
+            B.opac.o[g] = o;
+            if (B.opac.mode == 1) {
+                cr = __fmul_rn(cr, o);
+                cg = __fmul_rn(cg, o);
+                cb = __fmul_rn(cb, o);
+            }
+        }
         if (B.codec.bits > 0) {
             // Codec fine-tuning (Sec. 3.3): FP16 positions, b-bit Cholesky
             // vector, greedy RVQ colour; the codes are the encoded stream.

@@ -75,6 +75,28 @@ struct CodecCfg {
 
 __device__ __forceinline__ int codec_nvals(const CodecCfg& c) { return 6 + c.stages * c.size * 4 + 1; }
 
+// Separate opacity (the basic 2D Gaussian of Sec. 3.1, Table 3's "w/o M"):
+// o = sigmoid(logit) per Gaussian. mode 1: accumulated summation with
+// c' = c o (Eq. 5); mode 2: sorted alpha-blending (Eq. 3-4, "w/o AR").
+struct OpacCfg {
+    int32_t mode;        // 0: merged colour (c' stored directly)
+    float* logit;        // [N] parameter
+    float* o;            // [N] sigmoid(logit) of the last formation
+    float* m;            // [N] optimiser state
+    float* v;
+    float* n;            // [N] Adan only
+    float* gp;           // [N] Adan only
+    float* grad;         // [N] dL/dlogit of the last step
+    float* partial;      // [capacity] mode 2: per-pair sum of dL/dalpha w
+    int32_t* n_last;     // [pixels] mode 2: list entries each pixel walked
+};
+
+// 3D GS's alpha-blending thresholds: skip alpha < 1/255, clamp alpha to
+// 0.99, stop before the transmittance falls below 1e-4.
+constexpr float kBlendAlphaMin = 1.0f / 255.0f;
+constexpr float kBlendAlphaMax = 0.99f;
+constexpr float kBlendTMin = 1e-4f;
+
 // Either a single image (by value) or nimg > 1 images in device memory.
 struct Batch {
     ImgDesc one;
@@ -89,6 +111,7 @@ struct Batch {
     int32_t cov_mode;     // 0: covariance slots hold the Cholesky vector (l1, l2, l3);
                           // 1: rotation-scaling form (theta, s1, s2), Sigma = (R S)(R S)^T
     CodecCfg codec;       // quantisation-aware fine-tuning (fit contexts only)
+    OpacCfg opac;         // separate opacity / alpha-blending (fit contexts only)
 };
 
 // b-bit asymmetric quantiser of one Cholesky component (Sec. 3.3, LSQ+ form):

@@ -86,8 +86,11 @@ cudaError_t enqueue_forward(gi_fit* f, cudaStream_t s, bool train) {
     if (e == cudaSuccess && train) e = mark(f, 2, s);
     if (e == cudaSuccess) {
         NvtxRange r("gi:render");
-        e = launch_render(f->rec_binned, f->ranges, f->B, train ? f->targets : nullptr, f->out, nullptr,
-                          train ? f->dl_tiled : nullptr, train ? f->loss : nullptr, device_status(), s);
+        e = f->B.opac.mode == 2
+                ? launch_render_blend(f->rec_binned, f->ids, f->ranges, f->B, train ? f->targets : nullptr, f->out,
+                                      train ? f->dl_tiled : nullptr, train ? f->loss : nullptr, device_status(), s)
+                : launch_render(f->rec_binned, f->ranges, f->B, train ? f->targets : nullptr, f->out, nullptr,
+                                train ? f->dl_tiled : nullptr, train ? f->loss : nullptr, device_status(), s);
     }
     if (e == cudaSuccess && train) e = mark(f, 3, s);
     return e;
@@ -98,8 +101,11 @@ cudaError_t enqueue_step(gi_fit* f, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     {
         NvtxRange r("gi:backward");
-        e = launch_backward(f->rec_binned, f->keys, f->ids, f->rect, f->pair_off, f->dl_tiled, f->B, f->k_dev,
-                            f->capacity, f->partial, device_status(), s);
+        e = f->B.opac.mode == 2
+                ? launch_backward_blend(f->rec_binned, f->ids, f->ranges, f->rect, f->pair_off, f->B, f->out,
+                                        f->dl_tiled, f->capacity, f->partial, device_status(), s)
+                : launch_backward(f->rec_binned, f->keys, f->ids, f->rect, f->pair_off, f->dl_tiled, f->B, f->k_dev,
+                                  f->capacity, f->partial, device_status(), s);
     }
     if (e == cudaSuccess) e = mark(f, 4, s);
     if (e == cudaSuccess) {
@@ -153,6 +159,10 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
     if ((reinterpret_cast<uintptr_t>(d->params) & 15) != 0)
         return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: params must be 16-byte aligned");
     const bool codec = d->codec_bits != 0;
+    if (d->opacity_mode < 0 || d->opacity_mode > 2 || (d->opacity_mode == 2 && d->tile != 16) ||
+        (d->opacity_mode != 0 && (codec || d->cov_mode != 0)))
+        return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: opacity_mode must be 0, 1 or 2 (2 needs tile 16; "
+                                             "neither 1 nor 2 combines with the codec or the rotation-scaling form)");
     if (codec) {
         if (d->codec_bits < 1 || d->codec_bits > 8 || d->codec_stages < 1 || d->codec_stages > kCodecMaxStages ||
             d->codec_size < 1 || d->codec_size > kCodecMaxSize || !d->codebooks)
@@ -227,6 +237,9 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
         codec ? up256((size_t)N * d->codec_stages) : 0,                   // 28 RVQ indices
         codec ? up256((size_t)kCodecMaxVals * 8 * ((N + 127) / 128)) : 0,  // 29 per-block partials
         codec ? up256((size_t)kCodecMaxVals * 8) + 256 : 0,               // 30 totals, ticket, out
+        d->opacity_mode ? 7 * up256((size_t)N * 4) : 0,                   // 31 opacity state
+        d->opacity_mode == 2 ? up256((size_t)f->capacity * 4) : 0,        // 32 per-pair opacity sums
+        d->opacity_mode == 2 ? up256((size_t)P * 4) : 0,                  // 33 per-pixel walk lengths
     };
     size_t total = 0;
     for (size_t x : sz) total += x;
@@ -283,6 +296,21 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
     f->B.param_mode = d->param_mode;
     f->adam.cov_mode = d->cov_mode;
     f->B.cov_mode = d->cov_mode;
+    if (d->opacity_mode) {
+        OpacCfg& O = f->B.opac;
+        O.mode = d->opacity_mode;
+        float* o = reinterpret_cast<float*>(at(31));
+        const size_t st = up256((size_t)N * 4) / 4;
+        O.logit = o;
+        O.o = o + st;
+        O.m = o + 2 * st;
+        O.v = o + 3 * st;
+        O.n = o + 4 * st;
+        O.gp = o + 5 * st;
+        O.grad = o + 6 * st;
+        O.partial = d->opacity_mode == 2 ? reinterpret_cast<float*>(at(32)) : nullptr;
+        O.n_last = d->opacity_mode == 2 ? reinterpret_cast<int32_t*>(at(33)) : nullptr;
+    }
     std::vector<float> gb_init(30, 0.f);
     std::vector<float> cb_host;
     std::vector<double> ema_c, ema_t;
@@ -331,6 +359,8 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
     FIT_TRY(cudaMemcpyAsync(f->d_desc, desc.data(), sizeof(ImgDesc) * desc.size(), cudaMemcpyHostToDevice, s));
     FIT_TRY(cudaMemcpyAsync(f->params, d->params, (size_t)gauss * 32, cudaMemcpyDeviceToDevice, s));
     FIT_TRY(cudaMemcpyAsync(f->targets, d->targets, (size_t)pix * 12, cudaMemcpyDeviceToDevice, s));
+    if (d->opacity_mode && d->opacity_logits && gauss > 0)
+        FIT_TRY(cudaMemcpyAsync(f->B.opac.logit, d->opacity_logits, (size_t)gauss * 4, cudaMemcpyDeviceToDevice, s));
     if (codec) {
         const CodecCfg& Q = f->B.codec;
         FIT_TRY(cudaMemcpyAsync(Q.gb, gb_init.data(), 30 * sizeof(float), cudaMemcpyHostToDevice, s));
@@ -406,6 +436,8 @@ gi_status gi_fit_pointer(gi_fit* f, int32_t what, void** ptr) {
         case GI_FIT_CODES: *ptr = f->B.codec.codes; break;
         case GI_FIT_RVQ_IDX: *ptr = f->B.codec.idx; break;
         case GI_FIT_CODEC_OUT: *ptr = f->B.codec.out; break;
+        case GI_FIT_OPACITY: *ptr = f->B.opac.logit; break;
+        case GI_FIT_N_LAST: *ptr = f->B.opac.n_last; break;
         default: return set_error(GI_ERR_INVALID_ARG, "gi_fit_pointer: unknown field %d", what);
     }
     return GI_OK;

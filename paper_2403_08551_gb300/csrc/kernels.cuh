@@ -92,6 +92,16 @@ cudaError_t launch_render(const float4* rec_binned, const int2* ranges, const Ba
                           const float* target, float* out, float* dl_hwc, float* dl_tiled,
                           double* loss_sum, uint32_t* status, cudaStream_t s);
 
+// Sorted alpha-blending render (Eq. 3-4) and its backward (blend.cu), tile 16
+// only; opacity, per-pixel walk lengths and the ninth per-pair sum live in
+// B.opac.
+cudaError_t launch_render_blend(const float4* rec_binned, const uint32_t* ids, const int2* ranges, const Batch& B,
+                                const float* target, float* out, float* dl_tiled, double* loss_sum, uint32_t* status,
+                                cudaStream_t s);
+cudaError_t launch_backward_blend(const float4* rec_binned, const uint32_t* ids, const int2* ranges, const int4* rect,
+                                  const int64_t* pair_off, const Batch& B, const float* out, const float* dl_tiled,
+                                  int64_t capacity, float4* partial, uint32_t* status, cudaStream_t s);
+
 // Backward: per-pair partial sums (8 floats per pair at its emission index).
 cudaError_t launch_backward(const float4* rec_binned, const uint32_t* keys, const uint32_t* ids,
                             const int4* rect, const int64_t* pair_off, const float* dl_tiled,
