@@ -431,6 +431,54 @@ def large_image(gi, torch, stream, flush, T=16, reps=20):
     return out
 
 
+def ablation(gi, torch, stream, flush, T=16, reps=100, fit_steps=10000):
+    """Table 3's representation ablation on the 768x512, 70k-Gaussian
+    workload: the paper's merged colour (8 parameters, accumulated
+    summation), separate opacity with accumulated summation ("w/o M", 9
+    parameters) and sorted alpha-blending ("w/o AR + w/o M"). The
+    9-parameter forms start from c = 2 c', o = sigmoid(0) = 1/2 (the same
+    initial accumulated image). Per form: fit-step and render time (L2
+    flushed before each), and the PSNR after `fit_steps` Adam steps."""
+    w = synth.workload(WORKLOAD)
+    tgt = torch.from_numpy(w.target).cuda()
+    psnr = lambda e: 10 * math.log10(1.0 / e) if e > 0 else float("inf")  # noqa: E731
+    out = {}
+    for form in ("merged", "separate", "blend"):
+        p = pack(w)
+        kw = {}
+        if form != "merged":
+            p = p.copy()
+            p[:, 5:8] *= 2.0
+            kw = {"opacity": form, "opacity_logits": [torch.zeros(w.n, device="cuda")]}
+        fit = gi.Fit([tgt], [torch.from_numpy(p).cuda()], tile=T, lr=LR, capacity_factor=4.0, **kw)
+        fit.step(3)
+        step_ms = _time(torch, stream, lambda: fit.step(1), reps, flush)
+        render_ms = _time(torch, stream, fit.render, reps, flush)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fit.step(fit_steps - 3 - reps)
+        e1.record(stream)
+        e1.synchronize()
+        long_s = e0.elapsed_time(e1) / 1e3
+        fit.render()
+        torch.cuda.synchronize()
+        img = fit.images()[0]
+        out[form] = {"fit_iter_s": 1e3 / step_ms, "fit_step_ms": step_ms, "render_fps": 1e3 / render_ms,
+                     "render_ms": render_ms, "steady_iter_s": (fit_steps - 3 - reps) / long_s,
+                     "psnr_db": psnr(float(((img.clamp(0, 1) - tgt) ** 2).mean())), "steps": fit_steps,
+                     "params_per_gaussian": 8 if form == "merged" else 9,
+                     "device_errors": int(gi.device_errors(clear=True))}
+        fit.close()
+    base = out["merged"]
+    for form in ("separate", "blend"):
+        out[form]["step_time_vs_merged"] = out[form]["fit_step_ms"] / base["fit_step_ms"]
+        out[form]["render_time_vs_merged"] = out[form]["render_ms"] / base["render_ms"]
+    out["paper_context"] = {"fps": {"w/o AR + w/o M": 2340, "w/o M": 2555, "merged": 2565},
+                            "train_s": {"w/o AR + w/o M": 104.76, "w/o M": 98.54, "merged": 91.06},
+                            "hw": "V100, Kodak, 30k Gaussians, 50k steps (Table 3)"}
+    return out
+
+
 def codec_decode(gi, torch, stream, flush, T=16, reps=50):
     """RVQ decode (FP16 means, 2-stage 256-entry codebooks) then render, at
     768x512 with 50,000 Gaussians; and decode alone over a batch of 64 such
@@ -617,6 +665,7 @@ def main():
     if not args.no_extra and rank == 0:
         out["large_image"] = large_image(gi, torch, stream, flush)
         out["codec"] = codec_decode(gi, torch, stream, flush)
+        out["ablation"] = ablation(gi, torch, stream, flush)
     if args.long_steps > 1 and not args.no_extra and rank == 0:
         out["fit_long"] = long_fit(gi, torch, stream, T, args.long_steps,
                                    os.path.join(args.out, "fit_long_psnr.jsonl"))
