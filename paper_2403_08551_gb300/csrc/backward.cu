@@ -240,6 +240,7 @@ __global__ void k_pack_dl(const float* __restrict__ dl, Batch B, float* __restri
 }
 
 constexpr int kReduceThreads = 128;
+constexpr int kReduceRows = 128;  // pair rows a warp stages per chunk
 
 // Codec sums, stage 1 (Sec. 3.3-3.4): per block, dL/dgamma, dL/dbeta, the
 // commitment term and, per RVQ stage and codebook entry, the count and the
@@ -293,11 +294,6 @@ __device__ void codec_block_partials(const CodecCfg& Q, const float (&gb)[6], co
     }
 }
 
-// One thread per Gaussian. Every load that does not depend on another is
-// issued first (parameters, Adam state, Cholesky vector, pair offset), then
-// up to eight pair-partial rows at once, so the thread waits for about two
-// memory round trips. Per slot the partials are summed in emission order,
-// Kahan-compensated.
 // The optimiser step of one scalar parameter (Adam, or Adan without weight
 // decay), with the block's bias corrections s_bc and step count.
 __device__ __forceinline__ float opt_step(const AdamCfg& cfg, const float* s_bc, int step, float lr, float gr, float p,
@@ -316,6 +312,12 @@ __device__ __forceinline__ float opt_step(const AdamCfg& cfg, const float* s_bc,
     return p - (lr * s_bc[0]) * m / (sqrtf(v) * s_bc[1] + cfg.eps);
 }
 
+// One thread per Gaussian. A warp's 32 Gaussians own one contiguous range of
+// pair rows, which the warp stages through shared memory in coalesced chunks;
+// per slot each Gaussian's rows are summed in emission order, Kahan-
+// compensated. Then the conic and Cholesky chain (App. A.2), the chains of
+// the parameterisation, covariance form, codec and opacity modes, and the
+// optimiser step.
 template <bool ADAM, bool CODEC = false, int OPAC = 0>
 __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restrict__ partial,
                                                 const int64_t* __restrict__ pair_off,
@@ -324,7 +326,6 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
                                                 float* __restrict__ g_color, float* __restrict__ g_conic,
                                                 AdamCfg cfg, float* __restrict__ params, float* __restrict__ m,
                                                 float* __restrict__ v, float* __restrict__ grads_aos, Batch B) {
-    constexpr int kBatch = 8;
     __shared__ int s_step;
     // Adam: 1/(1 - b1^t), 1/sqrt(1 - b2^t); Adan: 1/(1 - b1^t), 1/(1 - b2^t),
     // 1/sqrt(1 - b3^t); [3] = learning-rate factor of the halving schedule.
@@ -347,6 +348,58 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
         __syncthreads();
     }
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    // Pair rows of the warp's 32 consecutive Gaussians are contiguous (emission
+    // order): the warp streams them through shared memory with coalesced loads,
+    // then each lane adds its own rows in emission order (Kahan), the same
+    // order and arithmetic as reading them one by one.
+    __shared__ float4 s_rows[kReduceThreads / 32][kReduceRows][2];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int64_t p0 = 0, p1 = 0;
+    int c = 0;
+    if (g < n) {
+        c = cnt[g];
+        p0 = pair_off[g];
+        p1 = min(p0 + (int64_t)c, capacity);
+    }
+    float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    float ca[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    {
+        const unsigned valid = __ballot_sync(0xffffffffu, g < n);
+        if (valid) {
+            const int64_t R0 = __shfl_sync(0xffffffffu, p0, __ffs(valid) - 1);
+            const int64_t R1 = __shfl_sync(0xffffffffu, p1, 31 - __clz(valid));
+            for (int64_t c0 = R0; c0 < R1; c0 += kReduceRows) {
+                const int nr = (int)min((int64_t)kReduceRows, R1 - c0);
+                float4 x[kReduceRows / 32], y[kReduceRows / 32];
+#pragma unroll
+                for (int i = 0; i < kReduceRows / 32; ++i) {
+                    const int r = lane + 32 * i;
+                    if (r < nr) {
+                        x[i] = partial[2 * (c0 + r)];
+                        y[i] = partial[2 * (c0 + r) + 1];
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < kReduceRows / 32; ++i) {
+                    const int r = lane + 32 * i;
+                    if (r < nr) {
+                        s_rows[wid][r][0] = x[i];
+                        s_rows[wid][r][1] = y[i];
+                    }
+                }
+                __syncwarp();
+                const int64_t q1 = min(p1, c0 + nr);
+                for (int64_t q = max(p0, c0); q < q1; ++q) {
+                    const float4 u = s_rows[wid][q - c0][0], w = s_rows[wid][q - c0][1];
+                    kahan_add(a[0], ca[0], u.x); kahan_add(a[1], ca[1], u.y);
+                    kahan_add(a[2], ca[2], u.z); kahan_add(a[3], ca[3], u.w);
+                    kahan_add(a[4], ca[4], w.x); kahan_add(a[5], ca[5], w.y);
+                    kahan_add(a[6], ca[6], w.z); kahan_add(a[7], ca[7], w.w);
+                }
+                __syncwarp();
+            }
+        }
+    }
     // codec fine-tuning: this Gaussian's dL/dgamma, dL/dbeta terms, RVQ indices,
     // stage residuals and commitment term (zero when off or g >= n)
     float cv_gb[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -384,38 +437,6 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
             l1 = lsq_quant(l1, Q.gb[0], Q.gb[3], Q.qp, cx[0], cq[0]);
             l2 = lsq_quant(l2, Q.gb[1], Q.gb[4], Q.qp, cx[1], cq[1]);
             l3 = lsq_quant(l3, Q.gb[2], Q.gb[5], Q.qp, cx[2], cq[2]);
-        }
-        const int c = cnt[g];
-        const int64_t p0 = pair_off[g];
-        const int64_t p1 = min(p0 + (int64_t)c, capacity);
-        const int np = (int)max((int64_t)0, p1 - p0);
-        float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        float ca[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        {
-            float4 x[kBatch], y[kBatch];
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                if (u < np) {
-                    x[u] = partial[2 * (p0 + u)];
-                    y[u] = partial[2 * (p0 + u) + 1];
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kBatch; ++u) {
-                if (u < np) {
-                    kahan_add(a[0], ca[0], x[u].x); kahan_add(a[1], ca[1], x[u].y);
-                    kahan_add(a[2], ca[2], x[u].z); kahan_add(a[3], ca[3], x[u].w);
-                    kahan_add(a[4], ca[4], y[u].x); kahan_add(a[5], ca[5], y[u].y);
-                    kahan_add(a[6], ca[6], y[u].z); kahan_add(a[7], ca[7], y[u].w);
-                }
-            }
-        }
-        for (int64_t p = p0 + kBatch; p < p1; ++p) {
-            const float4 x = partial[2 * p], y = partial[2 * p + 1];
-            kahan_add(a[0], ca[0], x.x); kahan_add(a[1], ca[1], x.y);
-            kahan_add(a[2], ca[2], x.z); kahan_add(a[3], ca[3], x.w);
-            kahan_add(a[4], ca[4], y.x); kahan_add(a[5], ca[5], y.y);
-            kahan_add(a[6], ca[6], y.z); kahan_add(a[7], ca[7], y.w);
         }
 #pragma unroll
         for (int s = 0; s < 8; ++s) a[s] -= ca[s];
