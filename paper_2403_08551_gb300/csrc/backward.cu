@@ -361,6 +361,20 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
         p0 = pair_off[g];
         p1 = min(p0 + (int64_t)c, capacity);
     }
+    // Parameters and optimiser state do not depend on the partials: their
+    // loads are issued first and overlap the staging below.
+    float pp[8], mm[8], vv[8];
+    float4* P4 = nullptr;
+    float4* M4 = nullptr;
+    float4* V4 = nullptr;
+    if (ADAM && g < n) {
+        P4 = reinterpret_cast<float4*>(params) + 2 * (size_t)g;
+        M4 = reinterpret_cast<float4*>(m) + 2 * (size_t)g;
+        V4 = reinterpret_cast<float4*>(v) + 2 * (size_t)g;
+        *reinterpret_cast<float4*>(pp) = P4[0]; *reinterpret_cast<float4*>(pp + 4) = P4[1];
+        *reinterpret_cast<float4*>(mm) = M4[0]; *reinterpret_cast<float4*>(mm + 4) = M4[1];
+        *reinterpret_cast<float4*>(vv) = V4[0]; *reinterpret_cast<float4*>(vv + 4) = V4[1];
+    }
     float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     float ca[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     {
@@ -407,18 +421,6 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
     float cv_r[kCodecMaxStages][3] = {};
     float cv_commit = 0.f;
     if (g < n) {
-        float pp[8], mm[8], vv[8];
-        float4* P4 = nullptr;
-        float4* M4 = nullptr;
-        float4* V4 = nullptr;
-        if (ADAM) {
-            P4 = reinterpret_cast<float4*>(params) + 2 * (size_t)g;
-            M4 = reinterpret_cast<float4*>(m) + 2 * (size_t)g;
-            V4 = reinterpret_cast<float4*>(v) + 2 * (size_t)g;
-            *reinterpret_cast<float4*>(pp) = P4[0]; *reinterpret_cast<float4*>(pp + 4) = P4[1];
-            *reinterpret_cast<float4*>(mm) = M4[0]; *reinterpret_cast<float4*>(mm + 4) = M4[1];
-            *reinterpret_cast<float4*>(vv) = V4[0]; *reinterpret_cast<float4*>(vv + 4) = V4[1];
-        }
         float l1 = P.chol[(int64_t)g * P.ls], l2 = P.chol[(int64_t)g * P.ls + 1], l3 = P.chol[(int64_t)g * P.ls + 2];
         const bool rs_mode = ADAM && cfg.cov_mode == 1;
         if (ADAM && cfg.param_mode == 1) {  // App. C.1: +0.5 on the Cholesky diagonal or on the scales
@@ -577,7 +579,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
                     const float ge = gr[s] + cfg.beta2 * dg;
                     nn[s] = cfg.beta3 * nn[s] + (1.f - cfg.beta3) * ge * ge;
                     const float dir = mm[s] * s_bc[0] + cfg.beta2 * (vv[s] * s_bc[1]);
-                    pp[s] -= lr * dir / (sqrtf(nn[s]) * s_bc[2] + cfg.eps);
+                    pp[s] -= __fdividef(lr * dir, sqrt_approx(nn[s]) * s_bc[2] + cfg.eps);
                     gp[s] = gr[s];
                 }
                 N4[0] = *reinterpret_cast<float4*>(nn); N4[1] = *reinterpret_cast<float4*>(nn + 4);
@@ -588,8 +590,8 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
                     const float lr = cfg.lr[s < 2 ? 0 : (s < 5 ? 1 : 2)] * s_bc[3];
                     mm[s] = cfg.beta1 * mm[s] + (1.f - cfg.beta1) * gr[s];
                     vv[s] = cfg.beta2 * vv[s] + (1.f - cfg.beta2) * gr[s] * gr[s];
-                    const float denom = sqrtf(vv[s]) * s_bc[1] + cfg.eps;
-                    pp[s] -= (lr * s_bc[0]) * mm[s] / denom;
+                    const float denom = sqrt_approx(vv[s]) * s_bc[1] + cfg.eps;
+                    pp[s] -= __fdividef((lr * s_bc[0]) * mm[s], denom);
                 }
             }
             P4[0] = *reinterpret_cast<float4*>(pp); P4[1] = *reinterpret_cast<float4*>(pp + 4);

@@ -522,7 +522,7 @@ BinWs bin_ws_layout(void* base, int64_t n, int64_t capacity, int total_tiles) {
     const int64_t nblk = std::max<int64_t>(1, (n + kProjBlock - 1) / kProjBlock);
     const int64_t sblk = std::max<int64_t>(1, (capacity + kSortTile - 1) / kSortTile);
     const int64_t nchunks = std::max<int64_t>(1, (n + kCmChunk - 1) / kCmChunk);
-    const int64_t groups = std::max<int64_t>(1, (total_tiles + 31) / 32);
+    const int64_t groups = std::max<int64_t>(1, (total_tiles + kCmGroupTiles - 1) / kCmGroupTiles);
     const int64_t cap = std::max<int64_t>(1, capacity);
     char* b = static_cast<char*>(base);
     size_t off = 0;

@@ -11,7 +11,7 @@
 //   k_count   one block per two chunks: shared-memory tile histograms give
 //             the rows of M and the chunk pair totals; clears the binning
 //             scratch when asked.
-//   k_colscan one block per 32 tiles: column prefix sums over the chunks
+//   k_colscan one block per 8 tiles: column prefix sums over the chunks
 //             (P[b][t] = start[t] + sum_{b' < b} M[b'][t], written over M),
 //             chained scan of the column totals across tile groups (bounded
 //             look-back) -> start, ranges, K and the capacity check.
@@ -26,8 +26,8 @@ namespace gi {
 
 namespace {
 
-constexpr int kCmGroupTiles = 32;              // k_colscan: tiles per block (one per lane)
-constexpr int kCmScanWarps = 32;               // k_colscan: warps splitting the chunk rows
+constexpr int kCmSlabs = 32;                   // k_colscan: row slabs per tile (one warp scans them)
+constexpr int kCmScanThreads = kCmGroupTiles * kCmSlabs;  // k_colscan: one thread per (tile, slab)
 constexpr int kCmRowRegs = 24;                 // k_colscan: rows a lane keeps in registers between passes
 
 __device__ __forceinline__ void zero_words(uint32_t* p, int64_t n) {
@@ -155,27 +155,31 @@ __global__ void __launch_bounds__(kCmChunk) k_count(const int4* __restrict__ rec
 // its range). The block holding the last tile stores K, updates k_max and
 // raises the capacity error.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kCmScanWarps * 32) k_colscan(uint32_t* __restrict__ M, int nchunks, int total_tiles,
-                                                               int2* __restrict__ ranges, uint32_t* __restrict__ keys,
-                                                               int64_t capacity,
-                                                               int64_t* __restrict__ k_dev, int64_t* __restrict__ k_max,
-                                                               uint32_t* __restrict__ lookback,
-                                                               uint32_t* __restrict__ ticket,
-                                                               uint32_t* __restrict__ status) {
-    __shared__ uint32_t s_part[kCmScanWarps][32];
-    __shared__ uint32_t s_start[32];
-    __shared__ uint32_t s_col[32];
+__global__ void __launch_bounds__(kCmScanThreads) k_colscan(uint32_t* __restrict__ M, int nchunks, int total_tiles,
+                                                          int2* __restrict__ ranges, uint32_t* __restrict__ keys,
+                                                          int64_t capacity, int64_t* __restrict__ k_dev,
+                                                          int64_t* __restrict__ k_max, uint32_t* __restrict__ lookback,
+                                                          uint32_t* __restrict__ ticket,
+                                                          uint32_t* __restrict__ status) {
+    constexpr int TG = kCmGroupTiles, NS = kCmSlabs, NW = kCmScanThreads / 32;
+    static_assert(NS == 32 && TG <= NW && 32 % TG == 0, "a warp scans one tile's 32 slabs; one warp per tile");
+    __shared__ uint32_t s_part[NS][TG];
+    __shared__ uint32_t s_start[TG];
+    __shared__ uint32_t s_col[TG];
     __shared__ uint32_t s_ticket;
     pdl_wait();
     if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1u);
     __syncthreads();
     const int blk = (int)s_ticket;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int t = blk * kCmGroupTiles + lane;
+    // thread -> (tile ti of the group, row slab sl): TG consecutive tiles of one
+    // slab row are one contiguous 4 TG-byte segment of M
+    const int ti = threadIdx.x % TG, sl = threadIdx.x / TG;
+    const int t = blk * TG + ti;
     const bool tv = t < total_tiles;
-    const int rs = (nchunks + kCmScanWarps - 1) / kCmScanWarps;
-    const int r0 = min(nchunks, warp * rs), r1 = min(nchunks, r0 + rs);
-    const bool in_regs = r1 - r0 <= kCmRowRegs;  // block-uniform
+    const int rs = (nchunks + NS - 1) / NS;
+    const int r0 = min(nchunks, sl * rs), r1 = min(nchunks, r0 + rs);
+    const bool in_regs = rs <= kCmRowRegs;  // block-uniform
     uint32_t sum = 0;
     uint32_t v[kCmRowRegs];
     if (tv) {
@@ -196,11 +200,10 @@ __global__ void __launch_bounds__(kCmScanWarps * 32) k_colscan(uint32_t* __restr
             for (; r < r1; ++r) sum += M[(size_t)r * total_tiles + t];
         }
     }
-    s_part[warp][lane] = sum;
+    s_part[sl][ti] = sum;
     __syncthreads();
-    {
-        // warp j scans tile j's 32 warp partials (lane = warp index) in place
-        static_assert(kCmScanWarps == 32, "one warp per tile of the group");
+    if (warp < TG) {
+        // warp j scans tile j's slab partials (lane = slab) in place
         const uint32_t x = s_part[lane][warp];
         uint32_t in = x;
 #pragma unroll
@@ -216,7 +219,7 @@ __global__ void __launch_bounds__(kCmScanWarps * 32) k_colscan(uint32_t* __restr
     }
     __syncthreads();
     if (warp == 0) {
-        const uint32_t col = s_start[lane];
+        const uint32_t col = lane < TG ? s_start[lane] : 0u;
         uint32_t incl = col;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -254,16 +257,19 @@ __global__ void __launch_bounds__(kCmScanWarps * 32) k_colscan(uint32_t* __restr
             if (lane == 0) st_relaxed_u32(lookback + blk, kFlagPre | ((excl + tot) & kValMask));
         }
         const uint32_t start = excl + incl - col;
-        s_start[lane] = start;
-        if (tv) {
-            int2 rg = make_int2(0, 0);
-            if (col) {
-                rg.x = (int)min((int64_t)start, capacity);
-                rg.y = (int)min((int64_t)start + col, capacity);
+        if (lane < TG) {
+            s_start[lane] = start;
+            const int tl = blk * TG + lane;
+            if (tl < total_tiles) {
+                int2 rg = make_int2(0, 0);
+                if (col) {
+                    rg.x = (int)min((int64_t)start, capacity);
+                    rg.y = (int)min((int64_t)start + col, capacity);
+                }
+                ranges[tl] = rg;
             }
-            ranges[t] = rg;
         }
-        if ((blk + 1) * kCmGroupTiles >= total_tiles && lane == 0) {
+        if ((blk + 1) * TG >= total_tiles && lane == 0) {
             const int64_t K = (int64_t)excl + tot;
             *k_dev = K;
             if (k_max) atomicMax(reinterpret_cast<unsigned long long*>(k_max), (unsigned long long)K);
@@ -271,38 +277,38 @@ __global__ void __launch_bounds__(kCmScanWarps * 32) k_colscan(uint32_t* __restr
         }
     }
     __syncthreads();
-    {
-        // keys: warp w writes tile (32 blk + w) over its sorted range
-        const int tk = blk * kCmGroupTiles + warp;
+    if (warp < TG) {
+        // keys: warp w writes tile (TG blk + w) over its sorted range
+        const int tk = blk * TG + warp;
         if (tk < total_tiles) {
             const int64_t s0 = s_start[warp], e0 = min(s0 + (int64_t)s_col[warp], capacity);
             for (int64_t q = s0 + lane; q < e0; q += 32) keys[q] = (uint32_t)tk;
         }
     }
     if (tv && in_regs) {
-        uint32_t run = s_start[lane] + s_part[warp][lane];
+        uint32_t run = s_start[ti] + s_part[sl][ti];
 #pragma unroll
         for (int i = 0; i < kCmRowRegs; ++i) {
             if (r0 + i < r1) M[(size_t)(r0 + i) * total_tiles + t] = run;
             run += v[i];
         }
     } else if (tv) {
-        uint32_t run = s_start[lane] + s_part[warp][lane];
+        uint32_t run = s_start[ti] + s_part[sl][ti];
         int r = r0;
         for (; r + 8 <= r1; r += 8) {
-            uint32_t v[8];
+            uint32_t u[8];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) v[i] = M[(size_t)(r + i) * total_tiles + t];
+            for (int i = 0; i < 8; ++i) u[i] = M[(size_t)(r + i) * total_tiles + t];
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 M[(size_t)(r + i) * total_tiles + t] = run;
-                run += v[i];
+                run += u[i];
             }
         }
         for (; r < r1; ++r) {
-            const uint32_t v = M[(size_t)r * total_tiles + t];
+            const uint32_t u = M[(size_t)r * total_tiles + t];
             M[(size_t)r * total_tiles + t] = run;
-            run += v;
+            run += u;
         }
     }
 }
@@ -411,7 +417,7 @@ cudaError_t launch_bin_cm(const int4* rect, const int32_t* cnt, const float4* re
                        ws.zero, ws.zero_words);
         if (e != cudaSuccess) return e;
     }
-    e = launch_pdl(k_colscan, dim3(groups), dim3(kCmScanWarps * 32), 0, s, ws.cm, nchunks, Tn, ranges, keys, capacity,
+    e = launch_pdl(k_colscan, dim3(groups), dim3(kCmScanThreads), 0, s, ws.cm, nchunks, Tn, ranges, keys, capacity,
                    k_dev, k_max, ws.lookback, ws.tickets, status);
     if (e != cudaSuccess) return e;
     static bool attr = false;  // up to 40 KB dynamic + the static layout: above the default 48 KB window
