@@ -82,8 +82,9 @@ typedef struct {
  * exp(-sigma) = exp2(-(z1^2 + z2^2)) (Sec. 3.1 with Sigma^-1 = L^-T L^-1). */
 #define GI_REC_FLOATS 8
 
-/* ABI version: 5 (gi_fit_desc gained param_mode, optimizer, beta3, lr_halve_every in 2,
- * cov_mode in 3, the codec fine-tuning fields in 4, opacity_mode and opacity_logits in 5). */
+/* ABI version: 6 (gi_fit_desc gained param_mode, optimizer, beta3, lr_halve_every in 2,
+ * cov_mode in 3, the codec fine-tuning fields in 4, opacity_mode and opacity_logits in 5;
+ * gi_fit_set_target_source in 6). */
 GI_API int32_t gi_abi_version(void);
 GI_API const char* gi_last_error(void);
 GI_API const char* gi_status_string(int32_t status);
@@ -292,6 +293,17 @@ GI_API gi_status gi_fit_step(gi_fit* fit, int32_t steps, gi_stream stream);
  * (formation, binning, Eq. 7; no loss, no dL/dC; GI_FIT_LOSS keeps the last
  * step's value). Replays a captured graph when use_graph. Asynchronous. */
 GI_API gi_status gi_fit_render(gi_fit* fit, gi_stream stream);
+/* Where the training steps read the target image(s) (Sec. 3.4's L2 loss):
+ * src = NULL selects the context's own device copy (GI_FIT_TARGET, the
+ * default); otherwise src is a buffer of the same layout (images
+ * concatenated, HWC f32) that the device can address: device memory of this
+ * device, managed memory, or pinned / registered host memory, which each
+ * step's render then reads over the host link, overlapped with its
+ * accumulation (no separate copy). The caller keeps src alive and unchanged
+ * while steps that read it are in flight. Synchronises `stream` and, with
+ * use_graph, recaptures the step graphs. GI_ERR_INVALID_ARG for pageable
+ * host memory or another device's memory. */
+GI_API gi_status gi_fit_set_target_source(gi_fit* fit, const float* src, gi_stream stream);
 
 /* Device pointers into the context (valid until gi_fit_destroy):
  *   GI_FIT_PARAMS [N][8], GI_FIT_ADAM_M [N][8], GI_FIT_ADAM_V [N][8] (the

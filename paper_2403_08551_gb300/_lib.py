@@ -46,6 +46,7 @@ SIGNATURES = {
     "gi_fit_create": (i32, [P, P, P]),
     "gi_fit_step": (i32, [P, i32, P]),
     "gi_fit_render": (i32, [P, P]),
+    "gi_fit_set_target_source": (i32, [P, P, P]),
     "gi_fit_pointer": (i32, [P, i32, P]),
     "gi_fit_destroy": (i32, [P]),
     "gi_fit_stage_times": (i32, [P, P]),

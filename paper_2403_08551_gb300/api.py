@@ -414,6 +414,22 @@ class Fit:
     def render(self):
         L.check(L.load().gi_fit_render(self._h_fit, L.stream_handle()), "gi_fit_render")
 
+    def set_target_source(self, src: Optional[torch.Tensor] = None):
+        """Train against `src` instead of the context's target copy: a CUDA
+        tensor, or a pinned CPU tensor that every step's render reads over
+        the host link (overlapped with its work, no separate copy); same
+        layout as the concatenated targets (float32, HWC). None restores the
+        context's own copy. `src` must stay alive while steps read it."""
+        ptr = None
+        if src is not None:
+            if src.dtype != torch.float32 or not src.is_contiguous() or src.numel() != self.targets.numel():
+                raise ValueError("target source must be a contiguous float32 tensor of the targets' size")
+            if src.device.type == "cpu" and not src.is_pinned():
+                raise ValueError("a CPU target source must be pinned")
+            ptr = src.data_ptr()
+        self._target_src = src
+        L.check(L.load().gi_fit_set_target_source(self._h_fit, ptr, L.stream_handle()), "gi_fit_set_target_source")
+
     def images(self) -> List[torch.Tensor]:
         outs, o = [], 0
         for W, H in self.shapes:

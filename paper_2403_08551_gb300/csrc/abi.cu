@@ -76,7 +76,7 @@ using namespace gi;
 
 extern "C" {
 
-int32_t gi_abi_version(void) { return 5; }
+int32_t gi_abi_version(void) { return 6; }
 
 const char* gi_last_error(void) { return t_err; }
 

@@ -143,17 +143,18 @@ __global__ void __launch_bounds__(kCmChunk) k_count(const int4* __restrict__ rec
 }
 
 // ---------------------------------------------------------------------------
-// Column scan: block (in ticket order) -> tiles [32 blk, 32 blk + 32), one
-// per lane; warp w -> chunk rows [w rs, (w + 1) rs). Pass 1 sums each warp's
-// rows per tile. The warp partials give every warp's offset inside the
+// Column scan: block (in ticket order) -> tiles [8 blk, 8 blk + 8); thread
+// (tile ti, slab sl) -> chunk rows [sl rs, (sl + 1) rs) of tile ti, 32 slabs.
+// Pass 1 sums each slab's rows (kept in registers when they fit). Warp j
+// scans tile j's 32 slab partials, giving every slab's offset inside the
 // column and the column totals; warp 0 scans the totals over the block's
 // tiles and chains the block total through lower tickets (warp-wide
 // look-back over 32 predecessors per round, retried until the words up to
 // the nearest inclusive prefix are all published; bounded spin). Pass 2
-// rereads the rows and writes P[r][t] = start[t] + prefix over M in place,
-// and warp w writes the sorted keys of the group's tile w (the tile id over
-// its range). The block holding the last tile stores K, updates k_max and
-// raises the capacity error.
+// writes P[r][t] = start[t] + prefix over M in place, and warp w writes the
+// sorted keys of the group's tile w (the tile id over its range). The block
+// holding the last tile stores K, updates k_max and raises the capacity
+// error.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kCmScanThreads) k_colscan(uint32_t* __restrict__ M, int nchunks, int total_tiles,
                                                           int2* __restrict__ ranges, uint32_t* __restrict__ keys,

@@ -32,6 +32,7 @@ struct gi_fit {
     ImgDesc* d_desc = nullptr;
     float *params = nullptr, *m = nullptr, *v = nullptr, *grads = nullptr;
     float *targets = nullptr, *out = nullptr;
+    const float* target_src = nullptr;  // where the render reads the target (default: targets)
     float4 *rec = nullptr, *rec_binned = nullptr, *partial = nullptr;
     float* dl_tiled = nullptr;
     int4* rect = nullptr;
@@ -87,9 +88,9 @@ cudaError_t enqueue_forward(gi_fit* f, cudaStream_t s, bool train) {
     if (e == cudaSuccess) {
         NvtxRange r("gi:render");
         e = f->B.opac.mode == 2
-                ? launch_render_blend(f->rec_binned, f->ids, f->ranges, f->B, train ? f->targets : nullptr, f->out,
+                ? launch_render_blend(f->rec_binned, f->ids, f->ranges, f->B, train ? f->target_src : nullptr, f->out,
                                       train ? f->dl_tiled : nullptr, train ? f->loss : nullptr, device_status(), s)
-                : launch_render(f->rec_binned, f->ranges, f->B, train ? f->targets : nullptr, f->out, nullptr,
+                : launch_render(f->rec_binned, f->ranges, f->B, train ? f->target_src : nullptr, f->out, nullptr,
                                 train ? f->dl_tiled : nullptr, train ? f->loss : nullptr, device_status(), s);
     }
     if (e == cudaSuccess && train) e = mark(f, 3, s);
@@ -117,12 +118,41 @@ cudaError_t enqueue_step(gi_fit* f, cudaStream_t s) {
     return e;
 }
 
-void release(gi_fit* f) {
-    if (!f) return;
+void destroy_graphs(gi_fit* f) {
     if (f->exec) cudaGraphExecDestroy(f->exec);
     if (f->graph) cudaGraphDestroy(f->graph);
     if (f->render_exec) cudaGraphExecDestroy(f->render_exec);
     if (f->render_graph) cudaGraphDestroy(f->render_graph);
+    f->exec = f->render_exec = nullptr;
+    f->graph = f->render_graph = nullptr;
+}
+
+// Captures the training step and the forward-only pass into graphs.
+cudaError_t capture_graphs(gi_fit* f) {
+    cudaError_t e = cudaStreamBeginCapture(f->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    cudaError_t ce = enqueue_step(f, f->cap_stream);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(f->cap_stream, &g);
+    f->graph = g;
+    if (ce != cudaSuccess) return ce;
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(&f->exec, f->graph, 0);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamBeginCapture(f->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    ce = enqueue_forward(f, f->cap_stream, false);
+    cudaGraph_t rg = nullptr;
+    e = cudaStreamEndCapture(f->cap_stream, &rg);
+    f->render_graph = rg;
+    if (ce != cudaSuccess) return ce;
+    if (e != cudaSuccess) return e;
+    return cudaGraphInstantiate(&f->render_exec, f->render_graph, 0);
+}
+
+void release(gi_fit* f) {
+    if (!f) return;
+    destroy_graphs(f);
     if (f->cap_stream) cudaStreamDestroy(f->cap_stream);
     for (cudaEvent_t e : f->ev)
         if (e) cudaEventDestroy(e);
@@ -372,24 +402,8 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
     FIT_TRY(cudaStreamCreateWithFlags(&f->cap_stream, cudaStreamNonBlocking));
     if (f->stage_events)
         for (cudaEvent_t& ev : f->ev) FIT_TRY(cudaEventCreate(&ev));
-    if (f->use_graph) {
-        FIT_TRY(cudaStreamBeginCapture(f->cap_stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t ce = enqueue_step(f, f->cap_stream);
-        cudaGraph_t g = nullptr;
-        cudaError_t ee = cudaStreamEndCapture(f->cap_stream, &g);
-        f->graph = g;
-        FIT_TRY(ce);
-        FIT_TRY(ee);
-        FIT_TRY(cudaGraphInstantiate(&f->exec, f->graph, 0));
-        FIT_TRY(cudaStreamBeginCapture(f->cap_stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t re = enqueue_forward(f, f->cap_stream, false);
-        cudaGraph_t rg = nullptr;
-        cudaError_t rende = cudaStreamEndCapture(f->cap_stream, &rg);
-        f->render_graph = rg;
-        FIT_TRY(re);
-        FIT_TRY(rende);
-        FIT_TRY(cudaGraphInstantiate(&f->render_exec, f->render_graph, 0));
-    }
+    f->target_src = f->targets;
+    if (f->use_graph) FIT_TRY(capture_graphs(f));
 #undef FIT_TRY
     *out = f;
     return GI_OK;
@@ -402,6 +416,42 @@ gi_status gi_fit_step(gi_fit* f, int32_t steps, gi_stream stream) {
     for (int i = 0; i < steps; ++i) {
         cudaError_t e = f->exec ? cudaGraphLaunch(f->exec, s) : enqueue_step(f, s);
         if (e != cudaSuccess) return set_cuda_error(e, "gi_fit_step");
+    }
+    return GI_OK;
+}
+
+gi_status gi_fit_set_target_source(gi_fit* f, const float* src, gi_stream stream) {
+    NvtxRange nvtx_("gi_fit_set_target_source");
+    if (!f) return set_error(GI_ERR_INVALID_ARG, "gi_fit_set_target_source: NULL fit");
+    const float* use = f->targets;
+    if (src) {
+        cudaPointerAttributes a{};
+        if (cudaPointerGetAttributes(&a, src) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(GI_ERR_INVALID_ARG, "gi_fit_set_target_source: pointer not known to CUDA");
+        }
+        if (a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) {
+            if (!a.devicePointer || (a.type == cudaMemoryTypeDevice && a.device != f->dev))
+                return set_error(GI_ERR_INVALID_ARG, "gi_fit_set_target_source: not addressable from this device");
+            use = static_cast<const float*>(a.devicePointer);
+        } else {
+            return set_error(GI_ERR_INVALID_ARG,
+                             "gi_fit_set_target_source: pageable host memory (pin or register it first)");
+        }
+    }
+    if (use == f->target_src) return GI_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    GI_CUDA_TRY(cudaStreamSynchronize(s));
+    GI_CUDA_TRY(cudaStreamSynchronize(f->cap_stream));
+    f->target_src = use;
+    if (f->use_graph) {
+        destroy_graphs(f);
+        const cudaError_t e = capture_graphs(f);
+        if (e != cudaSuccess) {
+            destroy_graphs(f);
+            f->use_graph = false;  // eager launches from here on
+            return set_cuda_error(e, "gi_fit_set_target_source: graph capture");
+        }
     }
     return GI_OK;
 }

@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(Cfg::kThreads) k_render(const float4* __restri
     float* spart = reinterpret_cast<float*>(smem);  // reused after the last batch
     __shared__ __align__(8) uint64_t bar;
     __shared__ float s_red[32];
+    __shared__ float s_tgt[3 * NPIX];
     pdl_wait();
 
     const int t = blockIdx.x;
@@ -75,6 +76,21 @@ __global__ void __launch_bounds__(Cfg::kThreads) k_render(const float4* __restri
     const int col0 = (strip % Cfg::kStripsPerRow) * PX;
     const float py = (float)(y0 + row) + 0.5f;
     const float px0 = (float)(x0 + col0) + 0.5f;
+
+    // The target pixels of this thread's epilogue are copied to shared memory
+    // now (cp.async): their latency, long when the target is read from host
+    // memory over the host link, overlaps the accumulation below.
+    if (target) {
+        for (int p = threadIdx.x; p < NPIX; p += NT) {
+            const int x = x0 + p % T, y = y0 + p / T;
+            if (x < d.W && y < d.H) {
+                const float* src = target + 3 * (d.pix_base + (int64_t)y * d.W + x);
+                cp_async4(&s_tgt[3 * p], src);
+                cp_async4(&s_tgt[3 * p + 1], src + 1);
+                cp_async4(&s_tgt[3 * p + 2], src + 2);
+            }
+        }
+    }
 
     // Packed FP32 pairs: acc[r][p] holds two neighbouring pixels of row r.
     constexpr int NP2 = PX / 2;
@@ -160,6 +176,7 @@ __global__ void __launch_bounds__(Cfg::kThreads) k_render(const float4* __restri
 
     const float scale = 2.0f / (3.0f * (float)d.W * (float)d.H);
     float lsum = 0.f;
+    if (target) cp_async_wait_all();  // each thread reads back only the pixels it copied
     for (int p = threadIdx.x; p < NPIX; p += NT) {
         float C[3];
 #pragma unroll
@@ -178,7 +195,7 @@ __global__ void __launch_bounds__(Cfg::kThreads) k_render(const float4* __restri
             if (target) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    const float r = C[c] - target[3 * pix + c];
+                    const float r = C[c] - s_tgt[3 * p + c];
                     lsum = fmaf(r, r, lsum);
                     dl[c] = r * scale;
                 }

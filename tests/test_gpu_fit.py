@@ -339,3 +339,48 @@ def test_render_split_is_validated(gi):
     p = torch.from_numpy(pack(*synth.init_gaussians(10, 32, 32, 41))).cuda()
     with pytest.raises(gi.GIError):
         gi.Fit([t], [p], tile=16, render_split=2)
+
+
+def test_target_source_pinned_host_and_device_match_the_own_copy(gi):
+    """A fit reading its target from pinned host memory (over the host link,
+    inside the render) or from another device buffer takes the same steps,
+    bit for bit, as one reading its own copy; graph replay and eager alike."""
+    W, H, T, n = 160, 120, 16, 1500
+    target = synth.image(W, H, 24, n_blobs=20)
+    p = torch.from_numpy(pack(*synth.init_gaussians(n, W, H, 24))).cuda()
+    tg = torch.from_numpy(target).cuda()
+    host = torch.from_numpy(target.reshape(-1).copy()).pin_memory()
+    dev = tg.reshape(-1).clone()
+    ref = gi.Fit([tg], [p], tile=T, lr=LR)
+    ref.step(4)
+    for ug in (True, False):
+        for src in (host, dev):
+            f = gi.Fit([torch.zeros_like(tg)], [p], tile=T, lr=LR, use_graph=ug)  # own copy is all zeros
+            f.set_target_source(src)
+            f.step(4)
+            torch.cuda.synchronize()
+            assert torch.equal(f.params, ref.params)
+            assert f.mse()[0] == ref.mse()[0]
+            f.set_target_source(None)  # back to the (zero) own copy: a different loss
+            f.step(1)
+            torch.cuda.synchronize()
+            assert f.mse()[0] != ref.mse()[0]
+            f.close()
+    with pytest.raises(ValueError):
+        ref.set_target_source(torch.from_numpy(target.reshape(-1).copy()))  # pageable
+    ref.close()
+
+
+def test_target_source_rejects_pageable_memory_in_the_abi(gi):
+    import ctypes
+    from paper_2403_08551_gb300 import _lib as L
+    W, H, T, n = 64, 64, 16, 100
+    target = synth.image(W, H, 25, n_blobs=4)
+    f = gi.Fit([torch.from_numpy(target).cuda()], [torch.from_numpy(pack(*synth.init_gaussians(n, W, H, 25))).cuda()],
+               tile=T, lr=LR)
+    pageable = np.ascontiguousarray(target.reshape(-1), np.float32)
+    rc = L.load().gi_fit_set_target_source(f._h_fit, pageable.ctypes.data_as(ctypes.c_void_p), L.stream_handle())
+    assert rc != 0
+    f.step(1)  # the context still works
+    torch.cuda.synchronize()
+    f.close()
