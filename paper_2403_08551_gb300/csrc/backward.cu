@@ -579,7 +579,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
                     const float ge = gr[s] + cfg.beta2 * dg;
                     nn[s] = cfg.beta3 * nn[s] + (1.f - cfg.beta3) * ge * ge;
                     const float dir = mm[s] * s_bc[0] + cfg.beta2 * (vv[s] * s_bc[1]);
-                    pp[s] -= __fdividef(lr * dir, sqrt_approx(nn[s]) * s_bc[2] + cfg.eps);
+                    pp[s] -= lr * dir / (sqrtf(nn[s]) * s_bc[2] + cfg.eps);
                     gp[s] = gr[s];
                 }
                 N4[0] = *reinterpret_cast<float4*>(nn); N4[1] = *reinterpret_cast<float4*>(nn + 4);
@@ -590,8 +590,8 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
                     const float lr = cfg.lr[s < 2 ? 0 : (s < 5 ? 1 : 2)] * s_bc[3];
                     mm[s] = cfg.beta1 * mm[s] + (1.f - cfg.beta1) * gr[s];
                     vv[s] = cfg.beta2 * vv[s] + (1.f - cfg.beta2) * gr[s] * gr[s];
-                    const float denom = sqrt_approx(vv[s]) * s_bc[1] + cfg.eps;
-                    pp[s] -= __fdividef((lr * s_bc[0]) * mm[s], denom);
+                    const float denom = sqrtf(vv[s]) * s_bc[1] + cfg.eps;
+                    pp[s] -= (lr * s_bc[0]) * mm[s] / denom;
                 }
             }
             P4[0] = *reinterpret_cast<float4*>(pp); P4[1] = *reinterpret_cast<float4*>(pp + 4);

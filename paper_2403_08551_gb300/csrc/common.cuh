@@ -182,15 +182,6 @@ __device__ __forceinline__ float ex2(float x) {
     return y;
 }
 
-// Square root on the SFU (sqrt.approx: relative error about 2^-23, 0 -> 0),
-// for optimiser denominators, where the IEEE-rounded sequence costs a dozen
-// instructions and a slow-path branch per call.
-__device__ __forceinline__ float sqrt_approx(float x) {
-    float y;
-    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
 __device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
     uint32_t v;
     asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
