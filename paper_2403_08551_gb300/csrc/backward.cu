@@ -644,9 +644,47 @@ __global__ void __launch_bounds__(kCodecSumThreads) k_codec_update(CodecCfg Q, A
     __threadfence();
     const int nv = codec_nvals(Q);
     const int t = threadIdx.x;
+    // Everything the update reads is loaded in parallel first (a chain of
+    // dependent global read-modify-writes would cost a round trip each).
+    constexpr int kMB = kCodecMaxStages * kCodecMaxSize;
+    __shared__ double s_tot[kCodecMaxVals];
+    __shared__ double s_cnt[kMB];
+    __shared__ double s_sum[kMB * 3];
+    __shared__ double s_stage[kCodecMaxStages];
+    const int MB = Q.stages * Q.size;
+    for (int i = t; i < nv; i += blockDim.x) s_tot[i] = __ldcg(tot + i);
+    for (int i = t; i < MB; i += blockDim.x) s_cnt[i] = Q.ema_count[i];
+    for (int i = t; i < 3 * MB; i += blockDim.x) s_sum[i] = Q.ema_total[i];
+    __syncthreads();
+    {
+        const double d = (double)Q.decay;
+        for (int i = t; i < MB; i += blockDim.x) {
+            const double c = d * s_cnt[i] + (1.0 - d) * s_tot[6 + 4 * i];
+            s_cnt[i] = c;
+            Q.ema_count[i] = c;
+            for (int k = 0; k < 3; ++k) {
+                const double s = d * s_sum[3 * i + k] + (1.0 - d) * s_tot[6 + 4 * i + 1 + k];
+                s_sum[3 * i + k] = s;
+                Q.ema_total[3 * i + k] = s;
+            }
+        }
+    }
+    __syncthreads();
+    if (t < Q.stages) {
+        double sum = 0.0;
+        for (int j = 0; j < Q.size; ++j) sum += s_cnt[t * Q.size + j];
+        s_stage[t] = sum;
+    }
+    __syncthreads();
+    for (int i = t; i < 3 * MB; i += blockDim.x) {
+        const int e = i / 3, st = e / Q.size;
+        const double e_ = (double)Q.eps, sum = s_stage[st];
+        const double sm = (s_cnt[e] + e_) / (sum + Q.size * e_) * sum;
+        Q.codebooks[i] = (float)(s_sum[i] / sm);
+    }
     if (t < 6) {
-        const float gr = (float)__ldcg(tot + t);
-        Q.out[1 + t] = __ldcg(tot + t);
+        const float gr = (float)s_tot[t];
+        Q.out[1 + t] = s_tot[t];
         const int step = *cfg.step;  // already advanced by the reduction
         const float lr = cfg.lr[1] * (cfg.lr_halve_every > 0 ? ldexpf(1.f, -((step - 1) / cfg.lr_halve_every)) : 1.f);
         float* p = Q.gb;
@@ -670,27 +708,8 @@ __global__ void __launch_bounds__(kCodecSumThreads) k_codec_update(CodecCfg Q, A
             const float b1 = 1.f / (1.f - powf(cfg.beta1, (float)step)), b2 = rsqrtf(1.f - powf(cfg.beta2, (float)step));
             p[t] -= (lr * b1) * m / (sqrtf(vv) * b2 + cfg.eps);
         }
-    } else if (t >= 32 && t < 32 + Q.stages) {
-        const int st = t - 32;
-        const double d = (double)Q.decay, e = (double)Q.eps;
-        double sum = 0.0;
-        for (int j = 0; j < Q.size; ++j) {
-            const int base = 6 + (st * Q.size + j) * 4;
-            double& c = Q.ema_count[st * Q.size + j];
-            c = d * c + (1.0 - d) * __ldcg(tot + base);
-            for (int k = 0; k < 3; ++k) {
-                double& s = Q.ema_total[(st * Q.size + j) * 3 + k];
-                s = d * s + (1.0 - d) * __ldcg(tot + base + 1 + k);
-            }
-            sum += c;
-        }
-        for (int j = 0; j < Q.size; ++j) {
-            const double sm = (Q.ema_count[st * Q.size + j] + e) / (sum + Q.size * e) * sum;
-            for (int k = 0; k < 3; ++k)
-                Q.codebooks[(st * Q.size + j) * 3 + k] = (float)(Q.ema_total[(st * Q.size + j) * 3 + k] / sm);
-        }
     } else if (t == 64) {
-        Q.out[0] = n > 0 ? __ldcg(tot + nv - 1) / ((double)n * Q.size) : 0.0;
+        Q.out[0] = n > 0 ? s_tot[nv - 1] / ((double)n * Q.size) : 0.0;
         *ticket = 0u;
     }
 }
