@@ -82,9 +82,9 @@ typedef struct {
  * exp(-sigma) = exp2(-(z1^2 + z2^2)) (Sec. 3.1 with Sigma^-1 = L^-T L^-1). */
 #define GI_REC_FLOATS 8
 
-/* ABI version: 6 (gi_fit_desc gained param_mode, optimizer, beta3, lr_halve_every in 2,
+/* ABI version: 7 (gi_fit_desc gained param_mode, optimizer, beta3, lr_halve_every in 2,
  * cov_mode in 3, the codec fine-tuning fields in 4, opacity_mode and opacity_logits in 5;
- * gi_fit_set_target_source in 6). */
+ * gi_fit_set_target_source in 6; gi_codec_decode in 7). */
 GI_API int32_t gi_abi_version(void);
 GI_API const char* gi_last_error(void);
 GI_API const char* gi_status_string(int32_t status);
@@ -211,6 +211,24 @@ GI_API gi_status gi_render_backward(const float* rec_binned, const uint32_t* key
 GI_API gi_status gi_vq_decode(const uint16_t* means16, const uint8_t* idx, const float* codebooks, int32_t n,
                        int32_t stages, int32_t cb_size, float* means, float* chol, float* color,
                        gi_stream stream);
+
+/* ------------------------------------------------------------------------
+ * gi_codec_decode -- decode of the paper's codec (Sec. 3.3), the stream a
+ * codec fine-tuning context produces: FP16 positions, b-bit Cholesky codes
+ * with per-component scale and offset (Eq. 9: l_bar_i = code_i gamma_i +
+ * beta_i, FP32 product then sum, each rounded once) and the greedy RVQ
+ * colour (Eq. 10: the chosen entries summed in stage order in FP64, rounded
+ * once).
+ *   means16 [n][2] binary16 bits; codes [n][4] u8 (x, y, z used);
+ *   gamma_beta HOST [6] f32 (gamma[3], beta[3]); idx [stages][n] u8;
+ *   codebooks [stages][size][3] f32 (size <= 256);
+ *   means [n][2], chol [n][3], color [n][3] f32 (written).
+ * Bit-exact against the oracle; an index >= size raises GI_DEVERR_BOUNDS
+ * and decodes as entry 0.
+ * ---------------------------------------------------------------------- */
+GI_API gi_status gi_codec_decode(const uint16_t* means16, const uint8_t* codes, const float* gamma_beta,
+                          const uint8_t* idx, const float* codebooks, int32_t n, int32_t stages, int32_t size,
+                          float* means, float* chol, float* color, gi_stream stream);
 
 /* ------------------------------------------------------------------------
  * Fitting (Sec. 3.4: L2 loss, no adaptive density control, Gaussian count

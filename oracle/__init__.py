@@ -680,3 +680,26 @@ def blend_forward_backward(means, chol, color, logit, target, T, thresholds=BLEN
     g["abs_ambiguous_logit"] = g["abs_ambiguous"][:, 8] * o64 * (1.0 - o64)
     return dict(rect=rect, cnt=cnt, ids=ids, ranges=ranges, out=out, t_final=tf, n_last=nl, ambiguous=amb,
                 loss=L, dldc=d, grads=g, opac=o)
+
+
+def codec_decode(means16, codes, gamma, beta, idx, codebooks):
+    """Decode of the codec stream (Sec. 3.3): FP16 positions to FP32; the
+    Cholesky vector from its b-bit codes, l_bar_i = code_i gamma_i + beta_i
+    (Eq. 9, FP32 product and sum); the colour as the sum of the chosen RVQ
+    entries in stage order (Eq. 10) in FP64, rounded once. means16 [n,2]
+    float16 (or uint16 bits), codes [n,>=3] uint8, gamma/beta [3],
+    idx [M][n], codebooks [M][B][3]."""
+    m16 = np.asarray(means16)
+    if m16.dtype in (np.uint16, np.int16):
+        m16 = m16.view(np.float16)
+    means = m16.astype(np.float32)
+    q = np.asarray(codes)[:, :3].astype(np.float32)
+    g = np.asarray(gamma, np.float32)
+    b = np.asarray(beta, np.float32)
+    chol = ((q * g).astype(np.float32) + b).astype(np.float32)
+    cb = np.asarray(codebooks, np.float32)
+    idx = np.asarray(idx).astype(np.int64)
+    acc = np.zeros((means.shape[0], 3), np.float64)
+    for m in range(cb.shape[0]):
+        acc = acc + cb[m][idx[m]].astype(np.float64)
+    return means, chol, acc.astype(np.float32)

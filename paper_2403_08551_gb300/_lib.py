@@ -43,6 +43,7 @@ SIGNATURES = {
     "gi_backward_workspace_size": (i32, [i32, None, i64, P]),
     "gi_render_backward": (i32, [P, P, P, P, P, P, P, P, P, i32, None, i64, P, P, size_t, P, P, P, P, P]),
     "gi_vq_decode": (i32, [P, P, P, i32, i32, i32, P, P, P, P]),
+    "gi_codec_decode": (i32, [P, P, P, P, P, i32, i32, i32, P, P, P, P]),
     "gi_fit_create": (i32, [P, P, P]),
     "gi_fit_step": (i32, [P, i32, P]),
     "gi_fit_render": (i32, [P, P]),

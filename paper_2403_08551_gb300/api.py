@@ -14,7 +14,7 @@ from . import _lib as L
 
 __all__ = ["project", "bin_tiles", "render", "render_backward", "vq_decode", "device_errors",
            "GIRender", "rasterize", "Fit", "Bins", "alu_peaks", "tiles", "autotune", "RENDER_SPLITS", "Renderer",
-           "selftest_bounded_waits", "paper_to_pixel", "rs_to_chol", "codec_init", "ADAN_BETAS"]
+           "selftest_bounded_waits", "paper_to_pixel", "rs_to_chol", "codec_init", "codec_decode", "ADAN_BETAS"]
 
 # Render splits (lane groups sharing one tile's list) available per tile edge.
 RENDER_SPLITS = {8: (2, 4), 16: (4, 8), 32: (1, 2)}
@@ -167,6 +167,32 @@ def vq_decode(means16, idx, codebooks):
     return means, chol, color
 
 
+def codec_decode(stream: dict):
+    """Decode of the paper's codec stream (Sec. 3.3), as `Fit.encode` returns
+    it: means16 [n,2] binary16 bits (int16/uint16 or float16), codes [n,4]
+    uint8, gamma_beta (6 floats: gamma, beta), idx [M,n] uint8, codebooks
+    [M,B,3] float32. Returns pixel-space means [n,2], Cholesky vectors [n,3]
+    and colours [n,3] (float32, on the device of means16)."""
+    lib = L.load()
+    m16 = stream["means16"]
+    if m16.dtype == torch.float16:
+        m16 = m16.view(torch.int16)
+    m16 = m16.contiguous()
+    codes = _dev(stream["codes"], torch.uint8, "codes")
+    idx = _dev(stream["idx"], torch.uint8, "idx")
+    cb = _dev(stream["codebooks"], torch.float32, "codebooks")
+    gb = (ctypes.c_float * 6)(*[float(x) for x in stream["gamma_beta"]])
+    n = m16.shape[0]
+    M, B = cb.shape[0], cb.shape[1]
+    dev = m16.device
+    means = torch.empty((n, 2), dtype=torch.float32, device=dev)
+    chol = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    color = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    L.check(lib.gi_codec_decode(L.ptr(m16), L.ptr(codes), ctypes.cast(gb, ctypes.c_void_p), L.ptr(idx), L.ptr(cb), n,
+                                M, B, L.ptr(means), L.ptr(chol), L.ptr(color), L.stream_handle()), "gi_codec_decode")
+    return means, chol, color
+
+
 class GIRender(torch.autograd.Function):
     """Differentiable render: forward runs formation, binning and Eq. 7;
     backward recomputes the weights per tile (no per-pixel state saved)."""
@@ -208,6 +234,15 @@ ADAN_BETAS = (0.98, 0.92, 0.99)
 OPACITY_MODES = {"merged": 0, "separate": 1, "blend": 2}
 CODEC_EMA_DECAY = 0.99  # codebook EMA decay (the paper gives none; the common VQ-VAE value)
 CODEC_EMA_EPS = 1e-5    # Laplace smoothing of the EMA counts
+
+
+def np_offsets(counts):
+    """Exclusive prefix sums of per-image Gaussian counts."""
+    out, o = [], 0
+    for n in counts:
+        out.append(o)
+        o += n
+    return out
 
 
 def codec_init(params, bits: int = 6, stages: int = 2, size: int = 8, iters: int = 5, seed: int = 0,
@@ -413,6 +448,30 @@ class Fit:
 
     def render(self):
         L.check(L.load().gi_fit_render(self._h_fit, L.stream_handle()), "gi_fit_render")
+
+    def encode(self) -> dict:
+        """The codec stream of the current parameters (Sec. 3.3; a codec
+        fine-tuning context only): renders once so that the codes and indices
+        match the current parameters, gamma, beta and codebooks, and returns
+        means16 (the pixel-space positions in FP16, as int16 bits), codes
+        [N,4] uint8, gamma_beta, idx [M,N] uint8, codebooks [M,B,3] and the
+        stream size in bits (positions 16 bits each, b bits per code,
+        log2 B per index, gamma, beta and codebooks as FP32)."""
+        import math
+        if self.codec is None:
+            raise ValueError("encode needs a codec fine-tuning context")
+        self.render()
+        p = self.params.clone()
+        if self.param_mode == "paper":
+            p = torch.cat([paper_to_pixel(p[o:o + n], W, H) for (W, H), n, o in
+                           zip(self.shapes, self.counts, np_offsets(self.counts))])
+        M, Bn, b = self.codec["stages"], self.codec["size"], self.codec["bits"]
+        N = sum(self.counts)
+        bits = N * (2 * 16 + 3 * b + M * max(1, math.ceil(math.log2(Bn)))) + 6 * 32 + M * Bn * 3 * 32
+        torch.cuda.current_stream().synchronize()
+        return {"means16": p[:, 0:2].half().view(torch.int16).contiguous(), "codes": self.codes.clone(),
+                "gamma_beta": self.codec_gb[0].cpu().tolist(), "idx": self.rvq_idx.clone(),
+                "codebooks": self.codebooks.clone(), "bits": bits}
 
     def set_target_source(self, src: Optional[torch.Tensor] = None):
         """Train against `src` instead of the context's target copy: a CUDA

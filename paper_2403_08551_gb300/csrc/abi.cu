@@ -76,7 +76,7 @@ using namespace gi;
 
 extern "C" {
 
-int32_t gi_abi_version(void) { return 6; }
+int32_t gi_abi_version(void) { return 7; }
 
 const char* gi_last_error(void) { return t_err; }
 
@@ -247,6 +247,25 @@ gi_status gi_vq_decode(const uint16_t* means16, const uint8_t* idx, const float*
     cudaError_t e = launch_vq_decode(means16, idx, codebooks, n, stages, cb_size, means, chol, color, 0,
                                      reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return set_cuda_error(e, "gi_vq_decode");
+    return GI_OK;
+}
+
+gi_status gi_codec_decode(const uint16_t* means16, const uint8_t* codes, const float* gamma_beta,
+                          const uint8_t* idx, const float* codebooks, int32_t n, int32_t stages, int32_t size,
+                          float* means, float* chol, float* color, gi_stream stream) {
+    NvtxRange nvtx_("gi_codec_decode");
+    GI_REQUIRE(n >= 0, "gi_codec_decode: n < 0");
+    GI_REQUIRE(stages >= 1 && stages <= 8 && size >= 1 && size <= 256,
+               "gi_codec_decode: stages must be 1..8 and size 1..256");
+    GI_REQUIRE(gamma_beta, "gi_codec_decode: NULL gamma_beta");
+    if (n == 0) return GI_OK;
+    GI_REQUIRE(means16 && codes && idx && codebooks && means && chol && color, "gi_codec_decode: NULL pointer");
+    GI_REQUIRE(aligned(means16, 2) && aligned(codes, 4) && aligned(codebooks, 4) && aligned(means, 4) &&
+                   aligned(chol, 4) && aligned(color, 4),
+               "gi_codec_decode: misaligned pointer");
+    cudaError_t e = launch_codec_decode(means16, codes, gamma_beta, idx, codebooks, n, stages, size, means, chol,
+                                        color, reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return set_cuda_error(e, "gi_codec_decode");
     return GI_OK;
 }
 

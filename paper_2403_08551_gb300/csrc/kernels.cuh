@@ -133,6 +133,13 @@ cudaError_t launch_reduce(const float4* partial, const int64_t* pair_off, const 
                           float* params, float* m, float* v, float* grads_aos, const Batch& B,
                           cudaStream_t s);
 
+struct GammaBeta {
+    float v[6];  // gamma[3], beta[3]
+};
+cudaError_t launch_codec_decode(const uint16_t* means16, const uint8_t* codes, const float* gamma_beta,
+                                const uint8_t* idx, const float* cb, int32_t n, int32_t stages, int32_t size,
+                                float* means, float* chol, float* color, cudaStream_t s);
+
 cudaError_t launch_vq_decode(const uint16_t* means16, const uint8_t* idx, const float* cb, int32_t n,
                              int32_t stages, int32_t cb_size, float* means, float* chol, float* color,
                              int32_t out_stride_aos, cudaStream_t s);

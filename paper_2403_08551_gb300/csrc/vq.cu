@@ -75,7 +75,62 @@ __global__ void __launch_bounds__(256) k_vq_decode(const uint16_t* __restrict__ 
     }
 }
 
+// The paper's codec (Sec. 3.3): FP16 positions, the b-bit Cholesky codes
+// reconstructed as l_bar_i = code_i gamma_i + beta_i (Eq. 9, the same two
+// roundings as the fit's quantiser), and the RVQ colour as the FP64 sum of
+// the chosen entries in stage order, rounded once (as the fit's formation).
+__global__ void __launch_bounds__(256) k_codec_decode(const uint16_t* __restrict__ means16,
+                                                      const uchar4* __restrict__ codes, GammaBeta gb,
+                                                      const uint8_t* __restrict__ idx, const float* __restrict__ cb,
+                                                      int n, int stages, int size, float* __restrict__ means,
+                                                      float* __restrict__ chol, float* __restrict__ color,
+                                                      uint32_t* status) {
+    extern __shared__ float scb[];  // [stages][size][3]
+    for (int i = threadIdx.x; i < stages * size * 3; i += blockDim.x) scb[i] = cb[i];
+    __syncthreads();
+    for (int g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+        means[2 * (size_t)g] = __half2float(__ushort_as_half(means16[2 * (size_t)g]));
+        means[2 * (size_t)g + 1] = __half2float(__ushort_as_half(means16[2 * (size_t)g + 1]));
+        const uchar4 q = codes[g];
+        chol[3 * (size_t)g] = __fadd_rn(__fmul_rn((float)q.x, gb.v[0]), gb.v[3]);
+        chol[3 * (size_t)g + 1] = __fadd_rn(__fmul_rn((float)q.y, gb.v[1]), gb.v[4]);
+        chol[3 * (size_t)g + 2] = __fadd_rn(__fmul_rn((float)q.z, gb.v[2]), gb.v[5]);
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+        for (int m = 0; m < stages; ++m) {
+            int j = idx[(size_t)m * n + g];
+            if (j >= size) {  // index outside the codebook: skip the read
+                flag_error(status, kErrBounds);
+                j = 0;
+            }
+            const float* e = scb + ((size_t)m * size + j) * 3;
+            s0 = __dadd_rn(s0, (double)e[0]);
+            s1 = __dadd_rn(s1, (double)e[1]);
+            s2 = __dadd_rn(s2, (double)e[2]);
+        }
+        color[3 * (size_t)g] = (float)s0;
+        color[3 * (size_t)g + 1] = (float)s1;
+        color[3 * (size_t)g + 2] = (float)s2;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_codec_decode(const uint16_t* means16, const uint8_t* codes, const float* gamma_beta,
+                                const uint8_t* idx, const float* cb, int32_t n, int32_t stages, int32_t size,
+                                float* means, float* chol, float* color, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    GammaBeta gb;
+    for (int i = 0; i < 6; ++i) gb.v[i] = gamma_beta[i];
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 148;
+    const int blocks = std::max(1, std::min((n + 255) / 256, nsm * 4));
+    k_codec_decode<<<blocks, 256, (size_t)stages * size * 3 * sizeof(float), s>>>(
+        means16, reinterpret_cast<const uchar4*>(codes), gb, idx, cb, n, stages, size, means, chol, color,
+        device_status());
+    return cudaGetLastError();
+}
 
 cudaError_t launch_vq_decode(const uint16_t* means16, const uint8_t* idx, const float* cb, int32_t n, int32_t stages,
                              int32_t cb_size, float* means, float* chol, float* color, int32_t out_stride_aos,

@@ -203,3 +203,54 @@ def test_codec_arguments_are_validated(gi):
             gi.Fit([target], [p0], tile=16, codec=s)
     with pytest.raises(gi.GIError):
         gi.Fit([target], [p0], tile=16, codec=spec, cov="rs")
+
+
+def test_codec_decode_bit_exact(gi):
+    """gi_codec_decode against the oracle on random streams (two and three
+    stages), including the bounds check of an index outside the codebook."""
+    gen = np.random.default_rng(45)
+    for n, M, Bn in ((5000, 2, 8), (3000, 3, 16)):
+        m16 = gen.uniform(0, 2000, size=(n, 2)).astype(np.float16)
+        codes = gen.integers(0, 64, size=(n, 4)).astype(np.uint8)
+        gb = [0.13, 0.07, 0.11, 0.6, -2.5, 0.4]
+        idx = gen.integers(0, Bn, size=(M, n)).astype(np.uint8)
+        cb = gen.uniform(-0.3, 0.5, size=(M, Bn, 3)).astype(np.float32)
+        stream = {"means16": torch.from_numpy(m16.view(np.int16)).cuda(), "codes": torch.from_numpy(codes).cuda(),
+                  "gamma_beta": gb, "idx": torch.from_numpy(idx).cuda(), "codebooks": torch.from_numpy(cb).cuda()}
+        means, chol, color = gi.codec_decode(stream)
+        torch.cuda.synchronize()
+        rm, rl, rc = oracle.codec_decode(m16, codes, gb[0:3], gb[3:6], idx, cb)
+        np.testing.assert_array_equal(means.cpu().numpy(), rm)
+        np.testing.assert_array_equal(chol.cpu().numpy(), rl)
+        np.testing.assert_array_equal(color.cpu().numpy(), rc)
+        assert gi.device_errors(clear=True) == 0
+    bad = dict(stream)
+    bad_idx = idx.copy()
+    bad_idx[0, 7] = Bn  # one index past the codebook
+    bad["idx"] = torch.from_numpy(bad_idx).cuda()
+    gi.codec_decode(bad)
+    assert gi.device_errors(clear=True) & 4  # GI_DEVERR_BOUNDS
+
+
+@pytest.mark.parametrize("paper", [False, True])
+def test_codec_encode_decode_renders_the_fit_image(gi, paper):
+    """The stream a fine-tuning context encodes decodes (gi_codec_decode) to
+    the Gaussians its render used: rendering them with the plain renderer
+    gives the context's image bit for bit."""
+    W, H, T, n = 128, 96, 16, 900
+    target = synth.image(W, H, 46, n_blobs=12)
+    means, chol, color = synth.init_gaussians(n, W, H, 46)
+    p0 = paper_params(means, chol, color, W, H) if paper else np.concatenate([means, chol, color], axis=1)
+    pt = torch.from_numpy(p0.astype(np.float32)).cuda()
+    spec = gi.codec_init(pt, param_mode="paper" if paper else "pixel")
+    fit = gi.Fit([torch.from_numpy(target).cuda()], [pt], tile=T, codec=spec, render_split=8,
+                 param_mode="paper" if paper else "pixel", optimizer="adan" if paper else "adam")
+    fit.step(4)
+    stream = fit.encode()
+    img = fit.images()[0].clone()
+    m, l, c = gi.codec_decode(stream)
+    ref = gi.rasterize(m, l, c, W, H, T)
+    torch.cuda.synchronize()
+    assert torch.equal(ref, img)
+    assert stream["bits"] == n * (32 + 18 + 2 * 3) + 6 * 32 + 2 * 8 * 3 * 32
+    fit.close()

@@ -242,3 +242,26 @@ def test_codec_gamma_beta_gradients_match_finite_differences():
         for which, ana in (("g", cdc["grads"]["gamma"][i]), ("b", cdc["grads"]["beta"][i])):
             num = (4 * central(5e-4, which) - central(1e-3, which)) / 3
             assert num == pytest.approx(ana, rel=2e-3, abs=1e-5 * max(1.0, abs(ana)))
+
+
+def test_codec_decode_reproduces_what_the_quantisers_render():
+    """Decoding the codes, indices and FP16 positions that the quantisers
+    produce gives back exactly the positions, Cholesky vectors and colours
+    they handed to the render (Eq. 9's reconstruction, Eq. 10's sum)."""
+    gen = np.random.default_rng(9)
+    n = 500
+    means = gen.uniform(0, 700, size=(n, 2)).astype(np.float32)
+    chol = np.stack([gen.uniform(0.5, 9, n), gen.uniform(-3, 3, n), gen.uniform(0.5, 9, n)], axis=1).astype(np.float32)
+    color = gen.uniform(-0.1, 0.6, size=(n, 3)).astype(np.float32)
+    gamma = np.array([0.13, 0.09, 0.14], np.float32)
+    beta = np.array([0.5, -3.0, 0.5], np.float32)
+    cb = synth.codebooks(9, size=8, stages=2)[1]
+    lbar, x, q = oracle.lsq_fake_quant(chol, gamma, beta, 6)
+    idx, chat, _ = oracle.rvq_assign_f32(color, cb)
+    m16 = means.astype(np.float16)
+    codes = np.zeros((n, 4), np.uint8)
+    codes[:, :3] = q.astype(np.uint8)
+    dm, dl, dc = oracle.codec_decode(m16.view(np.uint16), codes, gamma, beta, idx, cb)
+    np.testing.assert_array_equal(dm, oracle.fp16_round(means))
+    np.testing.assert_array_equal(dl, lbar)
+    np.testing.assert_array_equal(dc, chat)
