@@ -356,16 +356,28 @@ def codec_finetune(gi, torch, stream, T, params, steps=10000, every=2500, bits=6
         t += e0.elapsed_time(e1) / 1e3
         done += n
         traj.append([done, psnr(fit.mse()[0])])
-    fit.render()
-    torch.cuda.synchronize()
+    stream_ = fit.encode()  # renders the current parameters once
     img = fit.images()[0]
     p_final = psnr(float(((img.clamp(0, 1) - ref) ** 2).mean()))
+    # decode + render of the encoded stream (the codec's decoder), L2 flushed
+    m_, l_, c_ = gi.codec_decode(stream_)
+    rdr = gi.Renderer(w.W, w.H, w.n, T, capacity=fit.capacity)
+    rdr(m_, l_, c_)
+    flush_ = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+
+    def decode_render():
+        mm, ll, cc = gi.codec_decode(stream_)
+        rdr(mm, ll, cc)
+
+    dr_ms = _time(torch, stream, decode_render, 50, flush_)
+    del flush_
     err = gi.device_errors(clear=True)
     n = w.n
-    bits_total = n * (2 * 16 + 3 * bits + stages * math.ceil(math.log2(size))) + 6 * 32 + stages * size * 3 * 32
+    bits_total = stream_["bits"]
     out = {"steps": steps, "iter_s": (steps - 1) / t, "psnr_db_unquantised": p_plain,
            "psnr_db_quantised_before": p1, "psnr_db_trajectory": traj, "psnr_db_final_render": p_final,
            "commitment_loss": float(fit.codec_out[0].item()), "bits": bits_total,
+           "decode_render_fps": 1e3 / dr_ms, "decode_render_ms": dr_ms,
            "bpp": bits_total / (w.W * w.H), "config": {"bits": bits, "stages": stages, "size": size, "lr": lr,
                                                        "ema_decay": fit.codec["ema_decay"]},
            "psnr_note": "training-loss PSNR of the step's render (unclamped) in the trajectory; the "
