@@ -8,7 +8,9 @@ printed. Run from the repository root:
 Modes: merged (the paper's 8-parameter form, Adam), separate (colour and
 opacity kept apart, accumulated summation), blend (sorted alpha-blending),
 paper (App. C.1 parameters with Adan), rs (rotation-scaling covariance with
-the paper's parameters and Adan), codec (b = 6, 2 x 8 RVQ fine-tuning)."""
+the paper's parameters and Adan), codec (b = 6, 2 x 8 RVQ fine-tuning),
+batch (64 synthetic images of uneven sizes, 5k-70k Gaussians each, fitted in
+one launch per stage at tile 16, render split 4)."""
 import argparse
 import os
 import sys
@@ -18,11 +20,17 @@ import torch
 
 sys.path.insert(0, os.getcwd())
 
-MODES = ("merged", "separate", "blend", "paper", "rs", "codec")
+MODES = ("merged", "separate", "blend", "paper", "rs", "codec", "batch")
 
 
 def make_fit(gi, mode: str):
     import synth
+    if mode == "batch":
+        ws = synth.batch_workload(64)
+        tg = [torch.from_numpy(w.target).cuda() for w in ws]
+        pr = [torch.from_numpy(np.concatenate([w.means, w.chol, w.color], axis=1).astype(np.float32)).cuda()
+              for w in ws]
+        return gi.Fit(tg, pr, tile=16, lr=(1e-3, 1e-2, 1e-2), render_split=4, use_graph=False)
     w = synth.workload("c1_768x512_70k")
     tgt = torch.from_numpy(w.target).cuda()
     p = np.concatenate([w.means, w.chol, w.color], axis=1).astype(np.float64)
