@@ -168,3 +168,33 @@ def test_opacity_arguments_are_validated(gi):
         gi.Fit([tg], [pt], tile=16, opacity="separate", cov="rs")
     with pytest.raises(ValueError):
         gi.Fit([tg], [pt], tile=16, opacity="transparent")
+
+
+@pytest.mark.parametrize("mode", ["separate", "blend"])
+def test_batched_equals_single(gi, mode):
+    """Two images of different sizes in one context take, bit for bit, the
+    steps each takes alone (per-image tiles, pixels, walk lengths and
+    opacity state)."""
+    cases = [case(96, 64, 400, 57), case(160, 112, 900, 58)]
+    lg = [torch.from_numpy(c[2].astype(np.float32)).cuda() for c in cases]
+    tg = [torch.from_numpy(c[0]).cuda() for c in cases]
+    pr = [torch.from_numpy(c[1]).cuda() for c in cases]
+    both = gi.Fit(tg, pr, tile=16, lr=LR, opacity=mode, opacity_logits=lg, render_split=8)
+    both.step(3)
+    torch.cuda.synchronize()
+    o = 0
+    for i in range(2):
+        one = gi.Fit([tg[i]], [pr[i]], tile=16, lr=LR, opacity=mode, opacity_logits=[lg[i]], render_split=8)
+        one.step(3)
+        torch.cuda.synchronize()
+        n = pr[i].shape[0]
+        assert torch.equal(both.params[o:o + n], one.params)
+        assert torch.equal(both.opacity_logit[o:o + n], one.opacity_logit)
+        assert torch.equal(both.images()[i], one.images()[0])
+        if mode == "blend":
+            H, W = tg[i].shape[0], tg[i].shape[1]
+            off = 0 if i == 0 else tg[0].shape[0] * tg[0].shape[1]
+            assert torch.equal(both.n_last[off:off + H * W], one.n_last)
+        o += n
+        one.close()
+    both.close()
