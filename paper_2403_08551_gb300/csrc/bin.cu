@@ -29,6 +29,14 @@ __device__ __forceinline__ float clampf_(float v, float lo, float hi) {
     return v < lo ? lo : (v > hi ? hi : v);
 }
 
+// tanh in FP64 as (1 - e) / (1 + e), e = exp(-2|x|), sign restored: a few
+// ulp of FP64, far below the FP32 rounding that follows, and cheaper than the
+// library tanh on this part's FP64 units (the App. C.1 positions).
+__device__ __forceinline__ double tanh_fp64(double x) {
+    const double e = exp(-2.0 * fabs(x));
+    return copysign((1.0 - e) / (1.0 + e), x);
+}
+
 __device__ void zero_job(const ZeroJob& zj) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
@@ -71,8 +79,8 @@ __global__ void __launch_bounds__(kProjBlock) k_project(ParamsIn P, Batch B, flo
             // App. C.1: positions through tanh into (-1, 1), read as
             // mu = (tanh(theta) + 1) / 2 * (W, H) (tanh in FP64, one rounding
             // to FP32); +0.5 on the Cholesky diagonal or on the scales.
-            mx = (float)__dmul_rn(__dmul_rn(__dadd_rn(tanh((double)mx), 1.0), 0.5), (double)d.W);
-            my = (float)__dmul_rn(__dmul_rn(__dadd_rn(tanh((double)my), 1.0), 0.5), (double)d.H);
+            mx = (float)__dmul_rn(__dmul_rn(__dadd_rn(tanh_fp64((double)mx), 1.0), 0.5), (double)d.W);
+            my = (float)__dmul_rn(__dmul_rn(__dadd_rn(tanh_fp64((double)my), 1.0), 0.5), (double)d.H);
             if (B.cov_mode == 0) {
                 l1 = __fadd_rn(l1, 0.5f);
                 l3 = __fadd_rn(l3, 0.5f);
