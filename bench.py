@@ -534,7 +534,7 @@ def main():
     ap.add_argument("--batch-images", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=2000, help="fit steps of the batched vs plain comparison")
     ap.add_argument("--long-steps", type=int, default=50000, help="steps of the full-length fit (0 = skip)")
-    ap.add_argument("--out", default=os.path.join(ROOT, "gpurun_out"))
+    ap.add_argument("--out", default=os.path.join(ROOT, "bench_out"), help="folder for the long fits' PSNR logs")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":

@@ -192,7 +192,8 @@ class Workload:
     name: str = ""
 
 
-# Named single-image workloads (sizes from the paper's settings).
+# Named single-image workloads (sizes from the paper's settings: Kodak-sized
+# 768x512 and DIV2K-sized 2040x1356 images).
 CONFIGS = {
     # 256x256, 2,000 Gaussians, 40 blobs: the small parity case.
     "c0_256x256_2k": dict(W=256, H=256, n=2000, blobs=40, lines=0, config=0, skew=False),
