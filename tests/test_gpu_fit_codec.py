@@ -254,3 +254,31 @@ def test_codec_encode_decode_renders_the_fit_image(gi, paper):
     assert torch.equal(ref, img)
     assert stream["bits"] == n * (32 + 18 + 2 * 3) + 6 * 32 + 2 * 8 * 3 * 32
     fit.close()
+
+
+def test_codec_checkpoint_resume_is_bit_identical(gi, tmp_path):
+    """A codec fine-tuning context (paper parameters, Adan) saved after 4
+    steps and restored into a fresh context continues exactly like the
+    uninterrupted one: parameters, Adan state, gamma/beta, codebooks, EMA."""
+    W, H, T, n = 128, 96, 16, 700
+    target = torch.from_numpy(synth.image(W, H, 47, n_blobs=12)).cuda()
+    p0 = torch.from_numpy(paper_params(*synth.init_gaussians(n, W, H, 47), W, H)).cuda()
+    spec = gi.codec_init(p0, param_mode="paper")
+    kw = dict(tile=T, lr=(1e-3, 1e-3, 1e-3), codec=spec, param_mode="paper", optimizer="adan")
+    a = gi.Fit([target], [p0], **kw)
+    a.step(4)
+    path = tmp_path / "codec.pt"
+    torch.save(a.state_dict(), path)
+    a.step(3)
+    b = gi.Fit([target], [p0], **kw)
+    b.load_state_dict(torch.load(path))
+    b.step(3)
+    torch.cuda.synchronize()
+    for k in ("params", "adam_m", "adam_v", "adan_n", "adan_gprev", "codec_gb", "codebooks", "ema_count",
+              "ema_total"):
+        assert torch.equal(getattr(a, k), getattr(b, k)), k
+    plain = gi.Fit([target], [p0], tile=T, lr=(1e-3, 1e-3, 1e-3), param_mode="paper", optimizer="adan")
+    with pytest.raises(ValueError):
+        plain.load_state_dict(torch.load(path))
+    for f in (a, b, plain):
+        f.close()

@@ -198,3 +198,25 @@ def test_batched_equals_single(gi, mode):
         o += n
         one.close()
     both.close()
+
+
+def test_blend_checkpoint_resume_is_bit_identical(gi, tmp_path):
+    target, p0, logit = case(96, 80, 600, 59)
+    tg, pt = torch.from_numpy(target).cuda(), torch.from_numpy(p0).cuda()
+    lg = [torch.from_numpy(logit.astype(np.float32)).cuda()]
+    a = gi.Fit([tg], [pt], tile=16, lr=LR, opacity="blend", opacity_logits=lg)
+    a.step(4)
+    path = tmp_path / "blend.pt"
+    torch.save(a.state_dict(), path)
+    a.step(3)
+    b = gi.Fit([tg], [pt], tile=16, lr=LR, opacity="blend", opacity_logits=lg)
+    b.load_state_dict(torch.load(path))
+    b.step(3)
+    torch.cuda.synchronize()
+    for k in ("params", "adam_m", "adam_v", "opacity_logit", "opacity_m", "opacity_v"):
+        assert torch.equal(getattr(a, k), getattr(b, k)), k
+    sep = gi.Fit([tg], [pt], tile=16, lr=LR, opacity="separate", opacity_logits=lg)
+    with pytest.raises(ValueError):
+        sep.load_state_dict(torch.load(path))
+    for f in (a, b, sep):
+        f.close()
