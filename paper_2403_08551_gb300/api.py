@@ -320,7 +320,30 @@ class Fit:
     CUDA graph when ``use_graph``.
 
     targets: list of [H,W,3] float32 CUDA tensors; params: list of [n,8]
-    float32 tensors (mx, my, l1, l2, l3, c'r, c'g, c'b) per image."""
+    float32 tensors (mx, my, l1, l2, l3, c'r, c'g, c'b) per image.
+
+    Options (all validated by the library, which refuses combinations it
+    does not support):
+      lr            learning rates of (positions, covariance, colour)
+      param_mode    "pixel" (parameters as above) or "paper" (App. C.1:
+                    positions through tanh, +0.5 on the Cholesky diagonal
+                    or on the scales)
+      optimizer     "adam" (betas, eps) or "adan" (betas = three decays,
+                    default ADAN_BETAS); lr_halve_every halves every rate
+                    every that many steps (0 = never)
+      cov           "cholesky" (l1, l2, l3) or "rs" (theta, s1, s2; Eq. 2-3)
+      codec         codec_init(...) dict: quantisation-aware fine-tuning
+                    (FP16 positions, b-bit Cholesky, RVQ colour; one image)
+      opacity       "merged" (c', the paper's form), "separate" (colour and
+                    a sigmoid opacity, accumulated summation) or "blend"
+                    (sorted alpha-blending, tile 16); opacity_logits gives
+                    the initial logits (default 0)
+      render_split  lane groups per tile in the render (0 = chosen from the
+                    first binning; see RENDER_SPLITS)
+      use_graph     replay each step from a captured CUDA graph
+      stage_events  record CUDA events between the stages (stage_times)
+    Methods: step, render, images, mse, stage_times, set_target_source,
+    encode (codec), state_dict / load_state_dict, close."""
 
     def __init__(self, targets: Sequence[torch.Tensor], params: Sequence[torch.Tensor], tile: int = 16,
                  lr=(1e-3, 1e-2, 1e-2), betas=(0.9, 0.999), eps=1e-8, capacity: Optional[int] = None,
