@@ -131,8 +131,9 @@ def run_codec(gi, target, p0, T, steps, paper, optimizer, lr, decay=0.9):
     return fit
 
 
-def test_codec_pixel_adam_steps_track_oracle(gi):
-    W, H, T, n = 128, 96, 16, 800
+@pytest.mark.parametrize("T", [8, 16, 32])
+def test_codec_pixel_adam_steps_track_oracle(gi, T):
+    W, H, n = 128, 96, 800
     target = synth.image(W, H, 41, n_blobs=20)
     p0 = np.concatenate(synth.init_gaussians(n, W, H, 41), axis=1).astype(np.float32)
     run_codec(gi, target, p0, T, 5, paper=False, optimizer="adam", lr=(1e-3, 1e-2, 1e-2)).close()

@@ -119,8 +119,9 @@ def run_rs(gi, target, p0, T, steps, paper, optimizer, lr=(1e-3, 1e-2, 1e-2), ha
     return fit
 
 
-def test_rs_pixel_adam_steps_track_oracle(gi):
-    W, H, T, n = 128, 96, 16, 800
+@pytest.mark.parametrize("T", [8, 16, 32])
+def test_rs_pixel_adam_steps_track_oracle(gi, T):
+    W, H, n = 128, 96, 800
     target = synth.image(W, H, 31, n_blobs=20)
     means, rs, color = synth.init_gaussians_rs(n, W, H, 31)
     p0 = np.concatenate([means, rs, color], axis=1).astype(np.float32)
