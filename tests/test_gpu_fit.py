@@ -189,8 +189,9 @@ def run_paper_adan(gi, W, H, means, chol, color, target, T, steps, lr=1e-3, halv
     return fit
 
 
-def test_paper_mode_adan_steps_track_oracle(gi):
-    W, H, T, n = 128, 96, 16, 800
+@pytest.mark.parametrize("T", [8, 16, 32])
+def test_paper_mode_adan_steps_track_oracle(gi, T):
+    W, H, n = 128, 96, 800
     target = synth.image(W, H, 25, n_blobs=20)
     means, chol, color = synth.init_gaussians(n, W, H, 25)
     fit = run_paper_adan(gi, W, H, means, chol, color, target, T, 5, halve=3)

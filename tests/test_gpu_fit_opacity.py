@@ -114,9 +114,10 @@ def case(W, H, n, seed):
     return target, np.concatenate([means, chol, color], axis=1).astype(np.float32), logit
 
 
-def test_separate_opacity_steps_track_oracle(gi):
+@pytest.mark.parametrize("T", [8, 16, 32])
+def test_separate_opacity_steps_track_oracle(gi, T):
     target, p0, logit = case(128, 96, 800, 51)
-    run_opacity(gi, target, p0, logit, 16, 5, "separate").close()
+    run_opacity(gi, target, p0, logit, T, 5, "separate").close()
 
 
 def test_blend_steps_track_oracle(gi):
