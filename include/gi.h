@@ -31,10 +31,11 @@
  *     rx = 3|l1|, ry = 3 sqrt(l2^2 + l3^2)
  *     tx0 = clamp(floor((mx - rx)/T), 0, tw), tx1 = clamp(floor((mx + rx)/T) + 1, 0, tw)
  * (y likewise), tw = ceil(W/T), th = ceil(H/T). A Gaussian whose parameters
- * are non-finite, whose det = (l1 l3)^2 is 0, whose FP32 conic or scaled
- * inverse Cholesky factor (GI_REC_FLOATS) is not finite, or whose rectangle
- * is empty is culled (count 0). Pixel i receives Gaussian n iff i's tile
- * lies in n's rectangle.
+ * are non-finite, whose det = (l1 l3)^2 is 0, whose FP32 inverse covariance
+ * (Sigma^-1 = [[A, B], [B, C]]) is not finite, or whose rectangle is empty is
+ * culled (count 0). (A finite FP32 Sigma^-1 implies a finite record factor,
+ * GI_REC_FLOATS.) Pixel i receives Gaussian n iff i's tile lies in n's
+ * rectangle.
  */
 #ifndef GI_H_
 #define GI_H_
@@ -82,9 +83,10 @@ typedef struct {
  * exp(-sigma) = exp2(-(z1^2 + z2^2)) (Sec. 3.1 with Sigma^-1 = L^-T L^-1). */
 #define GI_REC_FLOATS 8
 
-/* ABI version: 7 (gi_fit_desc gained param_mode, optimizer, beta3, lr_halve_every in 2,
+/* ABI version: 8 (gi_fit_desc gained param_mode, optimizer, beta3, lr_halve_every in 2,
  * cov_mode in 3, the codec fine-tuning fields in 4, opacity_mode and opacity_logits in 5;
- * gi_fit_set_target_source in 6; gi_codec_decode in 7). */
+ * gi_fit_set_target_source in 6; gi_codec_decode in 7; gi_fit_count_pairs and the
+ * GI_FIT_KEYS .. GI_FIT_MEANS16 pointers in 8). */
 GI_API int32_t gi_abi_version(void);
 GI_API const char* gi_last_error(void);
 GI_API const char* gi_status_string(int32_t status);
@@ -355,9 +357,30 @@ enum {
     /* separate opacity (NULL pointers when opacity_mode == 0): */
     GI_FIT_OPACITY = 18,     /* f32 [7][N]: logit, o of the last formation, optimiser m, v, n,
                                 g_prev, dL/dlogit of the last step */
-    GI_FIT_N_LAST = 19       /* i32 [pixels] alpha-blending: list entries each pixel walked */
+    GI_FIT_N_LAST = 19,      /* i32 [pixels] alpha-blending: list entries each pixel walked */
+    /* the binning of the last step (or render), as gi_bin_tiles returns it for the
+       batch: global tile id t = the image's first tile + ty tw + tx, global Gaussian
+       id = the image's first Gaussian + its index (images in order): */
+    GI_FIT_KEYS = 20,        /* u32 [capacity] sorted tile id of each pair (first GI_FIT_K valid) */
+    GI_FIT_IDS = 21,         /* u32 [capacity] Gaussian id of each pair, ascending within a tile */
+    GI_FIT_RANGES = 22,      /* i32 [tiles][2] [begin, end) of each tile, [0, 0) when empty */
+    GI_FIT_PAIR_OFF = 23,    /* i64 [N + 1] exclusive prefix of the counts (emission order) */
+    GI_FIT_RECT = 24,        /* i32 [N][4] support rectangle of each Gaussian (image tiles) */
+    GI_FIT_CNT = 25,         /* i32 [N] tiles in the rectangle, 0 when culled */
+    GI_FIT_MEANS16 = 26      /* u16 [N][2] codec fine-tuning: binary16 bits of the positions the
+                                last step rendered (the stream's positions; NULL without codec) */
 };
 GI_API gi_status gi_fit_pointer(gi_fit* fit, int32_t what, void** ptr);
+
+/* Number of (tile, Gaussian) pairs the first step of a context created from
+ * `desc` would bin: the formation of that context (its param_mode, cov_mode
+ * and codec quantiser, Sec. 3.1-3.3 and App. C.1) applied to desc->params,
+ * then the sum of the support-rectangle tile counts (the opacity forms do
+ * not move a rectangle and are not applied). For sizing desc->capacity;
+ * desc->capacity itself is ignored. *pairs is a host int64. Allocates
+ * temporary device memory (freed before returning) and synchronises
+ * `stream`; GI_ERR_INVALID_ARG for a descriptor gi_fit_create would refuse. */
+GI_API gi_status gi_fit_count_pairs(const gi_fit_desc* desc, gi_stream stream, int64_t* pairs);
 GI_API gi_status gi_fit_destroy(gi_fit* fit);
 
 /* With stage_events set: waits for the last step and writes the device time

@@ -59,9 +59,8 @@ static float clampf_(float v, float lo, float hi) {
  *   tx0 = clamp(floor((mx - rx) / T), 0, tw)
  *   tx1 = clamp(floor((mx + rx) / T) + 1, 0, tw)     (same for y with ry, th)
  * A Gaussian is culled (rect = 0, cnt = 0) if any parameter is non-finite,
- * det == 0, any of A, B, C, rx, ry is non-finite, the scaled inverse
- * Cholesky factor (k/l1, -(l2 k/l1)/l3, k/l3 with k = sqrt(log2(e)/2), FP32)
- * is non-finite, or the rectangle is empty.
+ * det == 0, any entry of Sigma^-1 = (A, B, C) or rx, ry is non-finite (Eq. 5
+ * needs a finite inverse covariance), or the rectangle is empty.
  * cnt = (tx1 - tx0) * (ty1 - ty0) tiles.
  */
 void gio_rect_rule(const float* means, const float* chol, const float* color,
@@ -87,10 +86,6 @@ void gio_rect_rule(const float* means, const float* chol, const float* color,
         if (det == 0.0f) continue;
         float ca = s22 / det, cb = -s12 / det, cc = s11 / det;
         if (!isfinite(det) || !isfinite(ca) || !isfinite(cb) || !isfinite(cc)) continue;
-        /* the FP32 inverse Cholesky factor the kernels evaluate sigma with */
-        const float kq = 0.84932180028801904272f; /* sqrt(log2(e) / 2) */
-        float m11 = kq / l1, m22 = kq / l3, m21 = -((l2 * m11) / l3);
-        if (!isfinite(m11) || !isfinite(m21) || !isfinite(m22)) continue;
         float rx = 3.0f * fabsf(l1);
         float ry = 3.0f * sqrtf(s22);
         if (!isfinite(rx) || !isfinite(ry)) continue;

@@ -6,12 +6,11 @@ include/gi.h); this package is its Python binding: per-stage calls, an
 autograd Function and multi-image fitting contexts.
 """
 from .api import (RENDER_SPLITS, Bins, Fit, GIRender, Renderer, alu_peaks, autotune, bin_tiles, codec_decode, codec_init,
-                  device_errors, project,
-                  paper_to_pixel, rasterize, render, render_backward, rs_to_chol, selftest_bounded_waits, tiles,
+                  device_errors, project, rasterize, render, render_backward, selftest_bounded_waits, tiles,
                   vq_decode)
 from ._lib import GIError, load
 
 __all__ = ["RENDER_SPLITS", "Bins", "Fit", "GIRender", "Renderer", "GIError", "alu_peaks", "autotune", "bin_tiles",
            "codec_decode", "codec_init",
-           "device_errors", "load", "paper_to_pixel", "project", "rasterize", "render", "render_backward",
-           "rs_to_chol", "selftest_bounded_waits", "tiles", "vq_decode"]
+           "device_errors", "load", "project", "rasterize", "render", "render_backward",
+           "selftest_bounded_waits", "tiles", "vq_decode"]

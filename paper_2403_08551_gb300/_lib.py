@@ -27,7 +27,8 @@ DEVERR_CAPACITY, DEVERR_TIMEOUT, DEVERR_BOUNDS = 1, 2, 4
 
 (FIT_PARAMS, FIT_ADAM_M, FIT_ADAM_V, FIT_GRADS, FIT_OUT, FIT_LOSS, FIT_STEP, FIT_K, FIT_TARGET, FIT_ADAN_N,
  FIT_ADAN_GPREV, FIT_CODEC_GB, FIT_CODEBOOKS, FIT_EMA_COUNT, FIT_EMA_TOTAL, FIT_CODES, FIT_RVQ_IDX,
- FIT_CODEC_OUT, FIT_OPACITY, FIT_N_LAST) = range(20)
+ FIT_CODEC_OUT, FIT_OPACITY, FIT_N_LAST, FIT_KEYS, FIT_IDS, FIT_RANGES, FIT_PAIR_OFF, FIT_RECT, FIT_CNT,
+ FIT_MEANS16) = range(27)
 
 # Every symbol include/gi.h declares, with (restype, argtypes).
 SIGNATURES = {
@@ -49,6 +50,7 @@ SIGNATURES = {
     "gi_fit_render": (i32, [P, P]),
     "gi_fit_set_target_source": (i32, [P, P, P]),
     "gi_fit_pointer": (i32, [P, i32, P]),
+    "gi_fit_count_pairs": (i32, [P, P, P]),
     "gi_fit_destroy": (i32, [P]),
     "gi_fit_stage_times": (i32, [P, P]),
     "gi_alu_peaks": (i32, [P, P]),

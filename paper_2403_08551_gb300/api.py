@@ -14,7 +14,7 @@ from . import _lib as L
 
 __all__ = ["project", "bin_tiles", "render", "render_backward", "vq_decode", "device_errors",
            "GIRender", "rasterize", "Fit", "Bins", "alu_peaks", "tiles", "autotune", "RENDER_SPLITS", "Renderer",
-           "selftest_bounded_waits", "paper_to_pixel", "rs_to_chol", "codec_init", "codec_decode", "ADAN_BETAS"]
+           "selftest_bounded_waits", "codec_init", "codec_decode", "ADAN_BETAS"]
 
 # Render splits (lane groups sharing one tile's list) available per tile edge.
 RENDER_SPLITS = {8: (2, 4), 16: (4, 8), 32: (1, 2)}
@@ -236,15 +236,6 @@ CODEC_EMA_DECAY = 0.99  # codebook EMA decay (the paper gives none; the common V
 CODEC_EMA_EPS = 1e-5    # Laplace smoothing of the EMA counts
 
 
-def np_offsets(counts):
-    """Exclusive prefix sums of per-image Gaussian counts."""
-    out, o = [], 0
-    for n in counts:
-        out.append(o)
-        o += n
-    return out
-
-
 def codec_init(params, bits: int = 6, stages: int = 2, size: int = 8, iters: int = 5, seed: int = 0,
                param_mode: str = "pixel") -> dict:
     """Starting point of the codec fine-tuning (Sec. 3.3-3.4, the paper's b = 6,
@@ -281,37 +272,6 @@ def codec_init(params, bits: int = 6, stages: int = 2, size: int = 8, iters: int
         cbs[m] = cent
     return {"bits": bits, "codebooks": torch.from_numpy(cbs.astype(np.float32)).to(params.device),
             "gamma": gamma.astype(np.float32).tolist(), "beta": lo.astype(np.float32).tolist()}
-
-
-def paper_to_pixel(p, W: int, H: int, cov: str = "cholesky"):
-    """Raw parameters of App. C.1 ([n,8]: theta, Cholesky without the +0.5 on
-    its diagonal, colour) -> pixel-space parameters, as the formation kernel
-    maps them (tanh in FP64, one rounding to FP32). With cov="rs" the
-    covariance slots are (theta, s1, s2), the +0.5 goes on s1, s2 and the
-    result holds the Cholesky vector of the same Sigma."""
-    q = p.clone()
-    t = torch.tanh(p[:, 0:2].double())
-    q[:, 0:2] = ((t + 1.0) * 0.5 * torch.tensor([W, H], dtype=torch.float64, device=p.device)).float()
-    if cov == "rs":
-        q[:, 2:5] = rs_to_chol(p[:, 2:5], 0.5)
-    else:
-        q[:, 2] = p[:, 2] + 0.5
-        q[:, 4] = p[:, 4] + 0.5
-    return q
-
-
-def rs_to_chol(rs, shift: float = 0.0):
-    """Rotation-scaling covariance parameters ([n,3]: theta, s1, s2; Sec. 3.1,
-    Eq. 2-3, Sigma = (R S)(R S)^T) -> the Cholesky vector (l1, l2, l3) of the
-    same Sigma, in FP64 with one rounding, as the formation kernel maps them:
-    l1 = sqrt(Sigma11), l2 = Sigma12 / l1, l3 = |s1 s2| / l1. `shift` is
-    added to s1, s2 first (App. C.1's +0.5)."""
-    r = rs.double().clone()
-    r[:, 1:3] += shift
-    c, s = torch.cos(r[:, 0]), torch.sin(r[:, 0])
-    a, b = r[:, 1] * r[:, 1], r[:, 2] * r[:, 2]
-    l1 = torch.sqrt(c * c * a + s * s * b)
-    return torch.stack([l1, c * s * (a - b) / l1, torch.abs(r[:, 1] * r[:, 2]) / l1], dim=1).float()
 
 
 class Fit:
@@ -364,36 +324,14 @@ class Fit:
         self.param_mode, self.optimizer, self.cov = param_mode, optimizer, cov
         if optimizer == "adan" and len(betas) != 3:
             betas = ADAN_BETAS
-        K = None
-        if capacity is None or (render_split == 0 and tile == 16):
-            K = 0
-            for (W, H), p in zip(self.shapes, params):
-                p = p.contiguous()
-                if param_mode == "paper":
-                    p = paper_to_pixel(p, W, H, cov)
-                elif cov == "rs":
-                    p = torch.cat([p[:, 0:2], rs_to_chol(p[:, 2:5]), p[:, 5:8]], dim=1)
-                rec, rect, cnt = project(p[:, 0:2].contiguous(), p[:, 2:5].contiguous(), p[:, 5:8].contiguous(),
-                                         W, H, tile)
-                K += bin_tiles(rect, cnt, None, W, H, tile).K
-        if capacity is None:
-            capacity = max(4096, int(K * capacity_factor) + 1024)
-        if render_split == 0 and tile == 16:
-            # Short tile lists are rendered faster by fewer lane groups per tile
-            # (measured on GB300: 97 pairs per tile, split 4 is 1.2x faster than
-            # 8; 234 pairs per tile, split 8 is 1.06x faster than 4).
-            n_tiles = sum(tiles(W, H, tile)[0] * tiles(W, H, tile)[1] for W, H in self.shapes)
-            render_split = 8 if K >= 160 * n_tiles else 4
-        self.render_split = int(render_split)
-        self.capacity = int(capacity)
         n_img = len(targets)
         self._w = (ctypes.c_int32 * n_img)(*[s[0] for s in self.shapes])
         self._h = (ctypes.c_int32 * n_img)(*[s[1] for s in self.shapes])
         self._n = (ctypes.c_int32 * n_img)(*self.counts)
         desc = L.GIFitDesc(n_img, ctypes.cast(self._w, ctypes.c_void_p), ctypes.cast(self._h, ctypes.c_void_p),
                            ctypes.cast(self._n, ctypes.c_void_p), tgt.data_ptr(), prm.data_ptr(), tile,
-                           lr[0], lr[1], lr[2], betas[0], betas[1], eps, self.capacity, int(use_graph),
-                           int(stage_events), int(render_split), int(param_mode == "paper"),
+                           lr[0], lr[1], lr[2], betas[0], betas[1], eps, 1, int(use_graph),
+                           int(stage_events), 0, int(param_mode == "paper"),
                            int(optimizer == "adan"), float(betas[2]) if optimizer == "adan" else 0.0,
                            int(lr_halve_every), int(cov == "rs"))
         if opacity not in OPACITY_MODES:
@@ -417,6 +355,25 @@ class Fit:
             desc.ema_eps = float(codec.get("ema_eps", CODEC_EMA_EPS))
             self.codec = {"bits": desc.codec_bits, "stages": M, "size": Bn, "ema_decay": desc.ema_decay,
                           "ema_eps": desc.ema_eps}
+        if capacity is None or (render_split == 0 and tile == 16):
+            # pairs of the first step, counted by the library with this
+            # context's own formation (parameterisation, covariance form, codec)
+            K = ctypes.c_int64(0)
+            L.check(lib.gi_fit_count_pairs(ctypes.byref(desc), L.stream_handle(), ctypes.byref(K)),
+                    "gi_fit_count_pairs")
+            K = K.value
+        if capacity is None:
+            capacity = max(4096, int(K * capacity_factor) + 1024)
+        if render_split == 0 and tile == 16:
+            # Short tile lists are rendered faster by fewer lane groups per tile
+            # (measured on GB300: 97 pairs per tile, split 4 is 1.2x faster than
+            # 8; 234 pairs per tile, split 8 is 1.06x faster than 4).
+            n_tiles = sum(tiles(W, H, tile)[0] * tiles(W, H, tile)[1] for W, H in self.shapes)
+            render_split = 8 if K >= 160 * n_tiles else 4
+        self.render_split = int(render_split)
+        self.capacity = int(capacity)
+        desc.render_split = self.render_split
+        desc.capacity = self.capacity
         h = ctypes.c_void_p()
         L.check(lib.gi_fit_create(ctypes.byref(desc), L.stream_handle(), ctypes.byref(h)), "gi_fit_create")
         self._h_fit = h
@@ -444,6 +401,7 @@ class Fit:
             self.codes = self._view(L.FIT_CODES, (N, 4), "|u1")
             self.rvq_idx = self._view(L.FIT_RVQ_IDX, (M, N), "|u1")
             self.codec_out = self._view(L.FIT_CODEC_OUT, (7,), "<f8")
+            self.means16 = self._view(L.FIT_MEANS16, (N, 2), "<i2")
         if self.opacity_mode != "merged":
             base = ctypes.c_void_p()
             L.check(L.load().gi_fit_pointer(self._h_fit, L.FIT_OPACITY, ctypes.byref(base)), "gi_fit_pointer")
@@ -461,6 +419,20 @@ class Fit:
 
     def step(self, n: int = 1):
         L.check(L.load().gi_fit_step(self._h_fit, int(n), L.stream_handle()), "gi_fit_step")
+
+    def binning(self) -> dict:
+        """The binning of the last step (or render), as the library holds it:
+        keys and ids [K] (global tile and Gaussian ids, sorted by tile,
+        ascending Gaussian id inside a tile), ranges [tiles, 2], pair_off
+        [N + 1], rect [N, 4] and cnt [N] (device views; synchronises)."""
+        N = sum(self.counts)
+        n_tiles = sum(tiles(W, H, self.tile)[0] * tiles(W, H, self.tile)[1] for W, H in self.shapes)
+        K = int(self.k.item())
+        return {"K": K, "keys": self._view(L.FIT_KEYS, (self.capacity,), "<i4")[:K],
+                "ids": self._view(L.FIT_IDS, (self.capacity,), "<i4")[:K],
+                "ranges": self._view(L.FIT_RANGES, (n_tiles, 2), "<i4"),
+                "pair_off": self._view(L.FIT_PAIR_OFF, (N + 1,), "<i8"),
+                "rect": self._view(L.FIT_RECT, (N, 4), "<i4"), "cnt": self._view(L.FIT_CNT, (N,), "<i4")}
 
     def stage_times(self):
         """Device ms of the last step's stages: formation, binning, render,
@@ -484,15 +456,11 @@ class Fit:
         if self.codec is None:
             raise ValueError("encode needs a codec fine-tuning context")
         self.render()
-        p = self.params.clone()
-        if self.param_mode == "paper":
-            p = torch.cat([paper_to_pixel(p[o:o + n], W, H) for (W, H), n, o in
-                           zip(self.shapes, self.counts, np_offsets(self.counts))])
         M, Bn, b = self.codec["stages"], self.codec["size"], self.codec["bits"]
         N = sum(self.counts)
         bits = N * (2 * 16 + 3 * b + M * max(1, math.ceil(math.log2(Bn)))) + 6 * 32 + M * Bn * 3 * 32
         torch.cuda.current_stream().synchronize()
-        return {"means16": p[:, 0:2].half().view(torch.int16).contiguous(), "codes": self.codes.clone(),
+        return {"means16": self.means16.clone(), "codes": self.codes.clone(),
                 "gamma_beta": self.codec_gb[0].cpu().tolist(), "idx": self.rvq_idx.clone(),
                 "codebooks": self.codebooks.clone(), "bits": bits}
 

@@ -3,6 +3,9 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "kernels.cuh"
 
@@ -58,6 +61,34 @@ gi_status set_cuda_error(cudaError_t e, const char* what) {
     return GI_ERR_CUDA;
 }
 
+cudaError_t smem_optin(const void* kernel, int bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> done;  // (kernel, device) -> limit set
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    int& have = done[{kernel, dev}];
+    if (have >= bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) have = bytes;
+    return e;
+}
+
+int sm_count() {
+    static std::mutex mu;
+    static std::map<int, int> cached;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+    std::lock_guard<std::mutex> lk(mu);
+    int& v = cached[dev];
+    if (v <= 0 && (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0)) {
+        v = 0;
+        return 152;
+    }
+    return v;
+}
+
 uint32_t* device_status() {
     static uint32_t* cache[64] = {nullptr};
     int dev = 0;
@@ -76,7 +107,7 @@ using namespace gi;
 
 extern "C" {
 
-int32_t gi_abi_version(void) { return 7; }
+int32_t gi_abi_version(void) { return 8; }
 
 const char* gi_last_error(void) { return t_err; }
 

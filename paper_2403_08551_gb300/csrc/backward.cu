@@ -714,32 +714,19 @@ __global__ void __launch_bounds__(kCodecSumThreads) k_codec_update(CodecCfg Q, A
     }
 }
 
-int sm_count_b() {
-    int dev = 0, v = 0;
-    cudaGetDevice(&dev);
-    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
-    return v;
-}
-
 }  // namespace
 
 cudaError_t launch_backward(const float4* rec_binned, const uint32_t* keys, const uint32_t* ids, const int4* rect,
                             const int64_t* pair_off, const float* dl_tiled, const Batch& B, const int64_t* k_dev,
                             int64_t capacity, float4* partial, uint32_t* status, cudaStream_t s) {
     if (capacity <= 0) return cudaSuccess;
-    static int nsm = 0;
-    if (!nsm) nsm = sm_count_b();
+    const int nsm = sm_count();
     const int64_t need = (capacity + 255) / 256;  // 8 warps x 32 pairs per block-iteration
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)nsm * 8));
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_backward<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)backward_smem<8>());
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_backward<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)backward_smem<16>());
+    {
+        cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_backward<8>), (int)backward_smem<8>());
+        if (e == cudaSuccess) e = smem_optin(reinterpret_cast<const void*>(k_backward<16>), (int)backward_smem<16>());
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     switch (B.tile) {
         case 8:

@@ -125,8 +125,13 @@ __global__ void __launch_bounds__(kProjBlock) k_project(ParamsIn P, Batch B, flo
             // Codec fine-tuning (Sec. 3.3): FP16 positions, b-bit Cholesky
             // vector, greedy RVQ colour; the codes are the encoded stream.
             const CodecCfg& Q = B.codec;
-            mx = __half2float(__float2half_rn(mx));
-            my = __half2float(__float2half_rn(my));
+            const __half hx = __float2half_rn(mx), hy = __float2half_rn(my);
+            mx = __half2float(hx);
+            my = __half2float(hy);
+            if (Q.means16) {
+                Q.means16[2 * (size_t)g] = __half_as_ushort(hx);
+                Q.means16[2 * (size_t)g + 1] = __half_as_ushort(hy);
+            }
             float x, q0, q1, q2;
             l1 = lsq_quant(l1, Q.gb[0], Q.gb[3], Q.qp, x, q0);
             l2 = lsq_quant(l2, Q.gb[1], Q.gb[4], Q.qp, x, q1);
@@ -502,19 +507,6 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, const uint32_t* __re
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-int sm_count() {
-    static int cached[64] = {0};
-    int dev = 0;
-    cudaGetDevice(&dev);
-    if (dev < 0 || dev >= 64) return 148;
-    if (!cached[dev]) {
-        int v = 0;
-        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
-        cached[dev] = v;
-    }
-    return cached[dev];
-}
-
 }  // namespace
 
 RadixPlan radix_plan(int total_tiles) {
@@ -595,12 +587,9 @@ cudaError_t launch_bin(const int4* rect, const int32_t* cnt, const float4* rec, 
     cudaError_t e = launch_pdl(k_emit, dim3(nblk), dim3(kProjBlock), 0, s, rect, cnt, ws.blk_sum, B, capacity, ka, va,
                                pair_off, k_dev, k_max, ws.hist, rp, status);
     if (e != cudaSuccess) return e;
-    static bool attr = false;  // the staging buffer and the static arrays exceed the default 48 KB window
-    if (!attr) {
-        e = cudaFuncSetAttribute(k_onesweep, cudaFuncAttributeMaxDynamicSharedMemorySize, kSortStageBytes);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    // the staging buffer and the static arrays exceed the default 48 KB window
+    e = smem_optin(reinterpret_cast<const void*>(k_onesweep), kSortStageBytes);
+    if (e != cudaSuccess) return e;
     for (int ps = 0; ps < rp.passes; ++ps) {
         e = launch_pdl(k_onesweep, dim3((unsigned)sblk), dim3(kSortThreads), (size_t)kSortStageBytes, s, ka, va, kb,
                        vb, k_dev, capacity,

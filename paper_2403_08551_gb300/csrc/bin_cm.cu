@@ -421,13 +421,9 @@ cudaError_t launch_bin_cm(const int4* rect, const int32_t* cnt, const float4* re
     e = launch_pdl(k_colscan, dim3(groups), dim3(kCmScanThreads), 0, s, ws.cm, nchunks, Tn, ranges, keys, capacity,
                    k_dev, k_max, ws.lookback, ws.tickets, status);
     if (e != cudaSuccess) return e;
-    static bool attr = false;  // up to 40 KB dynamic + the static layout: above the default 48 KB window
-    if (!attr) {
-        e = cudaFuncSetAttribute(k_place, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (kCmChunk / 32 + 1) * kCmMaxTiles * 4);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    // up to 40 KB dynamic + the static layout: above the default 48 KB window
+    e = smem_optin(reinterpret_cast<const void*>(k_place), (kCmChunk / 32 + 1) * kCmMaxTiles * 4);
+    if (e != cudaSuccess) return e;
     return launch_pdl(k_place, dim3(nchunks), dim3(kCmChunk), (size_t)(kCmChunk / 32 + 1) * Tn * 4, s, rect, cnt, rec,
                       B, ws.cm, ws.chunk_sum, nchunks, capacity, ids, rec_binned, pair_off, status);
 }

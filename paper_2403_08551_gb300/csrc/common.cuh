@@ -66,6 +66,7 @@ struct CodecCfg {
     double* ema_count;     // [M][B]
     double* ema_total;     // [M][B][3]
     uchar4* codes;         // [N] quantiser codes (x, y, z; w = 0)
+    uint16_t* means16;     // [N][2] binary16 bits of the rendered positions (nullable)
     uint8_t* idx;          // [M][N] RVQ indices
     double* part;          // [nvals][blocks of the reduction] per-block partial sums
     double* tot;           // [nvals] their totals

@@ -160,6 +160,64 @@ void release(gi_fit* f) {
     delete f;
 }
 
+// Checks a fitting descriptor (everything but the capacity).
+gi_status check_desc(const gi_fit_desc* d, const char* fn) {
+    if (d->n_images < 1 || !d->widths || !d->heights || !d->counts || !d->targets || !d->params)
+        return set_error(GI_ERR_INVALID_ARG, "%s: bad image list or NULL buffer", fn);
+    if (d->tile != 8 && d->tile != 16 && d->tile != 32)
+        return set_error(GI_ERR_INVALID_ARG, "%s: tile must be 8, 16 or 32", fn);
+    {
+        const int sp = d->render_split;
+        const bool ok = sp == 0 || (d->tile == 8 && (sp == 2 || sp == 4)) || (d->tile == 16 && (sp == 4 || sp == 8)) ||
+                        (d->tile == 32 && (sp == 1 || sp == 2));
+        if (!ok)
+            return set_error(GI_ERR_INVALID_ARG, "%s: render_split %d not available for tile %d", fn, sp, d->tile);
+    }
+    if ((d->param_mode != 0 && d->param_mode != 1) || (d->optimizer != 0 && d->optimizer != 1) ||
+        (d->cov_mode != 0 && d->cov_mode != 1) || d->lr_halve_every < 0 ||
+        (d->optimizer == 1 && !(d->beta3 >= 0.f && d->beta3 < 1.f)))
+        return set_error(GI_ERR_INVALID_ARG, "%s: bad param_mode, cov_mode, optimizer, beta3 or lr_halve_every", fn);
+    if ((reinterpret_cast<uintptr_t>(d->params) & 15) != 0)
+        return set_error(GI_ERR_INVALID_ARG, "%s: params must be 16-byte aligned", fn);
+    const bool codec = d->codec_bits != 0;
+    if (d->opacity_mode < 0 || d->opacity_mode > 2 || (d->opacity_mode == 2 && d->tile != 16) ||
+        (d->opacity_mode != 0 && (codec || d->cov_mode != 0)))
+        return set_error(GI_ERR_INVALID_ARG, "%s: opacity_mode must be 0, 1 or 2 (2 needs tile 16; neither 1 nor 2 "
+                                             "combines with the codec or the rotation-scaling form)", fn);
+    if (codec) {
+        if (d->codec_bits < 1 || d->codec_bits > 8 || d->codec_stages < 1 || d->codec_stages > kCodecMaxStages ||
+            d->codec_size < 1 || d->codec_size > kCodecMaxSize || !d->codebooks)
+            return set_error(GI_ERR_INVALID_ARG, "%s: codec needs bits in [1, 8], stages in [1, %d], size in [1, %d] "
+                                                 "and codebooks", fn, kCodecMaxStages, kCodecMaxSize);
+        if (d->n_images != 1 || d->cov_mode != 0)
+            return set_error(GI_ERR_INVALID_ARG, "%s: codec fine-tuning takes one image in Cholesky form", fn);
+        if (!(d->ema_decay >= 0.f && d->ema_decay < 1.f) || !(d->ema_eps >= 0.f) ||
+            !(d->lsq_gamma[0] > 0.f && d->lsq_gamma[1] > 0.f && d->lsq_gamma[2] > 0.f))
+            return set_error(GI_ERR_INVALID_ARG, "%s: codec needs ema_decay in [0, 1), ema_eps >= 0 and gamma > 0", fn);
+    }
+    return GI_OK;
+}
+
+// Per-image descriptors of the batch (first tile, Gaussian and pixel of
+// each image) and the totals.
+gi_status image_table(const gi_fit_desc* d, const char* fn, std::vector<ImgDesc>& desc, int64_t& tiles,
+                      int64_t& gauss, int64_t& pix) {
+    desc.assign(d->n_images, ImgDesc{});
+    tiles = gauss = pix = 0;
+    for (int i = 0; i < d->n_images; ++i) {
+        const int W = d->widths[i], H = d->heights[i], n = d->counts[i];
+        if (W <= 0 || H <= 0 || n < 0) return set_error(GI_ERR_INVALID_ARG, "%s: bad image %d", fn, i);
+        const int tw = (W + d->tile - 1) / d->tile, th = (H + d->tile - 1) / d->tile;
+        desc[i] = ImgDesc{W, H, tw, th, (int32_t)tiles, (int32_t)gauss, pix};
+        tiles += (int64_t)tw * th;
+        gauss += n;
+        pix += (int64_t)W * H;
+    }
+    if (tiles >= (int64_t(1) << 30) || gauss >= (int64_t(1) << 31) - 1)
+        return set_error(GI_ERR_INVALID_ARG, "%s: batch too large", fn);
+    return GI_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -168,58 +226,17 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
     NvtxRange nvtx_("gi_fit_create");
     if (!d || !out) return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: NULL argument");
     *out = nullptr;
-    if (d->n_images < 1 || !d->widths || !d->heights || !d->counts || !d->targets || !d->params)
-        return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: bad image list or NULL buffer");
-    if (d->tile != 8 && d->tile != 16 && d->tile != 32)
-        return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: tile must be 8, 16 or 32");
-    {
-        const int sp = d->render_split;
-        const bool ok = sp == 0 || (d->tile == 8 && (sp == 2 || sp == 4)) || (d->tile == 16 && (sp == 4 || sp == 8)) ||
-                        (d->tile == 32 && (sp == 1 || sp == 2));
-        if (!ok) return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: render_split %d not available for tile %d", sp,
-                                  d->tile);
-    }
+    gi_status st = check_desc(d, "gi_fit_create");
+    if (st != GI_OK) return st;
     if (d->capacity < 1 || d->capacity > kMaxCapacity)
         return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: capacity outside [1, 2^30)");
-    if ((d->param_mode != 0 && d->param_mode != 1) || (d->optimizer != 0 && d->optimizer != 1) ||
-        (d->cov_mode != 0 && d->cov_mode != 1) || d->lr_halve_every < 0 ||
-        (d->optimizer == 1 && !(d->beta3 >= 0.f && d->beta3 < 1.f)))
-        return set_error(GI_ERR_INVALID_ARG,
-                         "gi_fit_create: bad param_mode, cov_mode, optimizer, beta3 or lr_halve_every");
-    if ((reinterpret_cast<uintptr_t>(d->params) & 15) != 0)
-        return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: params must be 16-byte aligned");
     const bool codec = d->codec_bits != 0;
-    if (d->opacity_mode < 0 || d->opacity_mode > 2 || (d->opacity_mode == 2 && d->tile != 16) ||
-        (d->opacity_mode != 0 && (codec || d->cov_mode != 0)))
-        return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: opacity_mode must be 0, 1 or 2 (2 needs tile 16; "
-                                             "neither 1 nor 2 combines with the codec or the rotation-scaling form)");
-    if (codec) {
-        if (d->codec_bits < 1 || d->codec_bits > 8 || d->codec_stages < 1 || d->codec_stages > kCodecMaxStages ||
-            d->codec_size < 1 || d->codec_size > kCodecMaxSize || !d->codebooks)
-            return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: codec needs bits in [1, 8], stages in [1, %d], "
-                                                 "size in [1, %d] and codebooks", kCodecMaxStages, kCodecMaxSize);
-        if (d->n_images != 1 || d->cov_mode != 0)
-            return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: codec fine-tuning takes one image in Cholesky form");
-        if (!(d->ema_decay >= 0.f && d->ema_decay < 1.f) || !(d->ema_eps >= 0.f) ||
-            !(d->lsq_gamma[0] > 0.f && d->lsq_gamma[1] > 0.f && d->lsq_gamma[2] > 0.f))
-            return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: codec needs ema_decay in [0, 1), ema_eps >= 0 and "
-                                                 "gamma > 0");
-    }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
 
-    std::vector<ImgDesc> desc(d->n_images);
+    std::vector<ImgDesc> desc;
     int64_t tiles = 0, gauss = 0, pix = 0;
-    for (int i = 0; i < d->n_images; ++i) {
-        const int W = d->widths[i], H = d->heights[i], n = d->counts[i];
-        if (W <= 0 || H <= 0 || n < 0) return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: bad image %d", i);
-        const int tw = (W + d->tile - 1) / d->tile, th = (H + d->tile - 1) / d->tile;
-        desc[i] = ImgDesc{W, H, tw, th, (int32_t)tiles, (int32_t)gauss, pix};
-        tiles += (int64_t)tw * th;
-        gauss += n;
-        pix += (int64_t)W * H;
-    }
-    if (tiles >= (int64_t(1) << 30) || gauss >= (int64_t(1) << 31) - 1)
-        return set_error(GI_ERR_INVALID_ARG, "gi_fit_create: batch too large");
+    st = image_table(d, "gi_fit_create", desc, tiles, gauss, pix);
+    if (st != GI_OK) return st;
 
     gi_fit* f = new (std::nothrow) gi_fit();
     if (!f) return set_error(GI_ERR_NO_MEMORY, "gi_fit_create: host allocation failed");
@@ -270,6 +287,7 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
         d->opacity_mode ? 7 * up256((size_t)N * 4) : 0,                   // 31 opacity state
         d->opacity_mode == 2 ? up256((size_t)f->capacity * 4) : 0,        // 32 per-pair opacity sums
         d->opacity_mode == 2 ? up256((size_t)P * 4) : 0,                  // 33 per-pixel walk lengths
+        codec ? up256((size_t)N * 4) : 0,                                 // 34 FP16 positions
     };
     size_t total = 0;
     for (size_t x : sz) total += x;
@@ -362,6 +380,7 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
         Q.tot = reinterpret_cast<double*>(at(30));
         Q.ticket = reinterpret_cast<unsigned*>(at(30) + up256((size_t)kCodecMaxVals * 8));
         Q.out = reinterpret_cast<double*>(at(30) + up256((size_t)kCodecMaxVals * 8) + 64);
+        Q.means16 = reinterpret_cast<uint16_t*>(at(34));
         for (int i = 0; i < 3; ++i) {
             gb_init[i] = d->lsq_gamma[i];
             gb_init[3 + i] = d->lsq_beta[i];
@@ -488,6 +507,13 @@ gi_status gi_fit_pointer(gi_fit* f, int32_t what, void** ptr) {
         case GI_FIT_CODEC_OUT: *ptr = f->B.codec.out; break;
         case GI_FIT_OPACITY: *ptr = f->B.opac.logit; break;
         case GI_FIT_N_LAST: *ptr = f->B.opac.n_last; break;
+        case GI_FIT_KEYS: *ptr = f->keys; break;
+        case GI_FIT_IDS: *ptr = f->ids; break;
+        case GI_FIT_RANGES: *ptr = f->ranges; break;
+        case GI_FIT_PAIR_OFF: *ptr = f->pair_off; break;
+        case GI_FIT_RECT: *ptr = f->rect; break;
+        case GI_FIT_CNT: *ptr = f->cnt; break;
+        case GI_FIT_MEANS16: *ptr = f->B.codec.means16; break;
         default: return set_error(GI_ERR_INVALID_ARG, "gi_fit_pointer: unknown field %d", what);
     }
     return GI_OK;
@@ -498,6 +524,77 @@ gi_status gi_fit_stage_times(gi_fit* f, float* ms) {
     if (!f->stage_events) return set_error(GI_ERR_INVALID_ARG, "gi_fit_stage_times: created without stage_events");
     GI_CUDA_TRY(cudaEventSynchronize(f->ev[5]));
     for (int i = 0; i < 5; ++i) GI_CUDA_TRY(cudaEventElapsedTime(&ms[i], f->ev[i], f->ev[i + 1]));
+    return GI_OK;
+}
+
+gi_status gi_fit_count_pairs(const gi_fit_desc* d, gi_stream stream, int64_t* pairs) {
+    NvtxRange nvtx_("gi_fit_count_pairs");
+    if (!d || !pairs) return set_error(GI_ERR_INVALID_ARG, "gi_fit_count_pairs: NULL argument");
+    gi_status st = check_desc(d, "gi_fit_count_pairs");
+    if (st != GI_OK) return st;
+    std::vector<ImgDesc> desc;
+    int64_t tiles = 0, gauss = 0, pix = 0;
+    st = image_table(d, "gi_fit_count_pairs", desc, tiles, gauss, pix);
+    if (st != GI_OK) return st;
+    *pairs = 0;
+    if (gauss == 0) return GI_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const bool codec = d->codec_bits != 0;
+    const int64_t N = gauss;
+    const int64_t nblk = (N + kProjBlock - 1) / kProjBlock;
+    // Scratch: image table, records, rectangles, counts, block sums; with the
+    // codec, gamma and beta and the outputs the formation writes.
+    const size_t sz[] = {up256(sizeof(ImgDesc) * desc.size()), up256((size_t)N * 32), up256((size_t)N * 16),
+                         up256((size_t)N * 4), up256((size_t)nblk * 8), codec ? (size_t)256 : 0,
+                         codec ? up256((size_t)N * 4) : 0, codec ? up256((size_t)N * d->codec_stages) : 0};
+    size_t total = 0;
+    for (size_t x : sz) total += x;
+    void* arena = nullptr;
+    cudaError_t e = cudaMalloc(&arena, total);
+    if (e != cudaSuccess)
+        return set_error(GI_ERR_NO_MEMORY, "gi_fit_count_pairs: cudaMalloc(%zu) failed: %s", total,
+                         cudaGetErrorString(e));
+    char* p = static_cast<char*>(arena);
+    auto at = [&](int i) {
+        size_t off = 0;
+        for (int j = 0; j < i; ++j) off += sz[j];
+        return p + off;
+    };
+    Batch B{};
+    B.one = desc[0];
+    B.many = d->n_images > 1 ? reinterpret_cast<ImgDesc*>(at(0)) : nullptr;
+    B.nimg = d->n_images;
+    B.tile = d->tile;
+    B.total_tiles = (int32_t)tiles;
+    B.total_gauss = (int32_t)gauss;
+    B.param_mode = d->param_mode;
+    B.cov_mode = d->cov_mode;
+    float gb[6] = {d->lsq_gamma[0], d->lsq_gamma[1], d->lsq_gamma[2], d->lsq_beta[0], d->lsq_beta[1], d->lsq_beta[2]};
+    if (codec) {
+        CodecCfg& Q = B.codec;
+        Q.bits = d->codec_bits;
+        Q.stages = d->codec_stages;
+        Q.size = d->codec_size;
+        Q.qp = (float)((1 << d->codec_bits) - 1);
+        Q.gb = reinterpret_cast<float*>(at(5));
+        Q.codebooks = const_cast<float*>(d->codebooks);
+        Q.codes = reinterpret_cast<uchar4*>(at(6));
+        Q.idx = reinterpret_cast<uint8_t*>(at(7));
+    }
+    std::vector<int64_t> sums((size_t)nblk);
+    e = cudaMemcpyAsync(at(0), desc.data(), sizeof(ImgDesc) * desc.size(), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && codec) e = cudaMemcpyAsync(at(5), gb, sizeof(gb), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = launch_project(params_aos(d->params), B, reinterpret_cast<float4*>(at(1)), reinterpret_cast<int4*>(at(2)),
+                           reinterpret_cast<int32_t*>(at(3)), reinterpret_cast<int64_t*>(at(4)), ZeroJob{}, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(sums.data(), at(4), (size_t)nblk * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(arena);
+    if (e != cudaSuccess) return set_cuda_error(e, "gi_fit_count_pairs");
+    int64_t K = 0;
+    for (int64_t v : sums) K += v;
+    *pairs = K;
     return GI_OK;
 }
 

@@ -146,6 +146,12 @@ cudaError_t launch_vq_decode(const uint16_t* means16, const uint8_t* idx, const 
 
 // Per-device error word that kernels OR error bits into.
 uint32_t* device_status();
+// Raises `kernel`'s dynamic shared-memory limit to at least `bytes` on the
+// current device, once per (kernel, device); safe to call from several host
+// threads and for several devices in one process.
+cudaError_t smem_optin(const void* kernel, int bytes);
+// Number of SMs of the current device (cached per device).
+int sm_count();
 gi_status set_cuda_error(cudaError_t e, const char* what);
 gi_status set_error(gi_status st, const char* fmt, ...);
 

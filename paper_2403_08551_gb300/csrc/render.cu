@@ -231,13 +231,9 @@ cudaError_t launch_cfg(const float4* rec_binned, const int2* ranges, const Batch
                        cudaStream_t s) {
     static_assert(Cfg::kSmem <= 96 * 1024, "dynamic shared memory of the render");
     if (B.total_tiles <= 0) return cudaSuccess;
-    static bool attr = false;  // the dynamic window plus the static part may exceed the default 48 KB
-    if (!attr) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(k_render<Cfg>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::kSmem);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    // the dynamic window plus the static part may exceed the default 48 KB
+    const cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_render<Cfg>), Cfg::kSmem);
+    if (e != cudaSuccess) return e;
     return launch_pdl(k_render<Cfg>, dim3(B.total_tiles), dim3(Cfg::kThreads), Cfg::kSmem, s, rec_binned, ranges, B,
                       target, out, dl_hwc, dl_tiled, loss_sum, status);
 }

@@ -40,7 +40,7 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_version_and_status_strings(lib):
-    assert lib.gi_abi_version() == 7
+    assert lib.gi_abi_version() == 8
     assert lib.gi_status_string(0) == b"GI_OK"
     assert lib.gi_status_string(3) == b"GI_ERR_CAPACITY"
 

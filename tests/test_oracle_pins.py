@@ -171,6 +171,44 @@ def test_rect_culling():
     assert np.all(rect[1:] == 0)
 
 
+def test_culling_rule_covers_a_finite_record_factor():
+    """The support rule culls on the FP32 inverse covariance (Eq. 5 needs a
+    finite Sigma^-1). A renderer that evaluates sigma through the scaled
+    inverse Cholesky factor k L^-1 (k = sqrt(log2(e)/2), m11 = k/l1,
+    m21 = -(l2 m11)/l3, m22 = k/l3 in FP32) needs no cull of its own. With
+    F = FLT_MAX, a finite S22 = l2^2 + l3^2 and finite
+    A = S22/(l1 l3)^2 >= 1/l1^2, C = 1/l3^2 give |l1|, |l3| >= 1/sqrt(F) and
+    |l2/l1| <= sqrt(F) |l2 l3| / sqrt(l2^2 + l3^2) <= F/2, so |m11|, |m22|
+    <= k sqrt(F) and the largest intermediate, |l2 m11|, stays below k F/2:
+    a margin of 2.4x that rounding cannot close. Checked on the oracle's
+    own cull over random magnitudes across the whole FP32 range and a dense
+    sample at that extreme (l2 = l3 near sqrt(F/2), l1 near sqrt(2/F))."""
+    W, H, T = 64, 64, 16
+    g = np.random.default_rng(17)
+    n = 400000
+    mag = lambda lo, hi, k: (10.0 ** g.uniform(lo, hi, k)) * g.choice([-1.0, 1.0], k)
+    l1 = np.concatenate([mag(-46, 39, n), 10.0 ** g.uniform(np.log10(7.0e-20), np.log10(1.0e-19), n)])
+    l2 = np.concatenate([mag(-46, 39, n), mag(np.log10(1.1e19), np.log10(1.4e19), n)])
+    l3 = np.concatenate([mag(-46, 39, n), mag(np.log10(1.1e19), np.log10(1.4e19), n)])
+    with np.errstate(over="ignore"):  # magnitudes above FLT_MAX become infinities (culled)
+        chol = np.stack([l1, l2, l3], axis=1).astype(np.float32)
+    m = len(chol)
+    means = np.full((m, 2), 20.0, np.float32)
+    col = np.full((m, 3), 0.1, np.float32)
+    with np.errstate(all="ignore"):
+        rect, cnt = oracle.rect_rule(means, chol, col, W, H, T)
+        f1, f2, f3 = chol[:, 0], chol[:, 1], chol[:, 2]
+        k = np.float32(0.84932180028801904272)
+        m11 = k / f1
+        m22 = k / f3
+        m21 = -((f2 * m11) / f3)
+    kept = cnt > 0
+    assert kept[:n].sum() > 20000 and (~kept[:n]).sum() > 20000 and kept[n:].sum() > 20000
+    assert np.all(np.isfinite(m11[kept]) & np.isfinite(m21[kept]) & np.isfinite(m22[kept]))
+    with np.errstate(all="ignore"):
+        assert np.max(np.abs(f2[kept] * m11[kept])) <= 0.5 * np.finfo(np.float32).max
+
+
 @pytest.mark.parametrize("W,H,T", [(64, 48, 8), (61, 45, 8), (100, 70, 16), (130, 99, 32)])
 def test_binning_brute_force(W, H, T):
     """Per-tile lists = every g whose rect holds the tile, ascending g."""

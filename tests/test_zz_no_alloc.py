@@ -70,30 +70,55 @@ def _bin(lib, rec, rect, cnt, W, H, T, cap, noalloc):
                               _p(ids), _p(ranges), _p(recb), _p(pair_off), _p(k), _stream())
     assert rc == 0, lib.gi_last_error()
     torch.cuda.synchronize()
+    bits = ctypes.c_uint32(0)
+    assert lib.gi_device_errors(ctypes.byref(bits), 1, _stream()) == 0
     K = int(k.item())
-    assert K <= cap
-    return dict(K=K, keys=keys[:K].cpu().numpy(), ids=ids[:K].cpu().numpy(), ranges=ranges.cpu().numpy(),
-                recb=recb[:K].cpu().numpy().view(np.uint32), pair_off=pair_off.cpu().numpy())
+    Kv = min(K, cap)
+    return dict(K=K, bits=bits.value, keys=keys[:Kv].cpu().numpy(), ids=ids[:Kv].cpu().numpy(),
+                ranges=ranges.cpu().numpy(), recb=recb[:Kv].cpu().numpy().view(np.uint32),
+                pair_off=pair_off.cpu().numpy())
 
 
 def _same(a, b):
-    assert a["K"] == b["K"]
+    assert a["K"] == b["K"] and a["bits"] == b["bits"]
     for key in ("keys", "ids", "ranges", "recb", "pair_off"):
         np.testing.assert_array_equal(a[key], b[key], err_msg=key)
 
 
+# (W, H, T, n, seed, capacity): 256 and 273 tiles take the count-matrix
+# path; 768x512 at T = 8 (6144 tiles) and 1400x700 at T = 16 (3872 tiles)
+# take the radix path, which reuses the array's look-back words, digit
+# histograms and tickets at other offsets than the count-matrix layout.
+CM_A = (256, 256, 16, 2000, 0, 40000)
+CM_B = (161, 97, 8, 700, 7, 30000)
+RADIX_A = (768, 512, 8, 20000, 11, 400000)
+RADIX_B = (1400, 700, 16, 6000, 12, 200000)
+
+
 def test_noalloc_matches_bin_tiles_on_consecutive_calls(lib):
-    # Two different workloads back to back: the second call must not see any
-    # state left in the shared scratch by the first.
-    for (W, H, T, n, seed, cap) in [(256, 256, 16, 2000, 0, 40000), (161, 97, 8, 700, 7, 30000),
-                                    (256, 256, 16, 2000, 0, 40000)]:
+    # Workloads back to back, alternating the two binning paths, each case
+    # twice in a row: no call may see state another left in the shared array.
+    for (W, H, T, n, seed, cap) in [CM_A, RADIX_A, CM_B, RADIX_B, CM_A, RADIX_A]:
         rec, rect, cnt = _project(lib, W, H, T, n, seed)
         ref = _bin(lib, rec, rect, cnt, W, H, T, cap, noalloc=False)
         first = _bin(lib, rec, rect, cnt, W, H, T, cap, noalloc=True)
         second = _bin(lib, rec, rect, cnt, W, H, T, cap, noalloc=True)
-        assert ref["K"] > 0
+        assert 0 < ref["K"] <= cap and ref["bits"] == 0
         _same(ref, first)
         _same(ref, second)
+
+
+def test_noalloc_capacity_shortfall_matches_bin_tiles(lib):
+    # A capacity below the pair count: both entry points report the true K,
+    # raise the capacity bit and bin the same first pairs, on either path.
+    for (W, H, T, n, seed, _) in [CM_A, RADIX_A]:
+        rec, rect, cnt = _project(lib, W, H, T, n, seed)
+        K = int(cnt.to(torch.int64).sum().item())
+        cap = K // 2
+        ref = _bin(lib, rec, rect, cnt, W, H, T, cap, noalloc=False)
+        got = _bin(lib, rec, rect, cnt, W, H, T, cap, noalloc=True)
+        assert ref["K"] == K and ref["bits"] & 1
+        _same(ref, got)
 
 
 def test_noalloc_rejects_sizes_beyond_its_array(lib):
