@@ -507,15 +507,22 @@ def codec_decode(gi, torch, stream, flush, T=16, reps=50):
     K = gi.bin_tiles(rect, cnt, None, w.W, w.H, T).K
     r = gi.Renderer(w.W, w.H, n, T, capacity=int(K * 1.5) + 4096)
 
+    out1 = (torch.empty((n, 2), dtype=torch.float32, device="cuda"),
+            torch.empty((n, 3), dtype=torch.float32, device="cuda"),
+            torch.empty((n, 3), dtype=torch.float32, device="cuda"))
+
     def decode_render():
-        mm, ll, cc = gi.vq_decode(m16, idx, cb)
+        mm, ll, cc = gi.vq_decode(m16, idx, cb, out=out1)
         r(mm, ll, cc)
 
     dr_ms = _time(torch, stream, decode_render, reps, flush)
     nb = 64 * n
     idx_b = torch.from_numpy(synth.vq_indices(nb, 4001)).cuda()
     m16_b = torch.from_numpy(np.tile(w.means, (64, 1)).astype(np.float16)).cuda()
-    dec_ms = _time(torch, stream, lambda: gi.vq_decode(m16_b, idx_b, cb), reps, flush)
+    out_b = (torch.empty((nb, 2), dtype=torch.float32, device="cuda"),
+             torch.empty((nb, 3), dtype=torch.float32, device="cuda"),
+             torch.empty((nb, 3), dtype=torch.float32, device="cuda"))
+    dec_ms = _time(torch, stream, lambda: gi.vq_decode(m16_b, idx_b, cb, out=out_b), reps, flush)
     bytes_dec = nb * (4 + 4 + 32)
     assert gi.device_errors(clear=True) == 0
     return {"workload": "768x512, 50,000 Gaussians, FP16 means, 2x256-entry RVQ codebooks", "decode_render_fps":

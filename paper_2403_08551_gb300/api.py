@@ -147,9 +147,10 @@ def render_backward(bins: Bins, rect, cnt, chol, dl_dout, W: int, H: int, tile: 
     return gm, gl, gc, gq
 
 
-def vq_decode(means16, idx, codebooks):
+def vq_decode(means16, idx, codebooks, out=None):
     """Codec decode (Sec. 3.3). means16 [n,2] float16 or int16/uint16 bits,
-    idx [2,M,n] uint8, codebooks [2,M,B,3] float32."""
+    idx [2,M,n] uint8, codebooks [2,M,B,3] float32. out: optional
+    preallocated (means [n,2], chol [n,3], color [n,3]) float32 tensors."""
     lib = L.load()
     if means16.dtype == torch.float16:
         means16 = means16.view(torch.int16)
@@ -159,9 +160,12 @@ def vq_decode(means16, idx, codebooks):
     n = means16.shape[0]
     M, B = cb.shape[1], cb.shape[2]
     dev = means16.device
-    means = torch.empty((n, 2), dtype=torch.float32, device=dev)
-    chol = torch.empty((n, 3), dtype=torch.float32, device=dev)
-    color = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    if out is None:
+        means = torch.empty((n, 2), dtype=torch.float32, device=dev)
+        chol = torch.empty((n, 3), dtype=torch.float32, device=dev)
+        color = torch.empty((n, 3), dtype=torch.float32, device=dev)
+    else:
+        means, chol, color = (_dev(t, torch.float32, "out") for t in out)
     L.check(lib.gi_vq_decode(L.ptr(means16), L.ptr(idx), L.ptr(cb), n, M, B, L.ptr(means), L.ptr(chol),
                              L.ptr(color), L.stream_handle()), "gi_vq_decode")
     return means, chol, color

@@ -191,7 +191,7 @@ gi_status gi_bin_tiles(const int32_t* rect, const int32_t* cnt, const float* rec
     GI_REQUIRE(ws_bytes >= w.bytes, "gi_bin_tiles: workspace %zu bytes < %zu needed", ws_bytes, w.bytes);
     cudaError_t e = launch_bin(reinterpret_cast<const int4*>(rect), cnt, reinterpret_cast<const float4*>(rec), B,
                                capacity, w, false, keys, ids, reinterpret_cast<int2*>(ranges),
-                               reinterpret_cast<float4*>(rec_binned), pair_off, k_dev, nullptr, device_status(),
+                               reinterpret_cast<float4*>(rec_binned), nullptr, pair_off, k_dev, nullptr, device_status(),
                                reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return set_cuda_error(e, "gi_bin_tiles");
     return GI_OK;
@@ -210,7 +210,7 @@ gi_status gi_render(const float* rec_binned, const int32_t* ranges, gi_image img
                "gi_render: misaligned pointer");
     const Batch B = single(img, 0);
     cudaError_t e = launch_render(reinterpret_cast<const float4*>(rec_binned), reinterpret_cast<const int2*>(ranges),
-                                  B, target, out, dl_dout, nullptr, loss_sum, device_status(),
+                                  B, target, out, dl_dout, nullptr, loss_sum, nullptr, device_status(),
                                   reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return set_cuda_error(e, "gi_render");
     return GI_OK;
@@ -223,8 +223,9 @@ gi_status gi_backward_workspace_size(int32_t n, gi_image img, int64_t capacity, 
     GI_REQUIRE(n >= 0 && capacity >= 1 && capacity <= kMaxCapacity, "gi_backward_workspace_size: bad n or capacity");
     const Batch B = single(img, n);
     const size_t part = ((size_t)capacity * 32 + 255) / 256 * 256;
-    const size_t dl = (size_t)B.total_tiles * img.tile * img.tile * 12;
-    *bytes = part + dl;
+    const size_t dl = ((size_t)B.total_tiles * img.tile * img.tile * 12 + 255) / 256 * 256;
+    const size_t emit = ((size_t)capacity * 4 + 255) / 256 * 256;
+    *bytes = part + dl + emit;
     return GI_OK;
 }
 
@@ -243,20 +244,26 @@ gi_status gi_render_backward(const float* rec_binned, const uint32_t* keys, cons
     GI_REQUIRE(rec_binned && keys && ids && rect && cnt && pair_off && k_dev && chol && dl_dout && ws && g_means &&
                    g_chol && g_color,
                "gi_render_backward: NULL pointer");
-    GI_REQUIRE(aligned(rec_binned, 16) && aligned(rect, 16) && aligned(ws, 256) && aligned(pair_off, 8) &&
-                   aligned(k_dev, 8),
+    GI_REQUIRE(aligned(rec_binned, 16) && aligned(keys, 16) && aligned(rect, 16) && aligned(ws, 256) &&
+                   aligned(pair_off, 8) && aligned(k_dev, 8),
                "gi_render_backward: misaligned pointer");
     size_t need = 0;
     gi_backward_workspace_size(n, img, capacity, &need);
     GI_REQUIRE(ws_bytes >= need, "gi_render_backward: workspace %zu bytes < %zu needed", ws_bytes, need);
     const Batch B = single(img, n);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t part_bytes = ((size_t)capacity * 32 + 255) / 256 * 256;
+    const size_t dl_bytes = ((size_t)B.total_tiles * img.tile * img.tile * 12 + 255) / 256 * 256;
     float4* partial = static_cast<float4*>(ws);
-    float* dl_tiled = reinterpret_cast<float*>(static_cast<char*>(ws) + ((size_t)capacity * 32 + 255) / 256 * 256);
+    float* dl_tiled = reinterpret_cast<float*>(static_cast<char*>(ws) + part_bytes);
+    uint32_t* emit = reinterpret_cast<uint32_t*>(static_cast<char*>(ws) + part_bytes + dl_bytes);
     cudaError_t e = launch_pack_dl(dl_dout, B, dl_tiled, s);
     if (e == cudaSuccess)
-        e = launch_backward(reinterpret_cast<const float4*>(rec_binned), keys, ids, reinterpret_cast<const int4*>(rect),
-                            pair_off, dl_tiled, B, k_dev, capacity, partial, device_status(), s);
+        e = launch_emit_index(keys, ids, reinterpret_cast<const int4*>(rect), pair_off, B, k_dev, capacity, emit,
+                              device_status(), s);
+    if (e == cudaSuccess)
+        e = launch_backward(reinterpret_cast<const float4*>(rec_binned), keys, emit, dl_tiled, B, k_dev, capacity,
+                            partial, device_status(), s);
     if (e == cudaSuccess)
         e = launch_reduce(partial, pair_off, cnt, capacity, n, params_soa(nullptr, chol, nullptr), g_means, g_chol,
                           g_color, g_conic, nullptr, nullptr, nullptr, nullptr, nullptr, B, s);

@@ -21,6 +21,8 @@
 // has "g2 l2" where Sigma22 = l2^2 + l3^2 gives 2 g3 l2.) Optionally followed
 // by an Adam step (Kingma & Ba, bias-corrected) on the AoS parameters.
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "kernels.cuh"
 
@@ -36,20 +38,77 @@ __device__ __forceinline__ void kahan_add(float& s, float& c, float x) {
     s = t;
 }
 
-// Walks the T x T pixels of one tile for one pair. dL/dC is planar per tile
-// (R, G, B planes of T*T floats), so one float4 load gives four neighbouring
-// pixels of a channel and the arithmetic runs on packed FP32 pairs
-// (fma/add/mul.rn.f32x2): each instruction advances two pixels.
+// Sums of one row of the tile for one pair: u = sum e, v = sum e dx,
+// qm = sum e dx^2 over the row's pixels (e = <G, c'> w) and the colour sums
+// gc += G w. dL/dC is planar per tile (R, G, B planes of T*T floats), so one
+// float4 load gives four neighbouring pixels of a channel, and the arithmetic
+// runs on packed FP32 pairs (fma/add/mul.rn.f32x2): each instruction
+// advances two pixels. dx, dx^2 and z1^2 = (m11 dx)^2 of the row's pixel
+// pairs do not depend on the row and are passed in registers for tiles of up
+// to 16 x 16, so a pixel pair costs two packed operations for sigma.
+template <int T, bool kHoist, int NH>
+__device__ __forceinline__ void row_sums(const float* __restrict__ G, int y, float2 M11, float2 M21, float z2y,
+                                         float2 cr, float2 cg, float2 cb, float2 d0, const float2 (&DX)[NH],
+                                         const float2 (&DX2)[NH], const float2 (&Z1S)[NH], float2& gcr, float2& gcg,
+                                         float2& gcb, float& us, float& vs, float& qs) {
+    constexpr int NPIX = T * T;
+    const float2 Z2Y = make_float2(z2y, z2y);
+    float2 u = make_float2(0.f, 0.f), v = u, qm = u;
+    const float4* Rr = reinterpret_cast<const float4*>(G + y * T);
+    const float4* Rg = reinterpret_cast<const float4*>(G + NPIX + y * T);
+    const float4* Bb_ = reinterpret_cast<const float4*>(G + 2 * NPIX + y * T);
+#pragma unroll
+    for (int x4 = 0; x4 < T / 4; ++x4) {
+        const float4 R = Rr[x4], Gg = Rg[x4], Bb = Bb_[x4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float2 gr = h ? make_float2(R.z, R.w) : make_float2(R.x, R.y);
+            const float2 gg = h ? make_float2(Gg.z, Gg.w) : make_float2(Gg.x, Gg.y);
+            const float2 gb = h ? make_float2(Bb.z, Bb.w) : make_float2(Bb.x, Bb.y);
+            const float xo = (float)(4 * x4 + 2 * h);
+            const int hi = kHoist ? 2 * x4 + h : 0;
+            const float2 dx = kHoist ? DX[hi] : __fadd2_rn(d0, make_float2(xo, xo));
+            const float2 z2 = __ffma2_rn(M21, dx, Z2Y);
+            float2 z1s;
+            if (kHoist) {
+                z1s = Z1S[hi];
+            } else {
+                const float2 z1 = __fmul2_rn(M11, dx);
+                z1s = __fmul2_rn(z1, z1);
+            }
+            const float2 q = __ffma2_rn(z2, z2, z1s);            // sigma log2(e) = |M d|^2
+            const float2 w = make_float2(ex2(-q.x), ex2(-q.y));  // exp(-sigma)
+            gcr = __ffma2_rn(gr, w, gcr);
+            gcg = __ffma2_rn(gg, w, gcg);
+            gcb = __ffma2_rn(gb, w, gcb);
+            const float2 gw = __ffma2_rn(gb, cb, __ffma2_rn(gg, cg, __fmul2_rn(gr, cr)));
+            const float2 e = __fmul2_rn(gw, w);
+            u = __fadd2_rn(u, e);
+            if (kHoist) {
+                v = __ffma2_rn(e, dx, v);
+                qm = __ffma2_rn(e, DX2[hi], qm);
+            } else {
+                const float2 t1 = __fmul2_rn(e, dx);
+                v = __fadd2_rn(v, t1);
+                qm = __ffma2_rn(t1, dx, qm);
+            }
+        }
+    }
+    us = u.x + u.y;
+    vs = v.x + v.y;
+    qs = qm.x + qm.y;
+}
+
+// Walks the T x T pixels of one tile for one pair and returns its eight
+// sums. The moment sums are Kahan-compensated across pairs of rows: the
+// per-pair sums cancel strongly for Gaussians near equilibrium, and the row
+// partials are the large terms of that cancellation.
 template <int T>
 __device__ __forceinline__ void pair_sums(const float* __restrict__ G, float4 r0, float4 r1, float dx0, float dyb,
                                           float (&out)[8]) {
-    constexpr int NPIX = T * T;
     const float2 M11 = make_float2(r0.z, r0.z), M21 = make_float2(r0.w, r0.w);
     const float2 cr = make_float2(r1.y, r1.y), cg = make_float2(r1.z, r1.z), cb = make_float2(r1.w, r1.w);
     const float2 d0 = make_float2(dx0, dx0 + 1.0f);
-    // dx, dx^2 and z1^2 = (m11 dx)^2 of the strip's pixel pairs do not depend
-    // on the row: kept in registers for tiles of up to 16 x 16, so a pixel
-    // pair costs two packed operations for sigma (z2, then z2^2 + z1^2).
     constexpr bool kHoist = T <= 16;
     constexpr int NH = kHoist ? T / 2 : 1;
     float2 DX[NH], DX2[NH], Z1S[NH];
@@ -63,62 +122,21 @@ __device__ __forceinline__ void pair_sums(const float* __restrict__ G, float4 r0
         }
     }
     float2 gcr = make_float2(0.f, 0.f), gcg = gcr, gcb = gcr;
-    // Moment sums with Kahan compensation across rows: the per-pair sums
-    // cancel strongly for Gaussians near equilibrium, and the row partials
-    // are the large terms of that cancellation.
     float S[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, cS[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll 1
-    for (int y = 0; y < T; ++y) {
-        const float dy = dyb + (float)y;
-        const float z2y = r1.x * dy;
-        const float2 Z2Y = make_float2(z2y, z2y);
-        float2 u = make_float2(0.f, 0.f), v = u, qm = u;
-        const float4* Rr = reinterpret_cast<const float4*>(G + y * T);
-        const float4* Rg = reinterpret_cast<const float4*>(G + NPIX + y * T);
-        const float4* Bb_ = reinterpret_cast<const float4*>(G + 2 * NPIX + y * T);
-#pragma unroll
-        for (int x4 = 0; x4 < T / 4; ++x4) {
-            const float4 R = Rr[x4], Gg = Rg[x4], Bb = Bb_[x4];
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const float2 gr = h ? make_float2(R.z, R.w) : make_float2(R.x, R.y);
-                const float2 gg = h ? make_float2(Gg.z, Gg.w) : make_float2(Gg.x, Gg.y);
-                const float2 gb = h ? make_float2(Bb.z, Bb.w) : make_float2(Bb.x, Bb.y);
-                const float xo = (float)(4 * x4 + 2 * h);
-                const int hi = kHoist ? 2 * x4 + h : 0;
-                const float2 dx = kHoist ? DX[hi] : __fadd2_rn(d0, make_float2(xo, xo));
-                const float2 z2 = __ffma2_rn(M21, dx, Z2Y);
-                float2 z1s;
-                if (kHoist) {
-                    z1s = Z1S[hi];
-                } else {
-                    const float2 z1 = __fmul2_rn(M11, dx);
-                    z1s = __fmul2_rn(z1, z1);
-                }
-                const float2 q = __ffma2_rn(z2, z2, z1s);  // sigma log2(e) = |M d|^2
-                const float2 w = make_float2(ex2(-q.x), ex2(-q.y));  // exp(-sigma)
-                gcr = __ffma2_rn(gr, w, gcr);
-                gcg = __ffma2_rn(gg, w, gcg);
-                gcb = __ffma2_rn(gb, w, gcb);
-                const float2 gw = __ffma2_rn(gb, cb, __ffma2_rn(gg, cg, __fmul2_rn(gr, cr)));
-                const float2 e = __fmul2_rn(gw, w);
-                u = __fadd2_rn(u, e);
-                if (kHoist) {
-                    v = __ffma2_rn(e, dx, v);
-                    qm = __ffma2_rn(e, DX2[hi], qm);
-                } else {
-                    const float2 t1 = __fmul2_rn(e, dx);
-                    v = __fadd2_rn(v, t1);
-                    qm = __ffma2_rn(t1, dx, qm);
-                }
-            }
-        }
-        const float us = u.x + u.y, vs = v.x + v.y, qs = qm.x + qm.y;
-        kahan_add(S[0], cS[0], vs);
-        kahan_add(S[1], cS[1], us * dy);
-        kahan_add(S[2], cS[2], qs);
-        kahan_add(S[3], cS[3], vs * dy);
-        kahan_add(S[4], cS[4], us * dy * dy);
+    for (int y = 0; y < T; y += 2) {
+        const float dy0 = dyb + (float)y, dy1 = dy0 + 1.0f;
+        float us0, vs0, qs0, us1, vs1, qs1;
+        row_sums<T, kHoist, NH>(G, y, M11, M21, r1.x * dy0, cr, cg, cb, d0, DX, DX2, Z1S, gcr, gcg, gcb, us0, vs0,
+                                qs0);
+        row_sums<T, kHoist, NH>(G, y + 1, M11, M21, r1.x * dy1, cr, cg, cb, d0, DX, DX2, Z1S, gcr, gcg, gcb, us1,
+                                vs1, qs1);
+        const float a0 = us0 * dy0, a1 = us1 * dy1;
+        kahan_add(S[0], cS[0], vs0 + vs1);
+        kahan_add(S[1], cS[1], a0 + a1);
+        kahan_add(S[2], cS[2], qs0 + qs1);
+        kahan_add(S[3], cS[3], vs0 * dy0 + vs1 * dy1);
+        kahan_add(S[4], cS[4], a0 * dy0 + a1 * dy1);
     }
     out[0] = gcr.x + gcr.y;
     out[1] = gcg.x + gcg.y;
@@ -134,83 +152,194 @@ __device__ __forceinline__ void tile_origin(const Batch& B, uint32_t t, int T, i
     ty = lt / d.tw;
 }
 
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+constexpr int kBwdWarps = 8;  // warps per backward block
+constexpr int kBwdThreads = kBwdWarps * 32;
+
 // Planar dL/dC floats of one tile.
 template <int T>
 __host__ __device__ constexpr int tile_floats() { return 3 * T * T; }
-// Tiles of up to 16 x 16 pixels are staged in shared memory, two per warp.
+// Tiles of up to 16 x 16 pixels are staged in shared memory, two slots per warp.
 template <int T>
 __host__ __device__ constexpr bool stage_dl() { return T <= 16; }
-template <int T>
-constexpr size_t backward_smem() { return stage_dl<T>() ? 8 * 2 * tile_floats<T>() * sizeof(float) : 0; }
 
-// One warp task = 32 consecutive pairs of the sorted list, one per lane
-// (uniform work: every pair walks T x T pixels). Tiles of up to 16 x 16:
-// the warp copies the planar dL/dC of the tiles of its first and last
-// pending lane into its shared buffer (cp.async), then every lane whose pair
-// lies on one of those two tiles walks it from shared memory; a task that
-// spans more than two tiles (only tiles with fewer than 32 pairs do) repeats
-// this for the lanes left. Larger tiles read dL/dC from global memory.
+// Shared memory of one warp: the records, tile keys and emission indices of
+// its current and next task (double buffer), then the two staged tiles.
 template <int T>
-__global__ void __launch_bounds__(256, T <= 16 ? 2 : 3) k_backward(const float4* __restrict__ rec_binned,
-                                                  const uint32_t* __restrict__ keys,
-                                                  const uint32_t* __restrict__ ids, const int4* __restrict__ rect,
-                                                  const int64_t* __restrict__ pair_off,
-                                                  const float* __restrict__ dl_tiled, Batch B,
-                                                  const int64_t* __restrict__ k_dev, int64_t capacity,
-                                                  float4* __restrict__ partial, uint32_t* __restrict__ status) {
+struct BwdWarpSmem {
+    float4 rec[2][64];
+    uint32_t key[2][32];
+    uint32_t emit[2][32];
+    float g[stage_dl<T>() ? 2 * tile_floats<T>() : 4];
+};
+template <int T>
+constexpr size_t backward_smem() { return kBwdWarps * sizeof(BwdWarpSmem<T>); }
+
+// cp.async of the records, keys and emission indices of the 32 pairs of
+// task `task` (pairs 32 task .. 32 task + 31, those below K) into buffer b.
+template <int T>
+__device__ __forceinline__ void prefetch_task(BwdWarpSmem<T>& w, int b, int task, int K, int lane,
+                                              const float4* __restrict__ rec_binned, const uint32_t* __restrict__ keys,
+                                              const uint32_t* __restrict__ emit) {
+    const int k0 = task * 32;
+#pragma unroll
+    for (int c = lane; c < 64; c += 32)  // 16-byte halves of the 32-byte records
+        if (k0 + (c >> 1) < K) cp_async16(&w.rec[b][c], rec_binned + 2 * (size_t)k0 + c);
+    if (lane < 16) {  // lanes 0-7: keys, 8-15: emission indices, four per copy
+        const int c = lane & 7;
+        const uint32_t* src = (lane < 8 ? keys : emit) + k0 + 4 * c;
+        uint32_t* dst = (lane < 8 ? w.key[b] : w.emit[b]) + 4 * c;
+        if (k0 + 4 * c + 3 < K) {
+            cp_async16(dst, src);
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (k0 + 4 * c + e < K) cp_async4(dst + e, src + e);
+        }
+    }
+}
+
+// Persistent backward: one warp task = 32 consecutive pairs of the sorted
+// list, one per lane (uniform work: every pair walks T x T pixels). Warp r
+// of the grid (ranked block-minor, so that the warps with one task more are
+// spread over all SMs) owns a contiguous range of tasks; while it works on
+// one task, the records, keys and emission indices of the next are already
+// on their way to its shared memory (cp.async, double-buffered), so the
+// warps of an SM, which run equal-length tasks in step, do not all wait on
+// global memory at the same time. Tiles of up to 16 x 16: the warp keeps
+// two tiles of planar dL/dC in shared memory and reloads a slot only when
+// a task needs a tile it does not hold (consecutive tasks mostly share
+// tiles); a task whose pairs span more than two tiles (tiles with fewer than
+// 32 pairs) takes one more round per extra pair of tiles. Larger tiles read
+// dL/dC from global memory. Each pair's sums land at its emission index.
+template <int T>
+__global__ void __launch_bounds__(kBwdThreads, 2) k_backward(
+    const float4* __restrict__ rec_binned, const uint32_t* __restrict__ keys, const uint32_t* __restrict__ emit,
+    const float* __restrict__ dl_tiled, Batch B, const int64_t* __restrict__ k_dev, int64_t capacity,
+    float4* __restrict__ partial, uint32_t* __restrict__ status) {
     constexpr int TF = tile_floats<T>();
-    extern __shared__ float4 s_dl[];
+    extern __shared__ float4 s_dyn[];
     pdl_wait();
     const int K = (int)min(*k_dev, capacity);
-    const int lane = threadIdx.x & 31;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    float* wbuf = reinterpret_cast<float*>(s_dl) + (stage_dl<T>() ? (threadIdx.x >> 5) * 2 * TF : 0);
-    for (int task = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; task * 32 < K; task += nwarps) {
-        const int k = min(task * 32 + lane, K - 1);
-        const float4 r0 = rec_binned[2 * (size_t)k], r1 = rec_binned[2 * (size_t)k + 1];
-        uint32_t t = keys[k], g = ids[k];
-        const bool inb = gi_in_bounds(t < (uint32_t)B.total_tiles && g < (uint32_t)B.total_gauss, status);
-        if (!inb) t = g = 0;  // bounds-checking build: the pair is skipped
-        const int4 r = rect[g];
-        const int64_t po = pair_off[g];
-        int tx, ty;
-        tile_origin(B, t, T, tx, ty);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    BwdWarpSmem<T>& w = reinterpret_cast<BwdWarpSmem<T>*>(s_dyn)[wib];
+    const int nt = (K + 31) >> 5;
+    const int W = gridDim.x * kBwdWarps;
+    const int r = wib * gridDim.x + blockIdx.x;
+    const int Q = nt / W, R = nt % W;
+    const int t_begin = r * Q + min(r, R), t_end = t_begin + Q + (r < R ? 1 : 0);
+    if (t_begin >= t_end) return;
+    uint32_t tag[2] = {0xffffffffu, 0xffffffffu};  // tiles held by the two slots (warp-uniform)
+    prefetch_task<T>(w, 0, t_begin, K, lane, rec_binned, keys, emit);
+    cp_async_commit();
+    int cur = 0;
+    for (int task = t_begin; task < t_end; ++task, cur ^= 1) {
+        cp_async_wait<0>();  // this task's records
+        __syncwarp();
+        const int k = task * 32 + lane;
+        const bool valid = k < K;
+        const float4 r0 = w.rec[cur][2 * lane], r1 = w.rec[cur][2 * lane + 1];
+        uint32_t t = w.key[cur][lane];
+        const uint32_t p = w.emit[cur][lane];
+        const bool inb = gi_in_bounds(!valid || t < (uint32_t)B.total_tiles, status);
+        if (!inb) t = 0;
+        int tx = 0, ty = 0;
+        if (valid) tile_origin(B, t, T, tx, ty);
         const float dx0 = (float)(tx * T) + 0.5f - r0.x, dyb = (float)(ty * T) + 0.5f - r0.y;
         float o[8];
         bool have = false;
-        if (stage_dl<T>()) {
-            uint32_t pending = __ballot_sync(0xffffffffu, task * 32 + lane < K);
-            while (pending) {
+        uint32_t pending = __ballot_sync(0xffffffffu, valid && inb);
+        bool first = true;
+        do {
+            if (stage_dl<T>()) {
+                // Tiles of the first and last pending lanes; slots reloaded
+                // only for tiles the warp does not hold.
                 const uint32_t ta = __shfl_sync(0xffffffffu, t, __ffs(pending) - 1);
                 const uint32_t tb = __shfl_sync(0xffffffffu, t, 31 - __clz(pending));
-                const float4* sa = reinterpret_cast<const float4*>(dl_tiled + (size_t)ta * TF);
-                const float4* sb = reinterpret_cast<const float4*>(dl_tiled + (size_t)tb * TF);
-                float4* da = reinterpret_cast<float4*>(wbuf);
-                for (int i = lane; i < TF / 4; i += 32) {
-                    cp_async16(da + i, sa + i);
-                    if (tb != ta) cp_async16(da + TF / 4 + i, sb + i);
+                const bool ha = tag[0] == ta || tag[1] == ta, hb = tag[0] == tb || tag[1] == tb;
+                if (!ha || !hb) {
+                    // keep the slot that holds a needed tile, fill the other(s)
+                    int keep = -1;
+                    if (tag[0] == ta || tag[0] == tb) keep = 0;
+                    else if (tag[1] == ta || tag[1] == tb) keep = 1;
+                    const uint32_t need0 = ha ? tb : ta;  // the first missing tile
+                    const int s0 = keep == 0 ? 1 : 0;
+                    const float4* src0 = reinterpret_cast<const float4*>(dl_tiled + (size_t)need0 * TF);
+                    float4* dst0 = reinterpret_cast<float4*>(w.g + s0 * TF);
+                    for (int i = lane; i < TF / 4; i += 32) cp_async16(dst0 + i, src0 + i);
+                    tag[s0] = need0;
+                    if (!ha && !hb && tb != ta) {  // both missing: the second into the other slot
+                        const float4* src1 = reinterpret_cast<const float4*>(dl_tiled + (size_t)tb * TF);
+                        float4* dst1 = reinterpret_cast<float4*>(w.g + (1 - s0) * TF);
+                        for (int i = lane; i < TF / 4; i += 32) cp_async16(dst1 + i, src1 + i);
+                        tag[1 - s0] = tb;
+                    }
                 }
-                cp_async_wait_all();
+                cp_async_commit();
+                if (first) {
+                    // the next task's records go out behind this task's tiles
+                    if (task + 1 < t_end) prefetch_task<T>(w, cur ^ 1, task + 1, K, lane, rec_binned, keys, emit);
+                    cp_async_commit();
+                    cp_async_wait<1>();  // the tiles (all but the newest group)
+                } else {
+                    cp_async_wait<0>();
+                }
                 __syncwarp();
-                const bool mine = ((pending >> lane) & 1u) && (t == ta || t == tb);
+                const bool mine = ((pending >> lane) & 1u) && (t == tag[0] || t == tag[1]);
                 if (mine) {
-                    pair_sums<T>(wbuf + (t == ta ? 0 : TF), r0, r1, dx0, dyb, o);
+                    pair_sums<T>(w.g + (t == tag[0] ? 0 : TF), r0, r1, dx0, dyb, o);
                     have = true;
                 }
                 pending &= ~__ballot_sync(0xffffffffu, mine);
                 __syncwarp();
+            } else {
+                if (first && task + 1 < t_end) prefetch_task<T>(w, cur ^ 1, task + 1, K, lane, rec_binned, keys, emit);
+                cp_async_commit();
+                if ((pending >> lane) & 1u) {
+                    pair_sums<T>(dl_tiled + (size_t)t * TF, r0, r1, dx0, dyb, o);
+                    have = true;
+                }
+                pending = 0;
             }
-        } else if (task * 32 + lane < K) {
-            pair_sums<T>(dl_tiled + (size_t)t * TF, r0, r1, dx0, dyb, o);
-            have = true;
-        }
-        if (have && inb) {
-            const int64_t p = po + (int64_t)(ty - r.y) * (r.z - r.x) + (tx - r.x);
-            if (p >= 0 && p < capacity) {
-                partial[2 * p] = make_float4(o[0], o[1], o[2], o[3]);
-                partial[2 * p + 1] = make_float4(o[4], o[5], o[6], o[7]);
+            first = false;
+        } while (pending);
+        if (have) {
+            if (p < (uint64_t)capacity) {
+                partial[2 * (size_t)p] = make_float4(o[0], o[1], o[2], o[3]);
+                partial[2 * (size_t)p + 1] = make_float4(o[4], o[5], o[6], o[7]);
+            } else {
+                flag_error(status, kErrBounds);
             }
         }
+    }
+    cp_async_wait<0>();
+}
+
+// Emission index of each sorted pair (for a binning that did not write it):
+// pair_off[g] + the row-major position of its tile in g's rectangle.
+__global__ void k_emit_index(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ ids,
+                             const int4* __restrict__ rect, const int64_t* __restrict__ pair_off, Batch B,
+                             const int64_t* __restrict__ k_dev, int64_t capacity, uint32_t* __restrict__ emit,
+                             uint32_t* __restrict__ status) {
+    pdl_wait();
+    const int K = (int)min(*k_dev, capacity);
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
+        const uint32_t t = keys[k], g = ids[k];
+        uint32_t e = 0xffffffffu;
+        if (t < (uint32_t)B.total_tiles && g < (uint32_t)B.total_gauss) {
+            const ImgDesc d = img_desc(B, image_of_tile(B, (int)t));
+            const int lt = (int)t - d.tile_base;
+            const int4 r = rect[g];
+            e = (uint32_t)(pair_off[g] + (int64_t)(lt / d.tw - r.y) * (r.z - r.x) + (lt % d.tw - r.x));
+        } else {
+            flag_error(status, kErrBounds);
+        }
+        emit[k] = e;
     }
 }
 
@@ -325,12 +454,34 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
                                                 ParamsIn P, float* __restrict__ g_means, float* __restrict__ g_chol,
                                                 float* __restrict__ g_color, float* __restrict__ g_conic,
                                                 AdamCfg cfg, float* __restrict__ params, float* __restrict__ m,
-                                                float* __restrict__ v, float* __restrict__ grads_aos, Batch B) {
+                                                float* __restrict__ v, float* __restrict__ grads_aos, Batch B,
+                                                const double* __restrict__ loss_tile, double* __restrict__ loss) {
     __shared__ int s_step;
     // Adam: 1/(1 - b1^t), 1/sqrt(1 - b2^t); Adan: 1/(1 - b1^t), 1/(1 - b2^t),
     // 1/sqrt(1 - b3^t); [3] = learning-rate factor of the halving schedule.
     __shared__ float s_bc[4];
     pdl_wait();
+    if (ADAM && loss_tile) {
+        // each image's squared error: its tiles' partials in tile order, eight
+        // loads in flight per thread, combined in a fixed order, then a fixed
+        // reduction tree (reproducible run to run)
+        __shared__ double s_lw[32];
+        for (int b = blockIdx.x; b < B.nimg; b += gridDim.x) {
+            const ImgDesc d = img_desc(B, b);
+            const int nt = d.tw * d.th;
+            double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+            for (int i0 = threadIdx.x; i0 < nt; i0 += 8 * blockDim.x) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int i = i0 + u * blockDim.x;
+                    if (i < nt) acc[u] += loss_tile[d.tile_base + i];
+                }
+            }
+            double tot = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+            tot = block_sum<double>(tot, s_lw);
+            if (threadIdx.x == 0) loss[b] = tot;
+        }
+    }
     if (ADAM) {
         if (threadIdx.x == 0) {
             const int step = *cfg.step + 1;
@@ -716,31 +867,63 @@ __global__ void __launch_bounds__(kCodecSumThreads) k_codec_update(CodecCfg Q, A
 
 }  // namespace
 
-cudaError_t launch_backward(const float4* rec_binned, const uint32_t* keys, const uint32_t* ids, const int4* rect,
-                            const int64_t* pair_off, const float* dl_tiled, const Batch& B, const int64_t* k_dev,
-                            int64_t capacity, float4* partial, uint32_t* status, cudaStream_t s) {
+namespace {
+
+// Resident blocks per SM of a kernel at its launch shape (cached per device).
+template <int T>
+int backward_blocks_per_sm() {
+    static std::mutex mu;
+    static std::map<int, int> cached;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    std::lock_guard<std::mutex> lk(mu);
+    int& v = cached[dev];
+    if (v <= 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_backward<T>, kBwdThreads, backward_smem<T>()) !=
+                cudaSuccess ||
+            nb <= 0)
+            nb = 1;
+        v = nb;
+    }
+    return v;
+}
+
+template <int T>
+cudaError_t launch_backward_t(const float4* rec_binned, const uint32_t* keys, const uint32_t* emit,
+                              const float* dl_tiled, const Batch& B, const int64_t* k_dev, int64_t capacity,
+                              float4* partial, uint32_t* status, cudaStream_t s) {
+    cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_backward<T>), (int)backward_smem<T>());
+    if (e != cudaSuccess) return e;
+    // persistent: one wave of resident blocks (no more than the tasks need)
+    const int64_t tasks = (capacity + 31) / 32;
+    const int64_t full = (int64_t)sm_count() * backward_blocks_per_sm<T>();
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(full, (tasks + kBwdWarps - 1) / kBwdWarps));
+    return launch_pdl(k_backward<T>, dim3(blocks), dim3(kBwdThreads), backward_smem<T>(), s, rec_binned, keys, emit,
+                      dl_tiled, B, k_dev, capacity, partial, status);
+}
+
+}  // namespace
+
+cudaError_t launch_backward(const float4* rec_binned, const uint32_t* keys, const uint32_t* emit,
+                            const float* dl_tiled, const Batch& B, const int64_t* k_dev, int64_t capacity,
+                            float4* partial, uint32_t* status, cudaStream_t s) {
     if (capacity <= 0) return cudaSuccess;
-    const int nsm = sm_count();
-    const int64_t need = (capacity + 255) / 256;  // 8 warps x 32 pairs per block-iteration
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)nsm * 8));
-    {
-        cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_backward<8>), (int)backward_smem<8>());
-        if (e == cudaSuccess) e = smem_optin(reinterpret_cast<const void*>(k_backward<16>), (int)backward_smem<16>());
-        if (e != cudaSuccess) return e;
-    }
     switch (B.tile) {
-        case 8:
-            return launch_pdl(k_backward<8>, dim3(blocks), dim3(256), backward_smem<8>(), s, rec_binned, keys, ids,
-                              rect, pair_off, dl_tiled, B, k_dev, capacity, partial, status);
-        case 16:
-            return launch_pdl(k_backward<16>, dim3(blocks), dim3(256), backward_smem<16>(), s, rec_binned, keys, ids,
-                              rect, pair_off, dl_tiled, B, k_dev, capacity, partial, status);
-        case 32:
-            return launch_pdl(k_backward<32>, dim3(blocks), dim3(256), 0, s, rec_binned, keys, ids, rect, pair_off,
-                              dl_tiled, B, k_dev, capacity, partial, status);
-        default:
-            return cudaErrorInvalidValue;
+        case 8: return launch_backward_t<8>(rec_binned, keys, emit, dl_tiled, B, k_dev, capacity, partial, status, s);
+        case 16: return launch_backward_t<16>(rec_binned, keys, emit, dl_tiled, B, k_dev, capacity, partial, status, s);
+        case 32: return launch_backward_t<32>(rec_binned, keys, emit, dl_tiled, B, k_dev, capacity, partial, status, s);
+        default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_emit_index(const uint32_t* keys, const uint32_t* ids, const int4* rect, const int64_t* pair_off,
+                              const Batch& B, const int64_t* k_dev, int64_t capacity, uint32_t* emit, uint32_t* status,
+                              cudaStream_t s) {
+    if (capacity <= 0) return cudaSuccess;
+    const int blocks = std::max(1, std::min<int>(sm_count() * 8, (int)((capacity + 255) / 256)));
+    return launch_pdl(k_emit_index, dim3(blocks), dim3(256), 0, s, keys, ids, rect, pair_off, B, k_dev, capacity, emit,
+                      status);
 }
 
 cudaError_t launch_pack_dl(const float* dl_hwc, const Batch& B, float* dl_tiled, cudaStream_t s) {
@@ -753,11 +936,13 @@ cudaError_t launch_pack_dl(const float* dl_hwc, const Batch& B, float* dl_tiled,
     }
 }
 
+int64_t reduce_blocks(int64_t n) { return std::max<int64_t>(1, (n + kReduceThreads - 1) / kReduceThreads); }
+
 cudaError_t launch_reduce(const float4* partial, const int64_t* pair_off, const int32_t* cnt, int64_t capacity,
                           int32_t n, const ParamsIn& P, float* g_means, float* g_chol, float* g_color,
                           float* g_conic, const AdamCfg* adam, float* params, float* m, float* v, float* grads_aos,
-                          const Batch& B, cudaStream_t s) {
-    const int blocks = std::max(1, (n + kReduceThreads - 1) / kReduceThreads);
+                          const Batch& B, cudaStream_t s, const double* loss_tile, double* loss) {
+    const int blocks = (int)reduce_blocks(n);
     if (adam) {
         const bool codec = B.codec.bits > 0;
         auto kern = codec ? k_reduce<true, true, 0>
@@ -765,7 +950,7 @@ cudaError_t launch_reduce(const float4* partial, const int64_t* pair_off, const 
                                               : (B.opac.mode == 2 ? k_reduce<true, false, 2> : k_reduce<true, false, 0>));
         cudaError_t e = launch_pdl(kern, dim3(blocks), dim3(kReduceThreads), 0, s, partial, pair_off, cnt, capacity, n,
                                    P, (float*)nullptr, (float*)nullptr, (float*)nullptr, (float*)nullptr, *adam, params,
-                                   m, v, grads_aos, B);
+                                   m, v, grads_aos, B, loss_tile, loss);
         if (e != cudaSuccess || B.codec.bits == 0) return e;
         const int nv = 6 + B.codec.stages * B.codec.size * 4 + 1;
         return launch_pdl(k_codec_update, dim3(nv), dim3(kCodecSumThreads), 0, s, B.codec, *adam, blocks, n);
@@ -773,7 +958,7 @@ cudaError_t launch_reduce(const float4* partial, const int64_t* pair_off, const 
     AdamCfg none{};
     return launch_pdl(k_reduce<false>, dim3(blocks), dim3(kReduceThreads), 0, s, partial, pair_off, cnt, capacity, n, P,
                       g_means, g_chol, g_color, g_conic, none, (float*)nullptr, (float*)nullptr, (float*)nullptr,
-                      (float*)nullptr, B);
+                      (float*)nullptr, B, (const double*)nullptr, (double*)nullptr);
 }
 
 }  // namespace gi

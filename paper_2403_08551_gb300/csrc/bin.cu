@@ -250,20 +250,56 @@ __global__ void __launch_bounds__(kProjBlock) k_blocksum(const int32_t* __restri
 // (tile, g) for its rect in row-major order at pair_off[g] + j. Also builds
 // the per-pass digit histograms of the radix sort.
 // ---------------------------------------------------------------------------
+// Exclusive prefix of block b's pair total over blocks 0 .. b - 1, by a
+// look-back that never waits: every block's total is already in blk_sum, and
+// a block publishes its inclusive prefix (flag bit 63) as soon as it knows
+// it, so a block sums the totals of its nearest predecessors back to the
+// first published prefix (32 words per round, warp 0). Integer sums: the
+// result does not depend on how far a block had to look.
+__device__ int64_t block_prefix_lookback(const int64_t* __restrict__ blk_sum, uint64_t* __restrict__ lb, int b) {
+    constexpr uint64_t kPub = 1ull << 63;
+    const int lane = threadIdx.x & 31;
+    int64_t excl = 0;
+    for (int j = b - 1; j >= 0; j -= 32) {
+        const int idx = j - lane;  // lane 0 = nearest predecessor
+        uint64_t w = 0;
+        int64_t v = 0;
+        if (idx >= 0) {
+            asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(lb + idx) : "memory");
+            v = (w & kPub) ? (int64_t)(w & ~kPub) : blk_sum[idx];
+        }
+        const uint32_t pub = __ballot_sync(0xffffffffu, idx >= 0 && (w & kPub));
+        // lanes up to and including the nearest published one
+        const uint32_t upto = pub ? ((2u << (__ffs(pub) - 1)) - 1u) : 0xffffffffu;
+        excl += warp_sum<int64_t>(((upto >> lane) & 1u) ? v : 0);
+        if (pub) break;
+    }
+    if (lane == 0) {
+        const uint64_t w = kPub | (uint64_t)(excl + blk_sum[b]);
+        asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(lb + b), "l"(w) : "memory");
+    }
+    return excl;
+}
+
 __global__ void __launch_bounds__(kProjBlock) k_emit(const int4* __restrict__ rect, const int32_t* __restrict__ cnt,
-                                                     const int64_t* __restrict__ blk_sum, Batch B, int64_t capacity,
+                                                     const int64_t* __restrict__ blk_sum, uint64_t* __restrict__ blk_lb,
+                                                     Batch B, int64_t capacity,
                                                      uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
                                                      int64_t* __restrict__ pair_off, int64_t* __restrict__ k_dev,
                                                      int64_t* __restrict__ k_max, uint32_t* __restrict__ hist,
                                                      RadixPlan rp, uint32_t* __restrict__ status) {
     __shared__ int64_t s_warp[32];
+    __shared__ int64_t s_pre;
     __shared__ uint32_t s_hist[kMaxPasses * kMaxRadix];
     pdl_wait();
     const int n = B.total_gauss;
     for (int i = threadIdx.x; i < kMaxPasses * kMaxRadix; i += blockDim.x) s_hist[i] = 0;
-    int64_t pre = 0;
-    for (int i = threadIdx.x; i < (int)blockIdx.x; i += blockDim.x) pre += blk_sum[i];
-    pre = block_sum<int64_t>(pre, s_warp);
+    if (threadIdx.x < 32) {
+        const int64_t e = block_prefix_lookback(blk_sum, blk_lb, blockIdx.x);
+        if (threadIdx.x == 0) s_pre = e;
+    }
+    __syncthreads();
+    const int64_t pre = s_pre;
     const int g = blockIdx.x * kProjBlock + threadIdx.x;
     const int c = g < n ? cnt[g] : 0;
     const int64_t incl = block_incl_scan<int64_t>((int64_t)c, s_warp);
@@ -481,20 +517,33 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
 
 // ranges[t] = [first, last + 1) of key t in the sorted keys; with rec_binned,
 // also gathers the record of each sorted pair (rec_binned[k] = rec[ids[k]]),
-// one pair per thread so the random reads overlap across the whole grid.
+// one pair per thread so the random reads overlap across the whole grid; with
+// emit, the emission index of each sorted pair (pair_off[g] + its row-major
+// position in g's rectangle), which the backward stores its sums at.
 __global__ void k_ranges(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ ids,
-                         const int64_t* __restrict__ k_dev, int64_t capacity, int2* __restrict__ ranges,
-                         int total_tiles, const float4* __restrict__ rec, float4* __restrict__ rec_binned,
-                         int n_gauss, uint32_t* __restrict__ status) {
+                         const int64_t* __restrict__ k_dev, int64_t capacity, int2* __restrict__ ranges, Batch B,
+                         const float4* __restrict__ rec, float4* __restrict__ rec_binned,
+                         const int4* __restrict__ rect, const int64_t* __restrict__ pair_off,
+                         uint32_t* __restrict__ emit, uint32_t* __restrict__ status) {
     pdl_wait();
     const int K = (int)min(*k_dev, capacity);
+    const int total_tiles = B.total_tiles, n_gauss = B.total_gauss;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
         const uint32_t t = keys[k];
-        if (rec_binned) {
+        if (rec_binned || emit) {
             const uint32_t g = ids[k];
-            if (g < (uint32_t)n_gauss) {
-                rec_binned[2 * (size_t)k] = rec[2 * (size_t)g];
-                rec_binned[2 * (size_t)k + 1] = rec[2 * (size_t)g + 1];
+            if (g < (uint32_t)n_gauss && t < (uint32_t)total_tiles) {
+                if (rec_binned) {
+                    rec_binned[2 * (size_t)k] = rec[2 * (size_t)g];
+                    rec_binned[2 * (size_t)k + 1] = rec[2 * (size_t)g + 1];
+                }
+                if (emit) {
+                    const ImgDesc d = img_desc(B, image_of_tile(B, (int)t));
+                    const int lt = (int)t - d.tile_base;
+                    const int4 r = rect[g];
+                    const int64_t p = pair_off[g] + (int64_t)(lt / d.tw - r.y) * (r.z - r.x) + (lt % d.tw - r.x);
+                    emit[k] = (uint32_t)p;
+                }
             } else {
                 flag_error(status, kErrBounds);
             }
@@ -542,7 +591,10 @@ BinWs bin_ws_layout(void* base, int64_t n, int64_t capacity, int total_tiles) {
         w.vals_tmp = static_cast<uint32_t*>(take(cap * 4));
     }
     const size_t zero_off = off;
-    if (!w.cm_path) w.hist = static_cast<uint32_t*>(take((size_t)rp.passes * kHistReplicas * kMaxRadix * 4));
+    if (!w.cm_path) {
+        w.hist = static_cast<uint32_t*>(take((size_t)rp.passes * kHistReplicas * kMaxRadix * 4));
+        w.blk_lb = static_cast<uint64_t*>(take((size_t)nblk * 8));
+    }
     w.lookback =
         static_cast<uint32_t*>(take(w.cm_path ? (size_t)groups * 4 : (size_t)rp.passes * sblk * kMaxRadix * 4));
     w.tickets = static_cast<uint32_t*>(take(16));
@@ -562,11 +614,11 @@ cudaError_t launch_project(const ParamsIn& P, const Batch& B, float4* rec, int4*
 
 cudaError_t launch_bin(const int4* rect, const int32_t* cnt, const float4* rec, const Batch& B, int64_t capacity,
                        const BinWs& ws, bool blk_sum_ready, uint32_t* keys, uint32_t* ids, int2* ranges,
-                       float4* rec_binned, int64_t* pair_off, int64_t* k_dev, int64_t* k_max, uint32_t* status,
-                       cudaStream_t s) {
+                       float4* rec_binned, uint32_t* emit, int64_t* pair_off, int64_t* k_dev, int64_t* k_max,
+                       uint32_t* status, cudaStream_t s) {
     if (ws.cm_path)
-        return launch_bin_cm(rect, cnt, rec, B, capacity, ws, blk_sum_ready, keys, ids, ranges, rec_binned, pair_off,
-                             k_dev, k_max, status, s);
+        return launch_bin_cm(rect, cnt, rec, B, capacity, ws, blk_sum_ready, keys, ids, ranges, rec_binned, emit,
+                             pair_off, k_dev, k_max, status, s);
     const RadixPlan rp = radix_plan(B.total_tiles);
     const int n = B.total_gauss;
     const int nblk = std::max(1, (n + kProjBlock - 1) / kProjBlock);
@@ -584,8 +636,8 @@ cudaError_t launch_bin(const int4* rect, const int32_t* cnt, const float4* rec, 
     uint32_t* va = (rp.passes & 1) ? ws.vals_tmp : ids;
     uint32_t* kb = (rp.passes & 1) ? keys : ws.keys_tmp;
     uint32_t* vb = (rp.passes & 1) ? ids : ws.vals_tmp;
-    cudaError_t e = launch_pdl(k_emit, dim3(nblk), dim3(kProjBlock), 0, s, rect, cnt, ws.blk_sum, B, capacity, ka, va,
-                               pair_off, k_dev, k_max, ws.hist, rp, status);
+    cudaError_t e = launch_pdl(k_emit, dim3(nblk), dim3(kProjBlock), 0, s, rect, cnt, ws.blk_sum, ws.blk_lb, B,
+                               capacity, ka, va, pair_off, k_dev, k_max, ws.hist, rp, status);
     if (e != cudaSuccess) return e;
     // the staging buffer and the static arrays exceed the default 48 KB window
     e = smem_optin(reinterpret_cast<const void*>(k_onesweep), kSortStageBytes);
@@ -601,8 +653,8 @@ cudaError_t launch_bin(const int4* rect, const int32_t* cnt, const float4* rec, 
         std::swap(va, vb);
     }
     const int rblk = std::max(1, std::min<int>(sm_count() * 8, (int)((capacity + 255) / 256)));
-    return launch_pdl(k_ranges, dim3(rblk), dim3(256), 0, s, keys, ids, k_dev, capacity, ranges, B.total_tiles, rec,
-                      rec_binned, n, status);
+    return launch_pdl(k_ranges, dim3(rblk), dim3(256), 0, s, keys, ids, k_dev, capacity, ranges, B, rec, rec_binned,
+                      rect, pair_off, emit, status);
 }
 
 }  // namespace gi

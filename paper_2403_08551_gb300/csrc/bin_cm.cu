@@ -329,8 +329,8 @@ __global__ void __launch_bounds__(kCmChunk) k_place(const int4* __restrict__ rec
                                                     const uint32_t* __restrict__ P,
                                                     const uint32_t* __restrict__ chunk_sum, int nchunks,
                                                     int64_t capacity, uint32_t* __restrict__ ids,
-                                                    float4* __restrict__ rec_binned, int64_t* __restrict__ pair_off,
-                                                    uint32_t* __restrict__ status) {
+                                                    float4* __restrict__ rec_binned, uint32_t* __restrict__ emit,
+                                                    int64_t* __restrict__ pair_off, uint32_t* __restrict__ status) {
     constexpr int NW = kCmChunk / 32;
     constexpr int kRowLoads = kCmMaxTiles / kCmChunk;
     extern __shared__ uint32_t s_dyn[];  // [NW][total_tiles] lane masks, then [total_tiles] P row
@@ -390,6 +390,7 @@ __global__ void __launch_bounds__(kCmChunk) k_place(const int4* __restrict__ rec
         for (int v = 0; v < warp; ++v) pos += __popc(s_m[v * Tn + t]);
         if ((int64_t)pos >= capacity) continue;  // dropped; the scan raised the capacity error
         ids[pos] = (uint32_t)(b * kCmChunk + w0 + l);
+        if (emit) emit[pos] = (uint32_t)(pre + cs.off[w0 + l] + j);
         if (rec_binned) {
             rec_binned[2 * (size_t)pos] = s_rec[w0 + l][0];
             rec_binned[2 * (size_t)pos + 1] = s_rec[w0 + l][1];
@@ -406,8 +407,8 @@ bool cm_applies(int64_t n, int total_tiles) {
 
 cudaError_t launch_bin_cm(const int4* rect, const int32_t* cnt, const float4* rec, const Batch& B, int64_t capacity,
                           const BinWs& ws, bool prepared, uint32_t* keys, uint32_t* ids, int2* ranges,
-                          float4* rec_binned, int64_t* pair_off, int64_t* k_dev, int64_t* k_max, uint32_t* status,
-                          cudaStream_t s) {
+                          float4* rec_binned, uint32_t* emit, int64_t* pair_off, int64_t* k_dev, int64_t* k_max,
+                          uint32_t* status, cudaStream_t s) {
     const int n = B.total_gauss;
     const int Tn = B.total_tiles;
     const int nchunks = std::max(1, (n + kCmChunk - 1) / kCmChunk);
@@ -425,7 +426,7 @@ cudaError_t launch_bin_cm(const int4* rect, const int32_t* cnt, const float4* re
     e = smem_optin(reinterpret_cast<const void*>(k_place), (kCmChunk / 32 + 1) * kCmMaxTiles * 4);
     if (e != cudaSuccess) return e;
     return launch_pdl(k_place, dim3(nchunks), dim3(kCmChunk), (size_t)(kCmChunk / 32 + 1) * Tn * 4, s, rect, cnt, rec,
-                      B, ws.cm, ws.chunk_sum, nchunks, capacity, ids, rec_binned, pair_off, status);
+                      B, ws.cm, ws.chunk_sum, nchunks, capacity, ids, rec_binned, emit, pair_off, status);
 }
 
 }  // namespace gi

@@ -38,9 +38,10 @@ struct gi_fit {
     int4* rect = nullptr;
     int32_t* cnt = nullptr;
     int64_t *pair_off = nullptr, *k_dev = nullptr, *k_max = nullptr;
-    uint32_t *keys = nullptr, *ids = nullptr, *done = nullptr;
+    uint32_t *keys = nullptr, *ids = nullptr, *emit = nullptr, *done = nullptr;
     int2* ranges = nullptr;
     double* loss = nullptr;
+    double* loss_tile = nullptr;  // [tiles] squared error per tile of the last step
     int32_t* step = nullptr;
     BinWs bws{};
 };
@@ -82,7 +83,7 @@ cudaError_t enqueue_forward(gi_fit* f, cudaStream_t s, bool train) {
     if (e == cudaSuccess) {
         NvtxRange r("gi:binning");
         e = launch_bin(f->rect, f->cnt, f->rec, f->B, f->capacity, f->bws, true, f->keys, f->ids, f->ranges,
-                       f->rec_binned, f->pair_off, f->k_dev, f->k_max, device_status(), s);
+                       f->rec_binned, f->emit, f->pair_off, f->k_dev, f->k_max, device_status(), s);
     }
     if (e == cudaSuccess && train) e = mark(f, 2, s);
     if (e == cudaSuccess) {
@@ -91,7 +92,8 @@ cudaError_t enqueue_forward(gi_fit* f, cudaStream_t s, bool train) {
                 ? launch_render_blend(f->rec_binned, f->ids, f->ranges, f->B, train ? f->target_src : nullptr, f->out,
                                       train ? f->dl_tiled : nullptr, train ? f->loss : nullptr, device_status(), s)
                 : launch_render(f->rec_binned, f->ranges, f->B, train ? f->target_src : nullptr, f->out, nullptr,
-                                train ? f->dl_tiled : nullptr, train ? f->loss : nullptr, device_status(), s);
+                                train ? f->dl_tiled : nullptr, nullptr, train ? f->loss_tile : nullptr,
+                                device_status(), s);
     }
     if (e == cudaSuccess && train) e = mark(f, 3, s);
     return e;
@@ -105,14 +107,15 @@ cudaError_t enqueue_step(gi_fit* f, cudaStream_t s) {
         e = f->B.opac.mode == 2
                 ? launch_backward_blend(f->rec_binned, f->ids, f->ranges, f->rect, f->pair_off, f->B, f->out,
                                         f->dl_tiled, f->capacity, f->partial, device_status(), s)
-                : launch_backward(f->rec_binned, f->keys, f->ids, f->rect, f->pair_off, f->dl_tiled, f->B, f->k_dev,
-                                  f->capacity, f->partial, device_status(), s);
+                : launch_backward(f->rec_binned, f->keys, f->emit, f->dl_tiled, f->B, f->k_dev, f->capacity,
+                                  f->partial, device_status(), s);
     }
     if (e == cudaSuccess) e = mark(f, 4, s);
     if (e == cudaSuccess) {
         NvtxRange r("gi:update");
         e = launch_reduce(f->partial, f->pair_off, f->cnt, f->capacity, (int32_t)f->N, params_aos(f->params),
-                          nullptr, nullptr, nullptr, nullptr, &f->adam, f->params, f->m, f->v, f->grads, f->B, s);
+                          nullptr, nullptr, nullptr, nullptr, &f->adam, f->params, f->m, f->v, f->grads, f->B, s,
+                          f->B.opac.mode == 2 ? nullptr : f->loss_tile, f->loss);
     }
     if (e == cudaSuccess) e = mark(f, 5, s);
     return e;
@@ -282,12 +285,14 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
         codec ? up256((size_t)d->codec_stages * d->codec_size * 24) : 0,  // 26 EMA total
         codec ? up256((size_t)N * 4) : 0,                                 // 27 quantiser codes
         codec ? up256((size_t)N * d->codec_stages) : 0,                   // 28 RVQ indices
-        codec ? up256((size_t)kCodecMaxVals * 8 * ((N + 127) / 128)) : 0,  // 29 per-block partials
+        codec ? up256((size_t)kCodecMaxVals * 8 * reduce_blocks(N)) : 0,  // 29 per-block partials
         codec ? up256((size_t)kCodecMaxVals * 8) + 256 : 0,               // 30 totals, ticket, out
         d->opacity_mode ? 7 * up256((size_t)N * 4) : 0,                   // 31 opacity state
         d->opacity_mode == 2 ? up256((size_t)f->capacity * 4) : 0,        // 32 per-pair opacity sums
         d->opacity_mode == 2 ? up256((size_t)P * 4) : 0,                  // 33 per-pixel walk lengths
         codec ? up256((size_t)N * 4) : 0,                                 // 34 FP16 positions
+        up256((size_t)f->capacity * 4),                                   // 35 emission index per sorted pair
+        up256((size_t)tiles * 8),                                         // 36 squared error per tile
     };
     size_t total = 0;
     for (size_t x : sz) total += x;
@@ -321,6 +326,8 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
     f->keys = reinterpret_cast<uint32_t*>(at(15));
     f->ids = reinterpret_cast<uint32_t*>(at(16));
     f->ranges = reinterpret_cast<int2*>(at(17));
+    f->emit = reinterpret_cast<uint32_t*>(at(35));
+    f->loss_tile = reinterpret_cast<double*>(at(36));
     f->loss = reinterpret_cast<double*>(at(18));
     f->step = reinterpret_cast<int32_t*>(at(19));
     f->done = reinterpret_cast<uint32_t*>(at(19) + 16);

@@ -63,6 +63,7 @@ struct BinWs {
     uint32_t* zero;
     int64_t zero_words;
     uint32_t* hist;       // [passes][kHistReplicas][kMaxRadix] (radix)
+    uint64_t* blk_lb;     // [ceil(n / kProjBlock)] published block prefixes of the key emission (radix)
     uint32_t* lookback;
     uint32_t* tickets;    // [4]
     size_t bytes;
@@ -75,23 +76,26 @@ BinWs bin_ws_layout(void* base, int64_t n, int64_t capacity, int total_tiles);
 cudaError_t launch_project(const ParamsIn& P, const Batch& B, float4* rec, int4* rect, int32_t* cnt,
                            int64_t* blk_sum, const ZeroJob& zj, cudaStream_t s, uint32_t* cm = nullptr,
                            uint32_t* chunk_sum = nullptr);
+// emit (nullable): [capacity] emission index of each sorted pair.
 cudaError_t launch_bin(const int4* rect, const int32_t* cnt, const float4* rec, const Batch& B,
                        int64_t capacity, const BinWs& ws, bool blk_sum_ready, uint32_t* keys,
-                       uint32_t* ids, int2* ranges, float4* rec_binned, int64_t* pair_off,
+                       uint32_t* ids, int2* ranges, float4* rec_binned, uint32_t* emit, int64_t* pair_off,
                        int64_t* k_dev, int64_t* k_max, uint32_t* status, cudaStream_t s);
 
 // prepared: the projection already wrote the count-matrix rows and cleared
 // the scratch (fit path); otherwise k_count does both.
 cudaError_t launch_bin_cm(const int4* rect, const int32_t* cnt, const float4* rec, const Batch& B,
                           int64_t capacity, const BinWs& ws, bool prepared, uint32_t* keys, uint32_t* ids,
-                          int2* ranges, float4* rec_binned, int64_t* pair_off, int64_t* k_dev, int64_t* k_max,
-                          uint32_t* status, cudaStream_t s);
+                          int2* ranges, float4* rec_binned, uint32_t* emit, int64_t* pair_off, int64_t* k_dev,
+                          int64_t* k_max, uint32_t* status, cudaStream_t s);
 
-// Forward render: out (HWC), optional loss sum (double per image), dL/dC in
-// HWC (dl_hwc) and/or planar per tile (dl_tiled: [tile][R,G,B][T*T] f32).
+// Forward render: out (HWC), dL/dC in HWC (dl_hwc) and/or planar per tile
+// (dl_tiled: [tile][R,G,B][T*T] f32) and the squared error: with loss_tile
+// each tile's sum (a fixed order inside the tile) at loss_tile[t], else
+// added to loss_sum (double per image).
 cudaError_t launch_render(const float4* rec_binned, const int2* ranges, const Batch& B,
                           const float* target, float* out, float* dl_hwc, float* dl_tiled,
-                          double* loss_sum, uint32_t* status, cudaStream_t s);
+                          double* loss_sum, double* loss_tile, uint32_t* status, cudaStream_t s);
 
 // Sorted alpha-blending render (Eq. 3-4) and its backward (blend.cu), tile 16
 // only; opacity, per-pixel walk lengths and the ninth per-pair sum live in
@@ -103,11 +107,14 @@ cudaError_t launch_backward_blend(const float4* rec_binned, const uint32_t* ids,
                                   const int64_t* pair_off, const Batch& B, const float* out, const float* dl_tiled,
                                   int64_t capacity, float4* partial, uint32_t* status, cudaStream_t s);
 
-// Backward: per-pair partial sums (8 floats per pair at its emission index).
-cudaError_t launch_backward(const float4* rec_binned, const uint32_t* keys, const uint32_t* ids,
-                            const int4* rect, const int64_t* pair_off, const float* dl_tiled,
-                            const Batch& B, const int64_t* k_dev, int64_t capacity, float4* partial,
-                            uint32_t* status, cudaStream_t s);
+// Backward: per-pair partial sums (8 floats per pair at its emission index
+// emit[k], written by the binning or by launch_emit_index).
+cudaError_t launch_backward(const float4* rec_binned, const uint32_t* keys, const uint32_t* emit,
+                            const float* dl_tiled, const Batch& B, const int64_t* k_dev, int64_t capacity,
+                            float4* partial, uint32_t* status, cudaStream_t s);
+cudaError_t launch_emit_index(const uint32_t* keys, const uint32_t* ids, const int4* rect, const int64_t* pair_off,
+                              const Batch& B, const int64_t* k_dev, int64_t capacity, uint32_t* emit,
+                              uint32_t* status, cudaStream_t s);
 cudaError_t launch_pack_dl(const float* dl_hwc, const Batch& B, float* dl_tiled, cudaStream_t s);
 
 struct AdamCfg {
@@ -127,11 +134,15 @@ struct AdamCfg {
 // Reduce partials per Gaussian, chain conic -> Cholesky; then either write
 // gradients (g_means/g_chol/g_color/g_conic, SoA, any may be null) or, when
 // adam != null, update AoS params/m/v in place (grads_aos optional).
+// Blocks of the per-Gaussian reduction for n Gaussians.
+int64_t reduce_blocks(int64_t n);
+// With loss_tile (fitting), the reduction also writes each image's squared
+// error loss[b] as the sum of its tiles' partials in tile order.
 cudaError_t launch_reduce(const float4* partial, const int64_t* pair_off, const int32_t* cnt,
                           int64_t capacity, int32_t n, const ParamsIn& P, float* g_means,
                           float* g_chol, float* g_color, float* g_conic, const AdamCfg* adam,
                           float* params, float* m, float* v, float* grads_aos, const Batch& B,
-                          cudaStream_t s);
+                          cudaStream_t s, const double* loss_tile = nullptr, double* loss = nullptr);
 
 struct GammaBeta {
     float v[6];  // gamma[3], beta[3]

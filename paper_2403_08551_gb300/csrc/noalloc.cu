@@ -103,7 +103,7 @@ extern "C" gi_status gi_bin_tiles_noalloc(const int32_t* rect, const int32_t* cn
     const BinWs w = bin_ws_layout(base, n, capacity, B.total_tiles);
     cudaError_t e = launch_bin(reinterpret_cast<const int4*>(rect), cnt, reinterpret_cast<const float4*>(rec), B,
                                capacity, w, false, keys, ids, reinterpret_cast<int2*>(ranges),
-                               reinterpret_cast<float4*>(rec_binned), pair_off, k_dev, nullptr, device_status(),
+                               reinterpret_cast<float4*>(rec_binned), nullptr, pair_off, k_dev, nullptr, device_status(),
                                reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return set_cuda_error(e, "gi_bin_tiles_noalloc");
     return GI_OK;

@@ -48,14 +48,15 @@ __global__ void __launch_bounds__(Cfg::kThreads) k_render(const float4* __restri
                                                           const int2* __restrict__ ranges, Batch B,
                                                           const float* __restrict__ target, float* __restrict__ out,
                                                           float* __restrict__ dl_hwc, float* __restrict__ dl_tiled,
-                                                          double* __restrict__ loss_sum, uint32_t* status) {
+                                                          double* __restrict__ loss_sum, double* __restrict__ loss_tile,
+                                                          uint32_t* status) {
     constexpr int T = Cfg::T, PX = Cfg::PX, SPLIT = Cfg::SPLIT, NT = Cfg::kThreads, NPIX = Cfg::kPix;
     extern __shared__ __align__(128) unsigned char smem[];
     float4* srec = reinterpret_cast<float4*>(smem);
     float* spart = reinterpret_cast<float*>(smem);  // reused after the last batch
     __shared__ __align__(8) uint64_t bar;
     __shared__ float s_red[32];
-    __shared__ float s_tgt[3 * NPIX];
+    __shared__ __align__(16) float s_tgt[3 * NPIX];
     pdl_wait();
 
     const int t = blockIdx.x;
@@ -177,42 +178,78 @@ __global__ void __launch_bounds__(Cfg::kThreads) k_render(const float4* __restri
     const float scale = 2.0f / (3.0f * (float)d.W * (float)d.H);
     float lsum = 0.f;
     if (target) cp_async_wait_all();  // each thread reads back only the pixels it copied
-    for (int p = threadIdx.x; p < NPIX; p += NT) {
-        float C[3];
+    __syncthreads();                  // (the copies of a quad below may come from several threads)
+    // Epilogue on quads of four neighbouring pixels of a row: 16-byte loads
+    // of the partial images, the target and the planar dL/dC, and the quad's
+    // twelve HWC floats as three 16-byte stores where they are aligned.
+    for (int q = threadIdx.x; q < NPIX / 4; q += NT) {
+        const int p = 4 * q;
+        float4 C[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            float s = 0.f;
+            float4 sacc = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int sp = 0; sp < SPLIT; ++sp) s += spart[(sp * 3 + c) * NPIX + p];
-            C[c] = s;
+            for (int sp = 0; sp < SPLIT; ++sp) {
+                const float4 u = *reinterpret_cast<const float4*>(&spart[(sp * 3 + c) * NPIX + p]);
+                sacc.x += u.x;
+                sacc.y += u.y;
+                sacc.z += u.z;
+                sacc.w += u.w;
+            }
+            C[c] = sacc;
         }
+        // HWC order of the quad: r0 g0 b0 r1 g1 b1 r2 g2 b2 r3 g3 b3
+        float hwc[12] = {C[0].x, C[1].x, C[2].x, C[0].y, C[1].y, C[2].y,
+                         C[0].z, C[1].z, C[2].z, C[0].w, C[1].w, C[2].w};
         const int x = x0 + p % T, y = y0 + p / T;
-        float dl[3] = {0.f, 0.f, 0.f};
-        if (x < d.W && y < d.H) {
-            const int64_t pix = d.pix_base + (int64_t)y * d.W + x;
+        const int nx = y < d.H ? max(0, min(4, d.W - x)) : 0;  // pixels of the quad inside the image
+        float dl[12];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) out[3 * pix + c] = C[c];
-            if (target) {
+        for (int i = 0; i < 12; ++i) dl[i] = 0.f;
+        if (target && nx > 0) {
+            float tg[12];
+            const float4* tq = reinterpret_cast<const float4*>(&s_tgt[3 * p]);
+            *reinterpret_cast<float4*>(&tg[0]) = tq[0];
+            *reinterpret_cast<float4*>(&tg[4]) = tq[1];
+            *reinterpret_cast<float4*>(&tg[8]) = tq[2];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const float r = C[c] - s_tgt[3 * p + c];
+            for (int i = 0; i < 12; ++i) {
+                if (i < 3 * nx) {
+                    const float r = hwc[i] - tg[i];
                     lsum = fmaf(r, r, lsum);
-                    dl[c] = r * scale;
-                }
-                if (dl_hwc) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) dl_hwc[3 * pix + c] = dl[c];
+                    dl[i] = r * scale;
                 }
             }
         }
+        if (nx > 0) {
+            const int64_t pix = d.pix_base + (int64_t)y * d.W + x;
+            float* o = out + 3 * pix;
+            if (nx == 4 && (reinterpret_cast<uintptr_t>(o) & 15) == 0) {
+                float4* o4 = reinterpret_cast<float4*>(o);
+                o4[0] = make_float4(hwc[0], hwc[1], hwc[2], hwc[3]);
+                o4[1] = make_float4(hwc[4], hwc[5], hwc[6], hwc[7]);
+                o4[2] = make_float4(hwc[8], hwc[9], hwc[10], hwc[11]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < 12; ++i)
+                    if (i < 3 * nx) o[i] = hwc[i];
+            }
+            if (target && dl_hwc) {
+                float* dh = dl_hwc + 3 * pix;
+#pragma unroll
+                for (int i = 0; i < 12; ++i)
+                    if (i < 3 * nx) dh[i] = dl[i];
+            }
+        }
         if (dl_tiled) {  // planar per tile: R, G, B planes of T*T floats
-            float* dt = dl_tiled + (int64_t)t * 3 * NPIX;
-            dt[p] = dl[0];
-            dt[NPIX + p] = dl[1];
-            dt[2 * NPIX + p] = dl[2];
+            float4* dt = reinterpret_cast<float4*>(dl_tiled + (int64_t)t * 3 * NPIX);
+            dt[q] = make_float4(dl[0], dl[3], dl[6], dl[9]);
+            dt[NPIX / 4 + q] = make_float4(dl[1], dl[4], dl[7], dl[10]);
+            dt[2 * NPIX / 4 + q] = make_float4(dl[2], dl[5], dl[8], dl[11]);
         }
     }
-    if (target && loss_sum) {
+    if (target && (loss_sum || loss_tile)) {
+        // fixed order: butterfly within warps, then the warps in order
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
         if (lane == 0) s_red[warp] = lsum;
@@ -220,57 +257,59 @@ __global__ void __launch_bounds__(Cfg::kThreads) k_render(const float4* __restri
         if (threadIdx.x == 0) {
             float s = 0.f;
             for (int w = 0; w < Cfg::kWarps; ++w) s += s_red[w];
-            atomicAdd(&loss_sum[bimg], (double)s);
+            if (loss_tile) loss_tile[t] = (double)s;
+            else atomicAdd(&loss_sum[bimg], (double)s);
         }
     }
 }
 
 template <class Cfg>
 cudaError_t launch_cfg(const float4* rec_binned, const int2* ranges, const Batch& B, const float* target,
-                       float* out, float* dl_hwc, float* dl_tiled, double* loss_sum, uint32_t* status,
-                       cudaStream_t s) {
+                       float* out, float* dl_hwc, float* dl_tiled, double* loss_sum, double* loss_tile,
+                       uint32_t* status, cudaStream_t s) {
     static_assert(Cfg::kSmem <= 96 * 1024, "dynamic shared memory of the render");
     if (B.total_tiles <= 0) return cudaSuccess;
     // the dynamic window plus the static part may exceed the default 48 KB
     const cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_render<Cfg>), Cfg::kSmem);
     if (e != cudaSuccess) return e;
     return launch_pdl(k_render<Cfg>, dim3(B.total_tiles), dim3(Cfg::kThreads), Cfg::kSmem, s, rec_binned, ranges, B,
-                      target, out, dl_hwc, dl_tiled, loss_sum, status);
+                      target, out, dl_hwc, dl_tiled, loss_sum, loss_tile, status);
 }
 
 }  // namespace
 
 cudaError_t launch_render(const float4* rec_binned, const int2* ranges, const Batch& B, const float* target,
-                          float* out, float* dl_hwc, float* dl_tiled, double* loss_sum, uint32_t* status,
-                          cudaStream_t s) {
+                          float* out, float* dl_hwc, float* dl_tiled, double* loss_sum, double* loss_tile,
+                          uint32_t* status, cudaStream_t s) {
     // split: lane groups that share one tile's list (each group covers all
     // of the tile's pixels); 0 picks the default for the tile edge. Tile 16
-    // uses two rows per lane (16 lanes per group), tiles 8 and 32 one.
+    // gives a lane a 4 x 4 block (four rows share each column's terms; 16
+    // lanes per group), tiles 8 and 32 a strip of one row.
     const int sp = B.split;
     switch (B.tile) {
         case 8:
             if (sp == 2)
                 return launch_cfg<RCfg<8, 2, 2, 1>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
-                                                    status, s);
+                                                    loss_tile, status, s);
             if (sp == 0 || sp == 4)
                 return launch_cfg<RCfg<8, 2, 4, 1>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
-                                                    status, s);
+                                                    loss_tile, status, s);
             return cudaErrorInvalidValue;
         case 16:
             if (sp == 4)
-                return launch_cfg<RCfg<16, 8, 4, 2>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
-                                                     status, s);
+                return launch_cfg<RCfg<16, 4, 4, 4>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
+                                                     loss_tile, status, s);
             if (sp == 0 || sp == 8)
-                return launch_cfg<RCfg<16, 8, 8, 2>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
-                                                     status, s);
+                return launch_cfg<RCfg<16, 4, 8, 4>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
+                                                     loss_tile, status, s);
             return cudaErrorInvalidValue;
         case 32:
             if (sp == 1)
                 return launch_cfg<RCfg<32, 8, 1, 1>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
-                                                     status, s);
+                                                     loss_tile, status, s);
             if (sp == 0 || sp == 2)
                 return launch_cfg<RCfg<32, 8, 2, 1>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
-                                                     status, s);
+                                                     loss_tile, status, s);
             return cudaErrorInvalidValue;
         default:
             return cudaErrorInvalidValue;

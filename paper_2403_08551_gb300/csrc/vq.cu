@@ -75,6 +75,86 @@ __global__ void __launch_bounds__(256) k_vq_decode(const uint16_t* __restrict__ 
     }
 }
 
+// Four consecutive Gaussians per thread when every array is 16-byte aligned
+// (the usual case): the FP16 positions of the four as one 16-byte load, each
+// index plane as one 4-byte load, codebook rows from shared memory as one
+// 16-byte load each (rows padded to four floats), and the outputs as whole
+// 16-byte stores (2 for the positions, 3 for each attribute). Same
+// arithmetic as k_vq_decode.
+__global__ void __launch_bounds__(256) k_vq_decode4(const uint2* __restrict__ means16, const uint8_t* __restrict__ idx,
+                                                    const float* __restrict__ cb, int n, int stages, int cbs,
+                                                    float4* __restrict__ means, float4* __restrict__ chol,
+                                                    float4* __restrict__ color, uint32_t* status) {
+    extern __shared__ float4 srow[];  // [2][stages][cbs] rows (x, y, z, 0)
+    const int nrow = 2 * stages * cbs;
+    for (int i = threadIdx.x; i < nrow; i += blockDim.x)
+        srow[i] = make_float4(cb[3 * i], cb[3 * i + 1], cb[3 * i + 2], 0.f);
+    __syncthreads();
+    const int nq = n >> 2;  // whole quads; the tail is left to k_vq_decode
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+        const uint4 h = reinterpret_cast<const uint4*>(means16)[q];  // 4 Gaussians x (x, y) binary16
+        float o[2][4][3];
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            if (stages <= 2) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) o[a][j][0] = o[a][j][1] = o[a][j][2] = 0.f;
+                for (int s = 0; s < stages; ++s) {
+                    const uint32_t w = reinterpret_cast<const uint32_t*>(idx + ((size_t)a * stages + s) * n)[q];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        int i = (w >> (8 * j)) & 0xff;
+                        if (i >= cbs) {  // index outside the codebook: skip the read
+                            flag_error(status, kErrBounds);
+                            i = 0;
+                        }
+                        const float4 r = srow[((size_t)a * stages + s) * cbs + i];
+                        o[a][j][0] = __fadd_rn(o[a][j][0], r.x);
+                        o[a][j][1] = __fadd_rn(o[a][j][1], r.y);
+                        o[a][j][2] = __fadd_rn(o[a][j][2], r.z);
+                    }
+                }
+            } else {
+                double acc[4][3] = {};
+                for (int s = 0; s < stages; ++s) {
+                    const uint32_t w = reinterpret_cast<const uint32_t*>(idx + ((size_t)a * stages + s) * n)[q];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        int i = (w >> (8 * j)) & 0xff;
+                        if (i >= cbs) {
+                            flag_error(status, kErrBounds);
+                            i = 0;
+                        }
+                        const float4 r = srow[((size_t)a * stages + s) * cbs + i];
+                        acc[j][0] += (double)r.x;
+                        acc[j][1] += (double)r.y;
+                        acc[j][2] += (double)r.z;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    for (int c = 0; c < 3; ++c) o[a][j][c] = (float)acc[j][c];
+            }
+        }
+        const uint32_t hw[4] = {h.x, h.y, h.z, h.w};
+        float mf[8];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            mf[2 * j] = __half2float(__ushort_as_half((unsigned short)(hw[j] & 0xffffu)));
+            mf[2 * j + 1] = __half2float(__ushort_as_half((unsigned short)(hw[j] >> 16)));
+        }
+        means[2 * (size_t)q] = make_float4(mf[0], mf[1], mf[2], mf[3]);
+        means[2 * (size_t)q + 1] = make_float4(mf[4], mf[5], mf[6], mf[7]);
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            float4* dst = (a == 0 ? chol : color) + 3 * (size_t)q;
+            dst[0] = make_float4(o[a][0][0], o[a][0][1], o[a][0][2], o[a][1][0]);
+            dst[1] = make_float4(o[a][1][1], o[a][1][2], o[a][2][0], o[a][2][1]);
+            dst[2] = make_float4(o[a][2][2], o[a][3][0], o[a][3][1], o[a][3][2]);
+        }
+    }
+}
+
 // The paper's codec (Sec. 3.3): FP16 positions, the b-bit Cholesky codes
 // reconstructed as l_bar_i = code_i gamma_i + beta_i (Eq. 9, the same two
 // roundings as the fit's quantiser), and the RVQ colour as the FP64 sum of
@@ -136,6 +216,18 @@ cudaError_t launch_vq_decode(const uint16_t* means16, const uint8_t* idx, const 
                              int32_t cb_size, float* means, float* chol, float* color, int32_t out_stride_aos,
                              cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
+    auto a16 = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; };
+    if (out_stride_aos == 0 && n % 4 == 0 && a16(means16) && (reinterpret_cast<uintptr_t>(idx) & 3) == 0 &&
+        a16(means) && a16(chol) && a16(color)) {
+        const size_t smem = (size_t)2 * stages * cb_size * sizeof(float4);
+        cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_vq_decode4), (int)smem);
+        if (e != cudaSuccess) return e;
+        const int blocks = std::max(1, std::min((n / 4 + 255) / 256, sm_count() * 8));
+        k_vq_decode4<<<blocks, 256, smem, s>>>(reinterpret_cast<const uint2*>(means16), idx, cb, n, stages, cb_size,
+                                               reinterpret_cast<float4*>(means), reinterpret_cast<float4*>(chol),
+                                               reinterpret_cast<float4*>(color), device_status());
+        return cudaGetLastError();
+    }
     const size_t smem = (size_t)2 * stages * cb_size * 3 * sizeof(float);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k_vq_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

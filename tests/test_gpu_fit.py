@@ -278,7 +278,7 @@ def test_batched_equals_single(gi, T, split):
         single.step(3)
         torch.cuda.synchronize()
         assert torch.equal(single.params, pb[off:off + n]), f"image {i}"
-        assert single.mse()[0] == pytest.approx(mse_b[i], rel=1e-6)
+        assert single.mse()[0] == mse_b[i]  # per-tile loss partials summed in tile order
         single.close()
         off += n
     batched.close()

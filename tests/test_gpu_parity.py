@@ -306,8 +306,8 @@ def test_autograd_function(gi):
     check_grads(c.grad, ref["grads"]["color"], "color", ab["color"])
 
 
-def test_vq_decode_bit_exact(gi):
-    n = 50000
+@pytest.mark.parametrize("n", [50000, 49999])  # four Gaussians per thread / one per thread
+def test_vq_decode_bit_exact(gi, n):
     cb = synth.codebooks(4000)
     means = synth.init_gaussians(n, 768, 512, 4000)[0]
     x = synth.init_gaussians(n, 768, 512, 4001)
