@@ -249,13 +249,27 @@ def batched_vs_plain(gi, torch, n_images, steps, stream):
     mse_p = [f.mse()[0] for f in plain]
     for f in plain:
         f.close()
+    # the same batched fit with the render fed from the device tile queue
+    # (descending list length, persistent blocks): identical results
+    fq = gi.Fit(tg, pr, tile=T, lr=LR, render_split=sp, tile_queue=True)
+    fq.step(2)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    fq.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    t_q = e0.elapsed_time(e1) / 1e3
+    same_q = fq.mse() == mse_b
+    fq.close()
     psnr = lambda e: 10 * math.log10(1.0 / e) if e > 0 else float("inf")  # noqa: E731
     d = [abs(psnr(a) - psnr(b)) for a, b in zip(mse_b, mse_p)]
     dpsnr = max(d)
     return {"images": n_images, "steps": steps, "sizes": "uniform over 256x256, 512x384, 768x512, 1024x768",
             "gaussians": int(sum(w.n for w in ws)), "tile": T, "render_split": sp,
             "autotune_ms_per_step": {f"{k[0]}/{k[1]}": v for k, v in tune["ms_per_step"].items()},
+            "render_schedule": "tile order (one block per tile)",
             "batched_image_steps_per_s": n_images * steps / t_b, "plain_image_steps_per_s": n_images * steps / t_p,
+            "tile_queue_image_steps_per_s": n_images * steps / t_q, "tile_queue_same_loss": same_q,
             "batched_images_fitted_per_s": n_images / t_b, "plain_images_fitted_per_s": n_images / t_p,
             "speedup": t_p / t_b, "max_abs_dpsnr_db": dpsnr, "mean_abs_dpsnr_db": sum(d) / len(d),
             "mean_psnr_db_batched": sum(psnr(a) for a in mse_b) / len(mse_b),
@@ -428,17 +442,23 @@ def large_image(gi, torch, stream, flush, T=16, reps=20):
     out = {}
     for name in ("c2_2040x1356_100k", "c2_2040x1356_200k"):
         w = synth.workload(name)
-        fit = gi.Fit([torch.from_numpy(w.target).cuda()], [torch.from_numpy(pack(w)).cuda()], tile=T, lr=LR)
-        fit.step(3)
-        render_ms = _time(torch, stream, fit.render, reps, flush)
-        step_ms = _time(torch, stream, lambda: fit.step(1), reps, flush)
+        tq = {}
+        for queue in (True, False):  # the tile-queue schedule first, then the default (kept below)
+            fit = gi.Fit([torch.from_numpy(w.target).cuda()], [torch.from_numpy(pack(w)).cuda()], tile=T, lr=LR,
+                         tile_queue=queue)
+            fit.step(3)
+            render_ms = _time(torch, stream, fit.render, reps, flush)
+            step_ms = _time(torch, stream, lambda: fit.step(1), reps, flush)
+            if queue:
+                tq = {"render_ms": render_ms, "fit_step_ms": step_ms}
+                fit.close()
         p = fit.params
         _, rect, cnt = gi.project(p[:, 0:2].contiguous(), p[:, 2:5].contiguous(), p[:, 5:8].contiguous(), w.W, w.H, T)
         bins = gi.bin_tiles(rect, cnt, None, w.W, w.H, T)
         ev_in, ev_all = evals_per_render(bins.ranges.cpu().numpy(), w.W, w.H, T)
         out[name] = {"render_fps": 1e3 / render_ms, "render_ms": render_ms, "fit_step_ms": step_ms,
                      "fit_iter_s": 1e3 / step_ms, "pairs": bins.K, "evals_per_render": ev_in,
-                     "fwd_bwd_evals_per_s": ev_all / (step_ms * 1e-3)}
+                     "fwd_bwd_evals_per_s": ev_all / (step_ms * 1e-3), "tile_queue": tq}
         fit.close()
     return out
 
@@ -675,6 +695,8 @@ def main():
             "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS,
             "traffic": (NCU_TRAFFIC_BYTES.get("k_backward" if dom == "backward" else "k_render")
                         if T == 16 else None), "traffic_unit": "bytes per launch (ncu dram read + write)",
+            "traffic_source": "constant from one ncu capture of the current kernel at this workload "
+                              "(profiles/k_backward_c1_768x512_70k.md); not measured in this run",
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop/FMA x 2070 MHz",
             "sfu_frac": (ev_all / (stage_ms[3 if dom == 'backward' else 2] * 1e-3))
             / (SMS * SFU_LANES * SM_MAX_MHZ * 1e6)}
@@ -685,6 +707,7 @@ def main():
            "config": {"workload": f"{WORKLOAD}: 768x512 RGB synthetic image, 70,000 Gaussians, tile {T}, "
                                   f"FP32 Adam (lr 1e-3 means, 1e-2 others)", "global_batch": world,
                       "parallelism": f"replica x{world} (independent images)",
+                      "render_schedule": "tile order (one block per tile)",
                       "l2": "flushed (256 MB write) before every timed step"},
            "render_fps": 1e3 / render_ms, "render_ms": render_ms,
            "render_fps_modes": {"graph": 1e3 / render_ms, "eager": 1e3 / render_eager_ms},

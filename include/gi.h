@@ -302,6 +302,11 @@ typedef struct {
           tile 16 only. The logits take the optimiser's step at lr_color. */
     int32_t opacity_mode;     /* 0 (merged c', the paper's form), 1 or 2; codec needs 0 */
     const float* opacity_logits; /* device [sum counts] initial logits (copied); NULL = 0 */
+    /* Render schedule (results are identical either way): 0 = one block per
+       tile in tile order; 1 = a queue of all tiles of the batch ordered by
+       descending list length (built on the device each step), served to one
+       wave of persistent render blocks. The alpha-blending form ignores it. */
+    int32_t tile_queue;
 } gi_fit_desc;
 
 /* Allocates the context and copies targets and params (the caller's buffers

@@ -70,7 +70,7 @@ class GIFitDesc(ctypes.Structure):
                 ("beta3", f32), ("lr_halve_every", i32), ("cov_mode", i32), ("codec_bits", i32),
                 ("codec_stages", i32), ("codec_size", i32), ("codebooks", P), ("lsq_gamma", f32 * 3),
                 ("lsq_beta", f32 * 3), ("ema_decay", f32), ("ema_eps", f32), ("opacity_mode", i32),
-                ("opacity_logits", P)]
+                ("opacity_logits", P), ("tile_queue", i32)]
 
 
 class GIError(RuntimeError):

@@ -304,6 +304,9 @@ class Fit:
                     the initial logits (default 0)
       render_split  lane groups per tile in the render (0 = chosen from the
                     first binning; see RENDER_SPLITS)
+      tile_queue    render from a device queue of tiles ordered by
+                    descending list length with persistent blocks (same
+                    results as the default one block per tile)
       use_graph     replay each step from a captured CUDA graph
       stage_events  record CUDA events between the stages (stage_times)
     Methods: step, render, images, mse, stage_times, set_target_source,
@@ -314,7 +317,8 @@ class Fit:
                  capacity_factor: float = 1.5, use_graph: bool = True, stage_events: bool = False,
                  render_split: int = 0, param_mode: str = "pixel", optimizer: str = "adam",
                  lr_halve_every: int = 0, cov: str = "cholesky", codec: Optional[dict] = None,
-                 opacity: str = "merged", opacity_logits: Optional[Sequence[torch.Tensor]] = None):
+                 opacity: str = "merged", opacity_logits: Optional[Sequence[torch.Tensor]] = None,
+                 tile_queue: bool = False):
         lib = L.load()
         assert len(targets) == len(params) and len(targets) >= 1
         self.shapes = [(int(t.shape[1]), int(t.shape[0])) for t in targets]
@@ -342,6 +346,8 @@ class Fit:
             raise ValueError(f"opacity must be one of {tuple(OPACITY_MODES)}")
         self.opacity_mode = opacity
         desc.opacity_mode = OPACITY_MODES[opacity]
+        desc.tile_queue = int(bool(tile_queue))
+        self.tile_queue = bool(tile_queue)
         if opacity != "merged" and opacity_logits is not None:
             lg = torch.cat([_dev(x, torch.float32, "opacity_logits").reshape(-1) for x in opacity_logits]).contiguous()
             assert lg.numel() == sum(self.counts)

@@ -42,6 +42,8 @@ struct gi_fit {
     int2* ranges = nullptr;
     double* loss = nullptr;
     double* loss_tile = nullptr;  // [tiles] squared error per tile of the last step
+    bool use_queue = false;
+    TileQueue queue{};
     int32_t* step = nullptr;
     BinWs bws{};
 };
@@ -93,7 +95,7 @@ cudaError_t enqueue_forward(gi_fit* f, cudaStream_t s, bool train) {
                                       train ? f->dl_tiled : nullptr, train ? f->loss : nullptr, device_status(), s)
                 : launch_render(f->rec_binned, f->ranges, f->B, train ? f->target_src : nullptr, f->out, nullptr,
                                 train ? f->dl_tiled : nullptr, nullptr, train ? f->loss_tile : nullptr,
-                                device_status(), s);
+                                device_status(), s, f->use_queue ? &f->queue : nullptr);
     }
     if (e == cudaSuccess && train) e = mark(f, 3, s);
     return e;
@@ -182,6 +184,7 @@ gi_status check_desc(const gi_fit_desc* d, const char* fn) {
         return set_error(GI_ERR_INVALID_ARG, "%s: bad param_mode, cov_mode, optimizer, beta3 or lr_halve_every", fn);
     if ((reinterpret_cast<uintptr_t>(d->params) & 15) != 0)
         return set_error(GI_ERR_INVALID_ARG, "%s: params must be 16-byte aligned", fn);
+    if (d->tile_queue != 0 && d->tile_queue != 1) return set_error(GI_ERR_INVALID_ARG, "%s: tile_queue must be 0 or 1", fn);
     const bool codec = d->codec_bits != 0;
     if (d->opacity_mode < 0 || d->opacity_mode > 2 || (d->opacity_mode == 2 && d->tile != 16) ||
         (d->opacity_mode != 0 && (codec || d->cov_mode != 0)))
@@ -293,6 +296,7 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
         codec ? up256((size_t)N * 4) : 0,                                 // 34 FP16 positions
         up256((size_t)f->capacity * 4),                                   // 35 emission index per sorted pair
         up256((size_t)tiles * 8),                                         // 36 squared error per tile
+        d->tile_queue ? up256((size_t)tiles * 4) + 256 : 0,               // 37 tile queue, head
     };
     size_t total = 0;
     for (size_t x : sz) total += x;
@@ -328,6 +332,11 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
     f->ranges = reinterpret_cast<int2*>(at(17));
     f->emit = reinterpret_cast<uint32_t*>(at(35));
     f->loss_tile = reinterpret_cast<double*>(at(36));
+    f->use_queue = d->tile_queue != 0;
+    if (f->use_queue) {
+        f->queue.order = reinterpret_cast<uint32_t*>(at(37));
+        f->queue.head = reinterpret_cast<uint32_t*>(at(37) + up256((size_t)tiles * 4));
+    }
     f->loss = reinterpret_cast<double*>(at(18));
     f->step = reinterpret_cast<int32_t*>(at(19));
     f->done = reinterpret_cast<uint32_t*>(at(19) + 16);

@@ -93,9 +93,17 @@ cudaError_t launch_bin_cm(const int4* rect, const int32_t* cnt, const float4* re
 // (dl_tiled: [tile][R,G,B][T*T] f32) and the squared error: with loss_tile
 // each tile's sum (a fixed order inside the tile) at loss_tile[t], else
 // added to loss_sum (double per image).
+// queue (nullable): render with persistent blocks that take tiles from a
+// queue ordered by descending list length (built by a one-block kernel
+// first); otherwise one block per tile in index order.
+struct TileQueue {
+    uint32_t* order;  // [tiles]
+    uint32_t* head;   // [1]
+};
 cudaError_t launch_render(const float4* rec_binned, const int2* ranges, const Batch& B,
                           const float* target, float* out, float* dl_hwc, float* dl_tiled,
-                          double* loss_sum, double* loss_tile, uint32_t* status, cudaStream_t s);
+                          double* loss_sum, double* loss_tile, uint32_t* status, cudaStream_t s,
+                          const TileQueue* queue = nullptr);
 
 // Sorted alpha-blending render (Eq. 3-4) and its backward (blend.cu), tile 16
 // only; opacity, per-pixel walk lengths and the ninth per-pair sum live in

@@ -17,6 +17,8 @@
 // (sigma = 1/2 |L^-1 d|^2, Sec. 3.1 and Eq. 5), and exp(-sigma) as exp2 on
 // the SFU (MUFU.EX2).
 #include <algorithm>
+#include <map>
+#include <mutex>
 
 #include "kernels.cuh"
 
@@ -43,23 +45,33 @@ struct RCfg {
     static_assert(T % ROWS == 0 && T % PX == 0, "strips must tile the tile");
 };
 
+// Shared memory of a render block: the staging buffer (reused for the
+// partial images), the staging mbarrier, warp sums and the tile's target.
 template <class Cfg>
-__global__ void __launch_bounds__(Cfg::kThreads) k_render(const float4* __restrict__ rec_binned,
-                                                          const int2* __restrict__ ranges, Batch B,
-                                                          const float* __restrict__ target, float* __restrict__ out,
-                                                          float* __restrict__ dl_hwc, float* __restrict__ dl_tiled,
-                                                          double* __restrict__ loss_sum, double* __restrict__ loss_tile,
-                                                          uint32_t* status) {
-    constexpr int T = Cfg::T, PX = Cfg::PX, SPLIT = Cfg::SPLIT, NT = Cfg::kThreads, NPIX = Cfg::kPix;
-    extern __shared__ __align__(128) unsigned char smem[];
-    float4* srec = reinterpret_cast<float4*>(smem);
-    float* spart = reinterpret_cast<float*>(smem);  // reused after the last batch
-    __shared__ __align__(8) uint64_t bar;
-    __shared__ float s_red[32];
-    __shared__ __align__(16) float s_tgt[3 * NPIX];
-    pdl_wait();
+struct RSmem {
+    float4* srec;  // dynamic: Cfg::kSmem bytes
+    uint64_t* bar;
+    float* s_red;  // [32]
+    float* s_tgt;  // [3 * Cfg::kPix], 16-byte aligned
+};
 
-    const int t = blockIdx.x;
+// Renders tile t (the block's threads together). `phase` is the staging
+// mbarrier's parity, carried from tile to tile by persistent blocks.
+template <class Cfg>
+__device__ __forceinline__ void render_tile(int t, uint32_t& phase, const RSmem<Cfg>& sm,
+                                            const float4* __restrict__ rec_binned, const int2* __restrict__ ranges,
+                                            const Batch& B, const float* __restrict__ target, float* __restrict__ out,
+                                            float* __restrict__ dl_hwc, float* __restrict__ dl_tiled,
+                                            double* __restrict__ loss_sum, double* __restrict__ loss_tile,
+                                            uint32_t* status) {
+    constexpr int T = Cfg::T, PX = Cfg::PX, SPLIT = Cfg::SPLIT, NT = Cfg::kThreads, NPIX = Cfg::kPix;
+    float4* srec = sm.srec;
+    float* spart = reinterpret_cast<float*>(sm.srec);  // reused after the last batch
+    uint64_t* bar = sm.bar;
+    float* s_red = sm.s_red;
+    float* s_tgt = sm.s_tgt;
+    __syncthreads();  // the previous tile's reads of the shared buffers are done
+
     const int bimg = image_of_tile(B, t);
     const ImgDesc d = img_desc(B, bimg);
     const int lt = t - d.tile_base;
@@ -101,24 +113,18 @@ __global__ void __launch_bounds__(Cfg::kThreads) k_render(const float4* __restri
 #pragma unroll
         for (int p = 0; p < NP2; ++p) accr[r][p] = accg[r][p] = accb[r][p] = make_float2(0.f, 0.f);
 
-    if (threadIdx.x == 0) {
-        mbar_init(&bar, 1);
-        fence_mbar_init();
-    }
-    __syncthreads();
-    uint32_t phase = 0;
     bool ok = true;
     for (int j0 = 0; j0 < L && ok; j0 += Cfg::kStage) {
         const int nb = min(Cfg::kStage, L - j0);
         if (threadIdx.x == 0) {
-            mbar_arrive_expect_tx(&bar, (uint32_t)nb * 32u);
-            bulk_g2s(srec, rec_binned + 2 * ((int64_t)rg.x + j0), (uint32_t)nb * 32u, &bar);
+            mbar_arrive_expect_tx(bar, (uint32_t)nb * 32u);
+            bulk_g2s(srec, rec_binned + 2 * ((int64_t)rg.x + j0), (uint32_t)nb * 32u, bar);
         }
-        bool arrived = mbar_wait(&bar, phase);
+        bool arrived = mbar_wait(bar, phase);
         if (!arrived) {
             // Give up on this tile after a second bounded wait for the copy.
             flag_error(status, kErrTimeout);
-            mbar_wait(&bar, phase);
+            mbar_wait(bar, phase);
         }
         ok = __syncthreads_and(arrived) != 0;  // block-uniform decision
         phase ^= 1u;
@@ -263,13 +269,149 @@ __global__ void __launch_bounds__(Cfg::kThreads) k_render(const float4* __restri
     }
 }
 
+// One block per tile, tiles in index order.
+template <class Cfg>
+__global__ void __launch_bounds__(Cfg::kThreads) k_render(const float4* __restrict__ rec_binned,
+                                                          const int2* __restrict__ ranges, Batch B,
+                                                          const float* __restrict__ target, float* __restrict__ out,
+                                                          float* __restrict__ dl_hwc, float* __restrict__ dl_tiled,
+                                                          double* __restrict__ loss_sum, double* __restrict__ loss_tile,
+                                                          uint32_t* status) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ float s_red[32];
+    __shared__ __align__(16) float s_tgt[3 * Cfg::kPix];
+    const RSmem<Cfg> sm{reinterpret_cast<float4*>(smem), &bar, s_red, s_tgt};
+    pdl_wait();
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    uint32_t phase = 0;
+    render_tile<Cfg>(blockIdx.x, phase, sm, rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum, loss_tile,
+                     status);
+}
+
+// Persistent blocks (one wave) pulling tiles from the queue: queue.order
+// holds the tiles by descending list length, queue.head counts the tiles
+// handed out (zero at launch). A block asks for its next tile as it starts
+// the current one, so the atomic's latency is hidden. Each tile's result is
+// the same whichever block renders it and when.
+template <class Cfg>
+__global__ void __launch_bounds__(Cfg::kThreads) k_render_queued(const float4* __restrict__ rec_binned,
+                                                                 const int2* __restrict__ ranges, Batch B,
+                                                                 const float* __restrict__ target,
+                                                                 float* __restrict__ out, float* __restrict__ dl_hwc,
+                                                                 float* __restrict__ dl_tiled,
+                                                                 double* __restrict__ loss_sum,
+                                                                 double* __restrict__ loss_tile, TileQueue queue,
+                                                                 uint32_t* status) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ float s_red[32];
+    __shared__ __align__(16) float s_tgt[3 * Cfg::kPix];
+    __shared__ uint32_t s_next;
+    const RSmem<Cfg> sm{reinterpret_cast<float4*>(smem), &bar, s_red, s_tgt};
+    pdl_wait();
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        s_next = atomicAdd(queue.head, 1u);
+    }
+    __syncthreads();
+    uint32_t phase = 0;
+    const uint32_t ntiles = (uint32_t)B.total_tiles;
+    uint32_t idx = s_next;
+    while (idx < ntiles) {
+        uint32_t nxt = 0;
+        if (threadIdx.x == 0) nxt = atomicAdd(queue.head, 1u);  // read back after the tile
+        const uint32_t t = queue.order[idx];
+        if (gi_in_bounds(t < ntiles, status))
+            render_tile<Cfg>((int)t, phase, sm, rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
+                             loss_tile, status);
+        __syncthreads();
+        if (threadIdx.x == 0) s_next = nxt;
+        __syncthreads();
+        idx = s_next;
+    }
+}
+
+// The tile queue: tiles ordered by descending list length (lengths above
+// kQueueBuckets - 1 share the first bucket; inside a bucket the order is
+// whatever the atomics give, which no result depends on), and the head
+// counter reset. One block.
+constexpr int kQueueBuckets = 4096;
+constexpr int kQueueThreads = 1024;
+
+__global__ void __launch_bounds__(kQueueThreads) k_tile_queue(const int2* __restrict__ ranges, int total_tiles,
+                                                              TileQueue queue) {
+    __shared__ uint32_t s_cnt[kQueueBuckets];
+    __shared__ uint32_t s_warp[32];
+    pdl_wait();
+    for (int i = threadIdx.x; i < kQueueBuckets; i += blockDim.x) s_cnt[i] = 0u;
+    __syncthreads();
+    auto bucket = [&](int t) {
+        const int2 rg = ranges[t];
+        const int L = max(0, rg.y - rg.x);
+        return kQueueBuckets - 1 - min(L, kQueueBuckets - 1);  // longest first
+    };
+    for (int t = threadIdx.x; t < total_tiles; t += blockDim.x) atomicAdd(&s_cnt[bucket(t)], 1u);
+    __syncthreads();
+    // exclusive scan of the bucket counts, four buckets per thread
+    constexpr int PER = kQueueBuckets / kQueueThreads;
+    uint32_t v[PER], sum = 0;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        v[i] = s_cnt[threadIdx.x * PER + i];
+        sum += v[i];
+    }
+    const uint32_t incl = block_incl_scan<uint32_t>(sum, s_warp);
+    uint32_t run = incl - sum;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        s_cnt[threadIdx.x * PER + i] = run;
+        run += v[i];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < total_tiles; t += blockDim.x) queue.order[atomicAdd(&s_cnt[bucket(t)], 1u)] = t;
+    if (threadIdx.x == 0) *queue.head = 0u;
+}
+
+template <class Cfg>
+int render_blocks_per_sm() {
+    static std::mutex mu;
+    static std::map<int, int> cached;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    std::lock_guard<std::mutex> lk(mu);
+    int& v = cached[dev];
+    if (v <= 0) {
+        int nb = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_render_queued<Cfg>, Cfg::kThreads, Cfg::kSmem) !=
+                cudaSuccess ||
+            nb <= 0)
+            nb = 1;
+        v = nb;
+    }
+    return v;
+}
+
 template <class Cfg>
 cudaError_t launch_cfg(const float4* rec_binned, const int2* ranges, const Batch& B, const float* target,
                        float* out, float* dl_hwc, float* dl_tiled, double* loss_sum, double* loss_tile,
-                       uint32_t* status, cudaStream_t s) {
+                       const TileQueue* queue, uint32_t* status, cudaStream_t s) {
     static_assert(Cfg::kSmem <= 96 * 1024, "dynamic shared memory of the render");
     if (B.total_tiles <= 0) return cudaSuccess;
     // the dynamic window plus the static part may exceed the default 48 KB
+    if (queue) {
+        cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_render_queued<Cfg>), Cfg::kSmem);
+        if (e != cudaSuccess) return e;
+        e = launch_pdl(k_tile_queue, dim3(1), dim3(kQueueThreads), 0, s, ranges, B.total_tiles, *queue);
+        if (e != cudaSuccess) return e;
+        const int blocks = std::max(1, std::min(B.total_tiles, sm_count() * render_blocks_per_sm<Cfg>()));
+        return launch_pdl(k_render_queued<Cfg>, dim3(blocks), dim3(Cfg::kThreads), Cfg::kSmem, s, rec_binned, ranges,
+                          B, target, out, dl_hwc, dl_tiled, loss_sum, loss_tile, *queue, status);
+    }
     const cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_render<Cfg>), Cfg::kSmem);
     if (e != cudaSuccess) return e;
     return launch_pdl(k_render<Cfg>, dim3(B.total_tiles), dim3(Cfg::kThreads), Cfg::kSmem, s, rec_binned, ranges, B,
@@ -280,7 +422,7 @@ cudaError_t launch_cfg(const float4* rec_binned, const int2* ranges, const Batch
 
 cudaError_t launch_render(const float4* rec_binned, const int2* ranges, const Batch& B, const float* target,
                           float* out, float* dl_hwc, float* dl_tiled, double* loss_sum, double* loss_tile,
-                          uint32_t* status, cudaStream_t s) {
+                          uint32_t* status, cudaStream_t s, const TileQueue* queue) {
     // split: lane groups that share one tile's list (each group covers all
     // of the tile's pixels); 0 picks the default for the tile edge. Tile 16
     // gives a lane a 4 x 4 block (four rows share each column's terms; 16
@@ -290,26 +432,26 @@ cudaError_t launch_render(const float4* rec_binned, const int2* ranges, const Ba
         case 8:
             if (sp == 2)
                 return launch_cfg<RCfg<8, 2, 2, 1>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
-                                                    loss_tile, status, s);
+                                                    loss_tile, queue, status, s);
             if (sp == 0 || sp == 4)
                 return launch_cfg<RCfg<8, 2, 4, 1>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
-                                                    loss_tile, status, s);
+                                                    loss_tile, queue, status, s);
             return cudaErrorInvalidValue;
         case 16:
             if (sp == 4)
                 return launch_cfg<RCfg<16, 4, 4, 4>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
-                                                     loss_tile, status, s);
+                                                     loss_tile, queue, status, s);
             if (sp == 0 || sp == 8)
                 return launch_cfg<RCfg<16, 4, 8, 4>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
-                                                     loss_tile, status, s);
+                                                     loss_tile, queue, status, s);
             return cudaErrorInvalidValue;
         case 32:
             if (sp == 1)
                 return launch_cfg<RCfg<32, 8, 1, 1>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
-                                                     loss_tile, status, s);
+                                                     loss_tile, queue, status, s);
             if (sp == 0 || sp == 2)
                 return launch_cfg<RCfg<32, 8, 2, 1>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
-                                                     loss_tile, status, s);
+                                                     loss_tile, queue, status, s);
             return cudaErrorInvalidValue;
         default:
             return cudaErrorInvalidValue;

@@ -284,6 +284,34 @@ def test_batched_equals_single(gi, T, split):
     batched.close()
 
 
+@pytest.mark.parametrize("T", [8, 16, 32])
+def test_tile_queue_equals_tile_order(gi, T):
+    """The render fed from the device queue of tiles ordered by descending
+    list length (persistent blocks) gives the same parameters, moments,
+    losses and images, bit for bit, as one block per tile in tile order, on
+    an uneven batch."""
+    shapes = [(200, 136, 1600), (96, 64, 700), (130, 77, 1100)]
+    targets, params = [], []
+    for i, (W, H, n) in enumerate(shapes):
+        targets.append(torch.from_numpy(synth.image(W, H, 50 + i, n_blobs=10)).cuda())
+        params.append(torch.from_numpy(pack(*synth.init_gaussians(n, W, H, 50 + i))).cuda())
+    a = gi.Fit(targets, params, tile=T, lr=LR, tile_queue=False)
+    b = gi.Fit(targets, params, tile=T, lr=LR, tile_queue=True)
+    a.step(4)
+    b.step(4)
+    torch.cuda.synchronize()
+    assert torch.equal(a.params, b.params) and torch.equal(a.adam_m, b.adam_m) and torch.equal(a.adam_v, b.adam_v)
+    assert a.mse() == b.mse()
+    a.render()
+    b.render()
+    torch.cuda.synchronize()
+    for x, y in zip(a.images(), b.images()):
+        assert torch.equal(x, y)
+    assert gi.device_errors(clear=True) == 0
+    a.close()
+    b.close()
+
+
 def test_fit_reduces_loss(gi):
     W, H, T, n = 128, 128, 16, 1500
     target = torch.from_numpy(synth.image(W, H, 23, n_blobs=20)).cuda()
