@@ -735,6 +735,9 @@ def main():
                                                         os.path.join(args.out, "fit_long_paper_psnr.jsonl"),
                                                         paper=True, keep=True)
         out["codec_finetune"] = codec_finetune(gi, torch, stream, T, fitted)
+        # the same fine-tuning with 2 x 256-entry colour codebooks: the 2 x 8
+        # codebook (64 colours for 70,000 Gaussians) is the PSNR ceiling above
+        out["codec_finetune_b256"] = codec_finetune(gi, torch, stream, T, fitted, size=256)
         out["fit_long_paper_recipe_rs"] = long_fit(gi, torch, stream, T, args.long_steps,
                                                    os.path.join(args.out, "fit_long_paper_rs_psnr.jsonl"),
                                                    paper=True, cov="rs")

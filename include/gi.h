@@ -286,7 +286,7 @@ typedef struct {
        (count and sum start at 1 and the initial entry). */
     int32_t codec_bits;       /* b in [1, 8]; 0 = off (the fields below are then ignored) */
     int32_t codec_stages;     /* M in [1, 4] */
-    int32_t codec_size;       /* B in [1, 16] */
+    int32_t codec_size;       /* B in [1, 256], M x B <= 512 */
     const float* codebooks;   /* device [M][B][3] initial colour codebooks (copied) */
     float lsq_gamma[3];       /* initial gamma_i (> 0) */
     float lsq_beta[3];        /* initial beta_i */

@@ -261,17 +261,21 @@ def codec_init(params, bits: int = 6, stages: int = 2, size: int = 8, iters: int
     r = p[:, 5:8].copy()
     gen = np.random.default_rng(seed)
     cbs = np.zeros((stages, size, 3))
+    def nearest(x, c):  # index of the nearest centroid, in row blocks (bounded memory)
+        return np.concatenate([np.argmin(((x[i:i + 8192, None, :] - c[None]) ** 2).sum(-1), axis=1)
+                               for i in range(0, x.shape[0], 8192)]) if x.shape[0] else np.zeros(0, np.int64)
+
     for m in range(stages):
         cent = r[gen.permutation(r.shape[0])[:size]].copy()
         if cent.shape[0] < size:
             cent = np.concatenate([cent, np.zeros((size - cent.shape[0], 3))])
         for _ in range(iters):
-            a = np.argmin(((r[:, None, :] - cent[None]) ** 2).sum(-1), axis=1)
+            a = nearest(r, cent)
             for j in range(size):
                 sel = a == j
                 if sel.any():
                     cent[j] = r[sel].mean(axis=0)
-        a = np.argmin(((r[:, None, :] - cent[None]) ** 2).sum(-1), axis=1)
+        a = nearest(r, cent)
         r = r - cent[a]
         cbs[m] = cent
     return {"bits": bits, "codebooks": torch.from_numpy(cbs.astype(np.float32)).to(params.device),

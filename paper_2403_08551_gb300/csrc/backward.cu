@@ -379,17 +379,18 @@ constexpr int kReduceRows = 128;  // pair rows a warp stages per chunk
 __device__ void codec_block_partials(const CodecCfg& Q, const float (&gb)[6], const int (&jj)[kCodecMaxStages],
                                      const float (&rr)[kCodecMaxStages][3], float commit) {
     constexpr int kWarps = kReduceThreads / 32;
-    __shared__ float s_cv[kWarps][kCodecMaxVals];
+    extern __shared__ float s_cv_dyn[];  // [kWarps][nv] (dynamic: sized by the codebooks)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nv = codec_nvals(Q);
+    float* s_cv = s_cv_dyn + warp * nv;
 #pragma unroll
     for (int v = 0; v < 6; ++v) {
         const float w = warp_sum(gb[v]);
-        if (lane == 0) s_cv[warp][v] = w;
+        if (lane == 0) s_cv[v] = w;
     }
     {
         const float w = warp_sum(commit);
-        if (lane == 0) s_cv[warp][nv - 1] = w;
+        if (lane == 0) s_cv[nv - 1] = w;
     }
 #pragma unroll
     for (int m = 0; m < kCodecMaxStages; ++m) {
@@ -404,7 +405,7 @@ __device__ void codec_block_partials(const CodecCfg& Q, const float (&gb)[6], co
                     c2 = warp_sum(mine ? rr[m][2] : 0.f);
                 }
                 if (lane == 0) {
-                    float* o = &s_cv[warp][6 + (m * Q.size + j) * 4];
+                    float* o = &s_cv[6 + (m * Q.size + j) * 4];
                     o[0] = (float)__popc(mask);
                     o[1] = c0;
                     o[2] = c1;
@@ -418,7 +419,7 @@ __device__ void codec_block_partials(const CodecCfg& Q, const float (&gb)[6], co
     for (int v = threadIdx.x; v < nv; v += blockDim.x) {
         double acc = 0.0;
 #pragma unroll
-        for (int w = 0; w < kWarps; ++w) acc += (double)s_cv[w][v];
+        for (int w = 0; w < kWarps; ++w) acc += (double)s_cv_dyn[w * nv + v];
         Q.part[(size_t)v * nb + blockIdx.x] = acc;
     }
 }
@@ -797,7 +798,7 @@ __global__ void __launch_bounds__(kCodecSumThreads) k_codec_update(CodecCfg Q, A
     const int t = threadIdx.x;
     // Everything the update reads is loaded in parallel first (a chain of
     // dependent global read-modify-writes would cost a round trip each).
-    constexpr int kMB = kCodecMaxStages * kCodecMaxSize;
+    constexpr int kMB = kCodecMaxEntries;
     __shared__ double s_tot[kCodecMaxVals];
     __shared__ double s_cnt[kMB];
     __shared__ double s_sum[kMB * 3];
@@ -948,11 +949,17 @@ cudaError_t launch_reduce(const float4* partial, const int64_t* pair_off, const 
         auto kern = codec ? k_reduce<true, true, 0>
                           : (B.opac.mode == 1 ? k_reduce<true, false, 1>
                                               : (B.opac.mode == 2 ? k_reduce<true, false, 2> : k_reduce<true, false, 0>));
-        cudaError_t e = launch_pdl(kern, dim3(blocks), dim3(kReduceThreads), 0, s, partial, pair_off, cnt, capacity, n,
+        // codec: the per-warp sums of every codebook entry in dynamic shared memory
+        const int nv = 6 + B.codec.stages * B.codec.size * 4 + 1;
+        const size_t dyn = codec ? (size_t)(kReduceThreads / 32) * nv * sizeof(float) : 0;
+        if (codec) {
+            cudaError_t e0 = smem_optin(reinterpret_cast<const void*>(kern), (int)dyn);
+            if (e0 != cudaSuccess) return e0;
+        }
+        cudaError_t e = launch_pdl(kern, dim3(blocks), dim3(kReduceThreads), dyn, s, partial, pair_off, cnt, capacity, n,
                                    P, (float*)nullptr, (float*)nullptr, (float*)nullptr, (float*)nullptr, *adam, params,
                                    m, v, grads_aos, B, loss_tile, loss);
         if (e != cudaSuccess || B.codec.bits == 0) return e;
-        const int nv = 6 + B.codec.stages * B.codec.size * 4 + 1;
         return launch_pdl(k_codec_update, dim3(nv), dim3(kCodecSumThreads), 0, s, B.codec, *adam, blocks, n);
     }
     AdamCfg none{};

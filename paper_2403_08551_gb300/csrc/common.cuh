@@ -54,8 +54,9 @@ struct ImgDesc {
 // Codec fine-tuning state (Sec. 3.3): the render sees FP16 positions, the
 // b-bit quantised Cholesky vector and the RVQ colour; bits == 0 is off.
 constexpr int kCodecMaxStages = 4;
-constexpr int kCodecMaxSize = 16;
-constexpr int kCodecMaxVals = 6 + kCodecMaxStages * kCodecMaxSize * 4 + 1;
+constexpr int kCodecMaxSize = 256;     // entries per codebook
+constexpr int kCodecMaxEntries = 512;  // entries over all stages
+constexpr int kCodecMaxVals = 6 + kCodecMaxEntries * 4 + 1;
 struct CodecCfg {
     int32_t bits;          // b (1..8); 0: no codec
     int32_t stages, size;  // M, B

@@ -192,9 +192,11 @@ gi_status check_desc(const gi_fit_desc* d, const char* fn) {
                                              "combines with the codec or the rotation-scaling form)", fn);
     if (codec) {
         if (d->codec_bits < 1 || d->codec_bits > 8 || d->codec_stages < 1 || d->codec_stages > kCodecMaxStages ||
-            d->codec_size < 1 || d->codec_size > kCodecMaxSize || !d->codebooks)
-            return set_error(GI_ERR_INVALID_ARG, "%s: codec needs bits in [1, 8], stages in [1, %d], size in [1, %d] "
-                                                 "and codebooks", fn, kCodecMaxStages, kCodecMaxSize);
+            d->codec_size < 1 || d->codec_size > kCodecMaxSize || d->codec_stages * d->codec_size > kCodecMaxEntries ||
+            !d->codebooks)
+            return set_error(GI_ERR_INVALID_ARG, "%s: codec needs bits in [1, 8], stages in [1, %d], size in [1, %d], "
+                                                 "stages x size <= %d and codebooks", fn, kCodecMaxStages,
+                             kCodecMaxSize, kCodecMaxEntries);
         if (d->n_images != 1 || d->cov_mode != 0)
             return set_error(GI_ERR_INVALID_ARG, "%s: codec fine-tuning takes one image in Cholesky form", fn);
         if (!(d->ema_decay >= 0.f && d->ema_decay < 1.f) || !(d->ema_eps >= 0.f) ||
@@ -288,7 +290,7 @@ gi_status gi_fit_create(const gi_fit_desc* d, gi_stream stream, gi_fit** out) {
         codec ? up256((size_t)d->codec_stages * d->codec_size * 24) : 0,  // 26 EMA total
         codec ? up256((size_t)N * 4) : 0,                                 // 27 quantiser codes
         codec ? up256((size_t)N * d->codec_stages) : 0,                   // 28 RVQ indices
-        codec ? up256((size_t)kCodecMaxVals * 8 * reduce_blocks(N)) : 0,  // 29 per-block partials
+        codec ? up256((size_t)(6 + 4 * d->codec_stages * d->codec_size + 1) * 8 * reduce_blocks(N)) : 0,  // 29 partials
         codec ? up256((size_t)kCodecMaxVals * 8) + 256 : 0,               // 30 totals, ticket, out
         d->opacity_mode ? 7 * up256((size_t)N * 4) : 0,                   // 31 opacity state
         d->opacity_mode == 2 ? up256((size_t)f->capacity * 4) : 0,        // 32 per-pair opacity sums
