@@ -10,7 +10,9 @@ opacity kept apart, accumulated summation), blend (sorted alpha-blending),
 paper (App. C.1 parameters with Adan), rs (rotation-scaling covariance with
 the paper's parameters and Adan), codec (b = 6, 2 x 8 RVQ fine-tuning),
 batch (64 synthetic images of uneven sizes, 5k-70k Gaussians each, fitted in
-one launch per stage at tile 16, render split 4)."""
+one launch per stage at tile 16, render split 4), vq (the codec's RVQ decode
+of 64 x 50,000 Gaussians, FP16 means and 2 x 256-entry codebooks, into
+preallocated outputs; `--steps` calls)."""
 import argparse
 import os
 import sys
@@ -20,7 +22,30 @@ import torch
 
 sys.path.insert(0, os.getcwd())
 
-MODES = ("merged", "separate", "blend", "paper", "rs", "codec", "batch")
+MODES = ("merged", "separate", "blend", "paper", "rs", "codec", "batch", "vq")
+
+
+def run_vq(gi, steps: int, warmup: int) -> int:
+    import synth
+    w = synth.workload("c4_768x512_50k")
+    nb = 64 * w.n
+    cb = torch.from_numpy(synth.codebooks(4000)).cuda()
+    idx = torch.from_numpy(synth.vq_indices(nb, 4001)).cuda()
+    m16 = torch.from_numpy(np.tile(w.means, (64, 1)).astype(np.float16)).cuda()
+    out = tuple(torch.empty((nb, k), dtype=torch.float32, device="cuda") for k in (2, 3, 3))
+    for _ in range(warmup):
+        gi.vq_decode(m16, idx, cb, out=out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        gi.vq_decode(m16, idx, cb, out=out)
+    e1.record()
+    e1.synchronize()
+    err = gi.device_errors(clear=True)
+    ms = e0.elapsed_time(e1) / max(1, steps)
+    print(f"vq: {ms:.4f} ms per decode of {nb} Gaussians ({nb * 40 / ms / 1e6:.0f} GB/s), device errors {err}")
+    return 1 if err else 0
 
 
 def make_fit(gi, mode: str):
@@ -61,6 +86,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=2)
     args = ap.parse_args()
     import paper_2403_08551_gb300 as gi
+    if args.mode == "vq":
+        return run_vq(gi, args.steps, args.warmup)
     fit = make_fit(gi, args.mode)
     fit.step(args.warmup)
     torch.cuda.synchronize()

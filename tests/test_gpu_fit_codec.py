@@ -49,11 +49,11 @@ def oracle_step(pg, gb, cb, target, T, paper):
     return c, r["loss"], g_ref, g_abs
 
 
-def run_codec(gi, target, p0, T, steps, paper, optimizer, lr, decay=0.9):
+def run_codec(gi, target, p0, T, steps, paper, optimizer, lr, decay=0.9, size=8, stages=2):
     H, W, _ = target.shape
     n = p0.shape[0]
     pt = torch.from_numpy(p0).cuda()
-    spec = gi.codec_init(pt, bits=BITS, stages=2, size=8, param_mode="paper" if paper else "pixel")
+    spec = gi.codec_init(pt, bits=BITS, stages=stages, size=size, param_mode="paper" if paper else "pixel")
     spec["ema_decay"] = decay
     fit = gi.Fit([torch.from_numpy(target).cuda()], [pt], tile=T, lr=lr, param_mode="paper" if paper else "pixel",
                  optimizer=optimizer, codec=spec)
@@ -123,6 +123,17 @@ def test_codec_pixel_adam_steps_track_oracle(gi, T):
     target = synth.image(W, H, 41, n_blobs=20)
     p0 = np.concatenate(synth.init_gaussians(n, W, H, 41), axis=1).astype(np.float32)
     run_codec(gi, target, p0, T, 5, paper=False, optimizer="adam", lr=(1e-3, 1e-2, 1e-2)).close()
+
+
+@pytest.mark.parametrize("stages,size", [(2, 256), (3, 64)])
+def test_codec_large_codebooks_track_oracle(gi, stages, size):
+    """Codebooks beyond the paper's 8 entries (the sums of every entry go
+    through the reduction's dynamic shared memory): 2 x 256 and 3 x 64."""
+    W, H, T, n = 128, 96, 16, 2000
+    target = synth.image(W, H, 45, n_blobs=20)
+    p0 = np.concatenate(synth.init_gaussians(n, W, H, 45), axis=1).astype(np.float32)
+    run_codec(gi, target, p0, T, 3, paper=False, optimizer="adam", lr=(1e-3, 1e-2, 1e-2), size=size,
+              stages=stages).close()
 
 
 def paper_params(means, chol, color, W, H):
