@@ -369,6 +369,7 @@ class Fit:
             desc.ema_eps = float(codec.get("ema_eps", CODEC_EMA_EPS))
             self.codec = {"bits": desc.codec_bits, "stages": M, "size": Bn, "ema_decay": desc.ema_decay,
                           "ema_eps": desc.ema_eps}
+        K = None
         if capacity is None or (render_split == 0 and tile == 16):
             # pairs of the first step, counted by the library with this
             # context's own formation (parameterisation, covariance form, codec)
@@ -376,6 +377,7 @@ class Fit:
             L.check(lib.gi_fit_count_pairs(ctypes.byref(desc), L.stream_handle(), ctypes.byref(K)),
                     "gi_fit_count_pairs")
             K = K.value
+        self.initial_pairs = K  # pairs of the first step, counted by the library (None when not needed)
         if capacity is None:
             capacity = max(4096, int(K * capacity_factor) + 1024)
         if render_split == 0 and tile == 16:
