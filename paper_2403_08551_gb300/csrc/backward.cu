@@ -375,9 +375,10 @@ constexpr int kReduceRows = 128;  // pair rows a warp stages per chunk
 // commitment term and, per RVQ stage and codebook entry, the count and the
 // residual sum of the Gaussians assigned to it. Warp sums by butterfly, then
 // the block's warps in order: a fixed summation order, so the totals do not
-// depend on scheduling. Row v of Q.part holds value v of every block.
+// depend on scheduling. Row v of Q.part holds value v of each of the nb
+// Gaussian blocks; this block is number blk of them.
 __device__ void codec_block_partials(const CodecCfg& Q, const float (&gb)[6], const int (&jj)[kCodecMaxStages],
-                                     const float (&rr)[kCodecMaxStages][3], float commit) {
+                                     const float (&rr)[kCodecMaxStages][3], float commit, int blk, int nb) {
     constexpr int kWarps = kReduceThreads / 32;
     extern __shared__ float s_cv_dyn[];  // [kWarps][nv] (dynamic: sized by the codebooks)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -415,12 +416,11 @@ __device__ void codec_block_partials(const CodecCfg& Q, const float (&gb)[6], co
         }
     }
     __syncthreads();
-    const int nb = gridDim.x;
     for (int v = threadIdx.x; v < nv; v += blockDim.x) {
         double acc = 0.0;
 #pragma unroll
         for (int w = 0; w < kWarps; ++w) acc += (double)s_cv_dyn[w * nv + v];
-        Q.part[(size_t)v * nb + blockIdx.x] = acc;
+        Q.part[(size_t)v * nb + blk] = acc;
     }
 }
 
@@ -443,11 +443,13 @@ __device__ __forceinline__ float opt_step(const AdamCfg& cfg, const float* s_bc,
 }
 
 // One thread per Gaussian. A warp's 32 Gaussians own one contiguous range of
-// pair rows, which the warp stages through shared memory in coalesced chunks;
+// pair rows, which the warp stages through shared memory in chunks of
+// coalesced cp.async copies, the next chunk in flight while one is summed;
 // per slot each Gaussian's rows are summed in emission order, Kahan-
 // compensated. Then the conic and Cholesky chain (App. A.2), the chains of
 // the parameterisation, covariance form, codec and opacity modes, and the
-// optimiser step.
+// optimiser step. With loss_tile, one block per image precedes the
+// Gaussians' blocks and sums that image's squared error.
 template <bool ADAM, bool CODEC = false, int OPAC = 0>
 __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restrict__ partial,
                                                 const int64_t* __restrict__ pair_off,
@@ -462,12 +464,24 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
     // 1/sqrt(1 - b3^t); [3] = learning-rate factor of the halving schedule.
     __shared__ float s_bc[4];
     pdl_wait();
-    if (ADAM && loss_tile) {
-        // each image's squared error: its tiles' partials in tile order, eight
-        // loads in flight per thread, combined in a fixed order, then a fixed
-        // reduction tree (reproducible run to run)
+    // The step counter's load is issued here and used after the partials are
+    // summed, so no load below waits for it.
+    int step_prev = 0;
+    if (ADAM && threadIdx.x == 0) step_prev = *cfg.step;
+    const int gblocks = (int)max(1, (n + kReduceThreads - 1) / kReduceThreads);
+    // With loss_tile the first B.nimg blocks sum the images' squared errors
+    // (first, so that they start in the first wave) and the Gaussian blocks
+    // follow.
+    const int lblocks = ADAM && loss_tile ? B.nimg : 0;
+    const int gb = (int)blockIdx.x - lblocks;  // this block's index among the Gaussian blocks
+    if (gb < 0) {
+        // image b = blockIdx.x: its tiles' partials in tile order, eight loads
+        // in flight per thread, combined in a fixed order, then a fixed
+        // reduction tree (reproducible run to run); then the block counts
+        // itself done like the others
         __shared__ double s_lw[32];
-        for (int b = blockIdx.x; b < B.nimg; b += gridDim.x) {
+        {
+            const int b = (int)blockIdx.x;
             const ImgDesc d = img_desc(B, b);
             const int nt = d.tw * d.th;
             double acc[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
@@ -482,29 +496,23 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
             tot = block_sum<double>(tot, s_lw);
             if (threadIdx.x == 0) loss[b] = tot;
         }
-    }
-    if (ADAM) {
-        if (threadIdx.x == 0) {
-            const int step = *cfg.step + 1;
-            s_step = step;
-            s_bc[0] = 1.f / (1.f - powf(cfg.beta1, (float)step));
-            if (cfg.optimizer == 1) {
-                s_bc[1] = 1.f / (1.f - powf(cfg.beta2, (float)step));
-                s_bc[2] = rsqrtf(1.f - powf(cfg.beta3, (float)step));
-            } else {
-                s_bc[1] = rsqrtf(1.f - powf(cfg.beta2, (float)step));
-                s_bc[2] = 0.f;
-            }
-            s_bc[3] = cfg.lr_halve_every > 0 ? ldexpf(1.f, -((step - 1) / cfg.lr_halve_every)) : 1.f;
-        }
         __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            if (atomicAdd(cfg.done, 1u) == gridDim.x - 1) {
+                *cfg.step = step_prev + 1;
+                *cfg.done = 0u;
+                __threadfence();
+            }
+        }
+        return;
     }
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = gb * blockDim.x + threadIdx.x;
     // Pair rows of the warp's 32 consecutive Gaussians are contiguous (emission
     // order): the warp streams them through shared memory with coalesced loads,
     // then each lane adds its own rows in emission order (Kahan), the same
     // order and arithmetic as reading them one by one.
-    __shared__ float4 s_rows[kReduceThreads / 32][kReduceRows][2];
+    __shared__ float4 s_rows[kReduceThreads / 32][2][kReduceRows][2];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int64_t p0 = 0, p1 = 0;
     int c = 0;
@@ -534,29 +542,32 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
         if (valid) {
             const int64_t R0 = __shfl_sync(0xffffffffu, p0, __ffs(valid) - 1);
             const int64_t R1 = __shfl_sync(0xffffffffu, p1, 31 - __clz(valid));
-            for (int64_t c0 = R0; c0 < R1; c0 += kReduceRows) {
+            auto issue = [&](int64_t c0, int buf) {
                 const int nr = (int)min((int64_t)kReduceRows, R1 - c0);
-                float4 x[kReduceRows / 32], y[kReduceRows / 32];
 #pragma unroll
                 for (int i = 0; i < kReduceRows / 32; ++i) {
                     const int r = lane + 32 * i;
                     if (r < nr) {
-                        x[i] = partial[2 * (c0 + r)];
-                        y[i] = partial[2 * (c0 + r) + 1];
+                        cp_async16(&s_rows[wid][buf][r][0], partial + 2 * (c0 + r));
+                        cp_async16(&s_rows[wid][buf][r][1], partial + 2 * (c0 + r) + 1);
                     }
                 }
-#pragma unroll
-                for (int i = 0; i < kReduceRows / 32; ++i) {
-                    const int r = lane + 32 * i;
-                    if (r < nr) {
-                        s_rows[wid][r][0] = x[i];
-                        s_rows[wid][r][1] = y[i];
-                    }
+                cp_async_commit();
+            };
+            issue(R0, 0);
+            int buf = 0;
+            for (int64_t c0 = R0; c0 < R1; c0 += kReduceRows, buf ^= 1) {
+                const int nr = (int)min((int64_t)kReduceRows, R1 - c0);
+                if (c0 + kReduceRows < R1) {
+                    issue(c0 + kReduceRows, buf ^ 1);
+                    cp_async_wait<1>();
+                } else {
+                    cp_async_wait<0>();
                 }
                 __syncwarp();
                 const int64_t q1 = min(p1, c0 + nr);
                 for (int64_t q = max(p0, c0); q < q1; ++q) {
-                    const float4 u = s_rows[wid][q - c0][0], w = s_rows[wid][q - c0][1];
+                    const float4 u = s_rows[wid][buf][q - c0][0], w = s_rows[wid][buf][q - c0][1];
                     kahan_add(a[0], ca[0], u.x); kahan_add(a[1], ca[1], u.y);
                     kahan_add(a[2], ca[2], u.z); kahan_add(a[3], ca[3], u.w);
                     kahan_add(a[4], ca[4], w.x); kahan_add(a[5], ca[5], w.y);
@@ -565,6 +576,22 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
                 __syncwarp();
             }
         }
+    }
+    if (ADAM) {
+        if (threadIdx.x == 0) {
+            const int step = step_prev + 1;
+            s_step = step;
+            s_bc[0] = 1.f / (1.f - powf(cfg.beta1, (float)step));
+            if (cfg.optimizer == 1) {
+                s_bc[1] = 1.f / (1.f - powf(cfg.beta2, (float)step));
+                s_bc[2] = rsqrtf(1.f - powf(cfg.beta3, (float)step));
+            } else {
+                s_bc[1] = rsqrtf(1.f - powf(cfg.beta2, (float)step));
+                s_bc[2] = 0.f;
+            }
+            s_bc[3] = cfg.lr_halve_every > 0 ? ldexpf(1.f, -((step - 1) / cfg.lr_halve_every)) : 1.f;
+        }
+        __syncthreads();
     }
     // codec fine-tuning: this Gaussian's dL/dgamma, dL/dbeta terms, RVQ indices,
     // stage residuals and commitment term (zero when off or g >= n)
@@ -751,7 +778,7 @@ __global__ void __launch_bounds__(kReduceThreads) k_reduce(const float4* __restr
             V4[0] = *reinterpret_cast<float4*>(vv); V4[1] = *reinterpret_cast<float4*>(vv + 4);
         }
     }
-    if (ADAM && CODEC) codec_block_partials(B.codec, cv_gb, cv_j, cv_r, cv_commit);
+    if (ADAM && CODEC) codec_block_partials(B.codec, cv_gb, cv_j, cv_r, cv_commit, gb, gblocks);
     if (ADAM) {
         // The last block to finish advances the step counter (every block has
         // read it by then).
@@ -956,7 +983,9 @@ cudaError_t launch_reduce(const float4* partial, const int64_t* pair_off, const 
             cudaError_t e0 = smem_optin(reinterpret_cast<const void*>(kern), (int)dyn);
             if (e0 != cudaSuccess) return e0;
         }
-        cudaError_t e = launch_pdl(kern, dim3(blocks), dim3(kReduceThreads), dyn, s, partial, pair_off, cnt, capacity, n,
+        // one more block per image sums its squared error when loss_tile is given
+        const int grid = blocks + (loss_tile ? B.nimg : 0);
+        cudaError_t e = launch_pdl(kern, dim3(grid), dim3(kReduceThreads), dyn, s, partial, pair_off, cnt, capacity, n,
                                    P, (float*)nullptr, (float*)nullptr, (float*)nullptr, (float*)nullptr, *adam, params,
                                    m, v, grads_aos, B, loss_tile, loss);
         if (e != cudaSuccess || B.codec.bits == 0) return e;

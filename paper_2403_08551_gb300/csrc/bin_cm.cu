@@ -11,7 +11,7 @@
 //   k_count   one block per two chunks: shared-memory tile histograms give
 //             the rows of M and the chunk pair totals; clears the binning
 //             scratch when asked.
-//   k_colscan one block per 8 tiles: column prefix sums over the chunks
+//   k_colscan one block per 16 tiles: column prefix sums over the chunks
 //             (P[b][t] = start[t] + sum_{b' < b} M[b'][t], written over M),
 //             chained scan of the column totals across tile groups (bounded
 //             look-back) -> start, ranges, K and the capacity check.
@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kCmChunk) k_count(const int4* __restrict__ rec
 }
 
 // ---------------------------------------------------------------------------
-// Column scan: block (in ticket order) -> tiles [8 blk, 8 blk + 8); thread
+// Column scan: block (in ticket order) -> tiles [16 blk, 16 blk + 16); thread
 // (tile ti, slab sl) -> chunk rows [sl rs, (sl + 1) rs) of tile ti, 32 slabs.
 // Pass 1 sums each slab's rows (kept in registers when they fit). Warp j
 // scans tile j's 32 slab partials, giving every slab's offset inside the

@@ -44,7 +44,7 @@ constexpr int kSortStageBytes = kSortTile * 8;          // keys + values staged 
 // Count-matrix binning (bin_cm.cu): chunks of kCmChunk Gaussians; used when
 // the batch has at most kCmMaxTiles tiles and chunks x tiles <= kCmMaxCells.
 constexpr int kCmChunk = 128;
-constexpr int kCmGroupTiles = 8;  // count-matrix column scan: tiles per block
+constexpr int kCmGroupTiles = 16;  // count-matrix column scan: tiles per block
 constexpr int kCmMaxTiles = 2048;
 constexpr int64_t kCmMaxCells = int64_t(1) << 20;
 bool cm_applies(int64_t n, int total_tiles);
