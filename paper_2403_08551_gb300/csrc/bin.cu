@@ -246,9 +246,10 @@ __global__ void __launch_bounds__(kProjBlock) k_blocksum(const int32_t* __restri
 }
 
 // ---------------------------------------------------------------------------
-// Key emission: pair_off = exclusive scan of cnt; Gaussian g writes
-// (tile, g) for its rect in row-major order at pair_off[g] + j. Also builds
-// the per-pass digit histograms of the radix sort.
+// Key emission: pair_off = exclusive scan of cnt; the pair j of Gaussian g
+// (its rect in row-major order) is (tile, g) at pair_off[g] + j, written by
+// the lanes of g's warp in turn. Also builds the per-pass digit histograms
+// of the radix sort.
 // ---------------------------------------------------------------------------
 // Exclusive prefix of block b's pair total over blocks 0 .. b - 1, by a
 // look-back that never waits: every block's total is already in blk_sum, and
@@ -313,16 +314,47 @@ __global__ void __launch_bounds__(kProjBlock) k_emit(const int4* __restrict__ re
         if (K > capacity) flag_error(status, kErrCapacity);
     }
     const uint32_t dmask = (1u << rp.dbits) - 1;
-    if (c > 0) {
-        const int4 r = rect[g];
-        const ImgDesc d = img_desc(B, image_of_gauss(B, g));
-        int64_t p = off;
-        for (int ty = r.y; ty < r.w; ++ty) {
-            for (int tx = r.x; tx < r.z; ++tx, ++p) {
-                if (p >= capacity) break;
-                const uint32_t key = (uint32_t)(d.tile_base + ty * d.tw + tx);
-                keys[p] = key;
-                vals[p] = (uint32_t)g;
+    // The warp's Gaussians own one contiguous run of pairs: lane l takes
+    // pairs l, l + 32, ... of the run (coalesced stores), finds the owning
+    // lane by a search over the warp's count prefix, and the tile from the
+    // pair's row-major index j inside the owner's rect.
+    {
+        const int lane = threadIdx.x & 31;
+        int4 r = make_int4(0, 0, 0, 0);
+        int tb = 0, tw = 0;
+        if (c > 0) {
+            r = rect[g];
+            const ImgDesc d = img_desc(B, image_of_gauss(B, g));
+            tb = d.tile_base;
+            tw = d.tw;
+        }
+        int incl = c;  // warp inclusive prefix of the counts
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        const int woff = incl - c, wtot = __shfl_sync(0xffffffffu, incl, 31);
+        const int64_t wbase = __shfl_sync(0xffffffffu, off, 0);  // the run starts at lane 0's offset
+        for (int q = lane; q - lane < wtot; q += 32) {  // warp-uniform trip count
+            int lo = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const int cand = lo + step;
+                const int ov = __shfl_sync(0xffffffffu, woff, cand & 31);
+                if (cand < 32 && ov <= q) lo = cand;
+            }
+            const int j = q - __shfl_sync(0xffffffffu, woff, lo);
+            const int rx = __shfl_sync(0xffffffffu, r.x, lo), ry = __shfl_sync(0xffffffffu, r.y, lo);
+            const int rz = __shfl_sync(0xffffffffu, r.z, lo);
+            const int otb = __shfl_sync(0xffffffffu, tb, lo), otw = __shfl_sync(0xffffffffu, tw, lo);
+            const int64_t pp = wbase + q;
+            if (q < wtot && pp < capacity) {
+                const int w = max(1, rz - rx);
+                const int row = j / w;
+                const uint32_t key = (uint32_t)(otb + (ry + row) * otw + rx + (j - row * w));
+                keys[pp] = key;
+                vals[pp] = (uint32_t)(blockIdx.x * kProjBlock + (threadIdx.x & ~31) + lo);
                 for (int ps = 0; ps < rp.passes; ++ps)
                     atomicAdd(&s_hist[ps * kMaxRadix + ((key >> (ps * rp.dbits)) & dmask)], 1u);
             }
