@@ -247,9 +247,9 @@ __global__ void __launch_bounds__(kProjBlock) k_blocksum(const int32_t* __restri
 
 // ---------------------------------------------------------------------------
 // Key emission: pair_off = exclusive scan of cnt; the pair j of Gaussian g
-// (its rect in row-major order) is (tile, g) at pair_off[g] + j, written by
-// the lanes of g's warp in turn. Also builds the per-pass digit histograms
-// of the radix sort.
+// (its rect in row-major order) is (tile, g) at p = pair_off[g] + j (with
+// owner: (tile, p) and owner[p] = g), written by the lanes of g's warp in
+// turn. Also builds the per-pass digit histograms of the radix sort.
 // ---------------------------------------------------------------------------
 // Exclusive prefix of block b's pair total over blocks 0 .. b - 1, by a
 // look-back that never waits: every block's total is already in blk_sum, and
@@ -286,6 +286,7 @@ __global__ void __launch_bounds__(kProjBlock) k_emit(const int4* __restrict__ re
                                                      const int64_t* __restrict__ blk_sum, uint64_t* __restrict__ blk_lb,
                                                      Batch B, int64_t capacity,
                                                      uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                                     uint32_t* __restrict__ owner,
                                                      int64_t* __restrict__ pair_off, int64_t* __restrict__ k_dev,
                                                      int64_t* __restrict__ k_max, uint32_t* __restrict__ hist,
                                                      RadixPlan rp, uint32_t* __restrict__ status) {
@@ -354,7 +355,13 @@ __global__ void __launch_bounds__(kProjBlock) k_emit(const int4* __restrict__ re
                 const int row = j / w;
                 const uint32_t key = (uint32_t)(otb + (ry + row) * otw + rx + (j - row * w));
                 keys[pp] = key;
-                vals[pp] = (uint32_t)(blockIdx.x * kProjBlock + (threadIdx.x & ~31) + lo);
+                const uint32_t og = (uint32_t)(blockIdx.x * kProjBlock + (threadIdx.x & ~31) + lo);
+                if (owner) {
+                    vals[pp] = (uint32_t)pp;  // the sort carries the emission index
+                    owner[pp] = og;
+                } else {
+                    vals[pp] = og;
+                }
                 for (int ps = 0; ps < rp.passes; ++ps)
                     atomicAdd(&s_hist[ps * kMaxRadix + ((key >> (ps * rp.dbits)) & dmask)], 1u);
             }
@@ -424,7 +431,18 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         const uint32_t dg = dig[r];
-        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+        // lanes with the same digit: one ballot per digit bit (and one for
+        // "has a digit"), each lane keeping the lanes that agree with it
+        uint32_t peers = __ballot_sync(0xffffffffu, dg < kMaxRadix);
+        if (dg >= kMaxRadix) peers = ~peers;
+#pragma unroll
+        for (int b = 0; b < kMaxDigitBits; ++b) {
+            if (b < dbits) {
+                const bool bit = (dg >> b) & 1u;
+                const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+                peers &= bit ? bal : ~bal;
+            }
+        }
         const int leader = __ffs(peers) - 1;
         uint32_t base = 0;
         if (lane == leader && dg < kMaxRadix) {
@@ -550,10 +568,14 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
 // ranges[t] = [first, last + 1) of key t in the sorted keys; with rec_binned,
 // also gathers the record of each sorted pair (rec_binned[k] = rec[ids[k]]),
 // one pair per thread so the random reads overlap across the whole grid; with
-// emit, the emission index of each sorted pair (pair_off[g] + its row-major
-// position in g's rectangle), which the backward stores its sums at.
-__global__ void k_ranges(const uint32_t* __restrict__ keys, const uint32_t* __restrict__ ids,
-                         const int64_t* __restrict__ k_dev, int64_t capacity, int2* __restrict__ ranges, Batch B,
+// emit, the emission index of each sorted pair, which the backward stores its
+// sums at. With owner, the sort carried each pair's emission index p: then
+// ids[k] = owner[p] and emit[k] = p. Without it (the sort carried the
+// Gaussian g), the emission index is pair_off[g] + the pair's row-major
+// position in g's rectangle.
+__global__ void k_ranges(const uint32_t* __restrict__ keys, uint32_t* __restrict__ ids,
+                         const uint32_t* __restrict__ owner, const int64_t* __restrict__ k_dev, int64_t capacity,
+                         int2* __restrict__ ranges, Batch B,
                          const float4* __restrict__ rec, float4* __restrict__ rec_binned,
                          const int4* __restrict__ rect, const int64_t* __restrict__ pair_off,
                          uint32_t* __restrict__ emit, uint32_t* __restrict__ status) {
@@ -562,7 +584,22 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, const uint32_t* __re
     const int total_tiles = B.total_tiles, n_gauss = B.total_gauss;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
         const uint32_t t = keys[k];
-        if (rec_binned || emit) {
+        if (owner) {
+            // the sorted values are emission indices: the Gaussian is their
+            // owner, and the value itself is the pair's emission index
+            const uint32_t p = ids[k];
+            const uint32_t g = p < (uint32_t)K ? owner[p] : 0xffffffffu;
+            if (g < (uint32_t)n_gauss && t < (uint32_t)total_tiles) {
+                ids[k] = g;
+                if (emit) emit[k] = p;
+                if (rec_binned) {
+                    rec_binned[2 * (size_t)k] = rec[2 * (size_t)g];
+                    rec_binned[2 * (size_t)k + 1] = rec[2 * (size_t)g + 1];
+                }
+            } else {
+                flag_error(status, kErrBounds);
+            }
+        } else if (rec_binned || emit) {
             const uint32_t g = ids[k];
             if (g < (uint32_t)n_gauss && t < (uint32_t)total_tiles) {
                 if (rec_binned) {
@@ -598,7 +635,7 @@ RadixPlan radix_plan(int total_tiles) {
     return {bits, passes, dbits};
 }
 
-BinWs bin_ws_layout(void* base, int64_t n, int64_t capacity, int total_tiles) {
+BinWs bin_ws_layout(void* base, int64_t n, int64_t capacity, int total_tiles, bool with_owner) {
     const RadixPlan rp = radix_plan(total_tiles);
     const int64_t nblk = std::max<int64_t>(1, (n + kProjBlock - 1) / kProjBlock);
     const int64_t sblk = std::max<int64_t>(1, (capacity + kSortTile - 1) / kSortTile);
@@ -621,6 +658,7 @@ BinWs bin_ws_layout(void* base, int64_t n, int64_t capacity, int total_tiles) {
     } else {
         w.keys_tmp = static_cast<uint32_t*>(take(cap * 4));
         w.vals_tmp = static_cast<uint32_t*>(take(cap * 4));
+        if (with_owner) w.owner = static_cast<uint32_t*>(take(cap * 4));
     }
     const size_t zero_off = off;
     if (!w.cm_path) {
@@ -669,7 +707,7 @@ cudaError_t launch_bin(const int4* rect, const int32_t* cnt, const float4* rec, 
     uint32_t* kb = (rp.passes & 1) ? keys : ws.keys_tmp;
     uint32_t* vb = (rp.passes & 1) ? ids : ws.vals_tmp;
     cudaError_t e = launch_pdl(k_emit, dim3(nblk), dim3(kProjBlock), 0, s, rect, cnt, ws.blk_sum, ws.blk_lb, B,
-                               capacity, ka, va, pair_off, k_dev, k_max, ws.hist, rp, status);
+                               capacity, ka, va, ws.owner, pair_off, k_dev, k_max, ws.hist, rp, status);
     if (e != cudaSuccess) return e;
     // the staging buffer and the static arrays exceed the default 48 KB window
     e = smem_optin(reinterpret_cast<const void*>(k_onesweep), kSortStageBytes);
@@ -685,8 +723,8 @@ cudaError_t launch_bin(const int4* rect, const int32_t* cnt, const float4* rec, 
         std::swap(va, vb);
     }
     const int rblk = std::max(1, std::min<int>(sm_count() * 8, (int)((capacity + 255) / 256)));
-    return launch_pdl(k_ranges, dim3(rblk), dim3(256), 0, s, keys, ids, k_dev, capacity, ranges, B, rec, rec_binned,
-                      rect, pair_off, emit, status);
+    return launch_pdl(k_ranges, dim3(rblk), dim3(256), 0, s, keys, ids, ws.owner, k_dev, capacity, ranges, B, rec,
+                      rec_binned, rect, pair_off, emit, status);
 }
 
 }  // namespace gi

@@ -58,6 +58,8 @@ struct BinWs {
     int64_t* blk_sum;     // [ceil(n / kProjBlock)]
     uint32_t* keys_tmp;   // [capacity]          (radix)
     uint32_t* vals_tmp;   // [capacity]          (radix)
+    uint32_t* owner;      // [capacity] Gaussian of each emission index (radix, optional: then the
+                          //            sort carries the emission index instead of the Gaussian)
     uint32_t* cm;         // [chunks][tiles]     (count matrix)
     uint32_t* chunk_sum;  // [chunks]            (count matrix)
     uint32_t* zero;
@@ -68,7 +70,7 @@ struct BinWs {
     uint32_t* tickets;    // [4]
     size_t bytes;
 };
-BinWs bin_ws_layout(void* base, int64_t n, int64_t capacity, int total_tiles);
+BinWs bin_ws_layout(void* base, int64_t n, int64_t capacity, int total_tiles, bool with_owner = true);
 
 // Launchers (stream-ordered, no host synchronisation).
 // With cm != null (count-matrix binning to follow) the projection also

@@ -93,14 +93,14 @@ extern "C" gi_status gi_bin_tiles_noalloc(const int32_t* rect, const int32_t* cn
     B.tile = img.tile;
     B.total_tiles = (int32_t)(tw * th);
     B.total_gauss = n;
-    const size_t need = bin_ws_layout(nullptr, n, capacity, B.total_tiles).bytes;
+    const size_t need = bin_ws_layout(nullptr, n, capacity, B.total_tiles, false).bytes;
     if (need > kNoAllocScratchBytes)
         return set_error(GI_ERR_INVALID_ARG, "gi_bin_tiles_noalloc: needs %zu scratch bytes, the fixed array has %zu",
                          need, kNoAllocScratchBytes);
     void* base = nullptr;
     gi_status st = scratch_address(&base);
     if (st != GI_OK) return st;
-    const BinWs w = bin_ws_layout(base, n, capacity, B.total_tiles);
+    const BinWs w = bin_ws_layout(base, n, capacity, B.total_tiles, false);
     cudaError_t e = launch_bin(reinterpret_cast<const int4*>(rect), cnt, reinterpret_cast<const float4*>(rec), B,
                                capacity, w, false, keys, ids, reinterpret_cast<int2*>(ranges),
                                reinterpret_cast<float4*>(rec_binned), nullptr, pair_off, k_dev, nullptr, device_status(),
