@@ -310,8 +310,8 @@ __global__ void __launch_bounds__(kBwdThreads, 2) k_backward(
         } while (pending);
         if (have) {
             if (p < (uint64_t)capacity) {
-                partial[2 * (size_t)p] = make_float4(o[0], o[1], o[2], o[3]);
-                partial[2 * (size_t)p + 1] = make_float4(o[4], o[5], o[6], o[7]);
+                st_global_v8(partial + 2 * (size_t)p, make_float4(o[0], o[1], o[2], o[3]),
+                             make_float4(o[4], o[5], o[6], o[7]));
             } else {
                 flag_error(status, kErrBounds);
             }

@@ -582,6 +582,8 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, uint32_t* __restrict
     pdl_wait();
     const int K = (int)min(*k_dev, capacity);
     const int total_tiles = B.total_tiles, n_gauss = B.total_gauss;
+    // records moved as one 32-byte access each when both arrays allow it
+    const bool v8 = ((reinterpret_cast<uintptr_t>(rec) | reinterpret_cast<uintptr_t>(rec_binned)) & 31) == 0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < K; k += gridDim.x * blockDim.x) {
         const uint32_t t = keys[k];
         if (owner) {
@@ -593,8 +595,14 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, uint32_t* __restrict
                 ids[k] = g;
                 if (emit) emit[k] = p;
                 if (rec_binned) {
-                    rec_binned[2 * (size_t)k] = rec[2 * (size_t)g];
-                    rec_binned[2 * (size_t)k + 1] = rec[2 * (size_t)g + 1];
+                    if (v8) {
+                        float4 a, b;
+                        ld_global_v8(rec + 2 * (size_t)g, a, b);
+                        st_global_v8(rec_binned + 2 * (size_t)k, a, b);
+                    } else {
+                        rec_binned[2 * (size_t)k] = rec[2 * (size_t)g];
+                        rec_binned[2 * (size_t)k + 1] = rec[2 * (size_t)g + 1];
+                    }
                 }
             } else {
                 flag_error(status, kErrBounds);
@@ -603,8 +611,14 @@ __global__ void k_ranges(const uint32_t* __restrict__ keys, uint32_t* __restrict
             const uint32_t g = ids[k];
             if (g < (uint32_t)n_gauss && t < (uint32_t)total_tiles) {
                 if (rec_binned) {
-                    rec_binned[2 * (size_t)k] = rec[2 * (size_t)g];
-                    rec_binned[2 * (size_t)k + 1] = rec[2 * (size_t)g + 1];
+                    if (v8) {
+                        float4 a, b;
+                        ld_global_v8(rec + 2 * (size_t)g, a, b);
+                        st_global_v8(rec_binned + 2 * (size_t)k, a, b);
+                    } else {
+                        rec_binned[2 * (size_t)k] = rec[2 * (size_t)g];
+                        rec_binned[2 * (size_t)k + 1] = rec[2 * (size_t)g + 1];
+                    }
                 }
                 if (emit) {
                     const ImgDesc d = img_desc(B, image_of_tile(B, (int)t));

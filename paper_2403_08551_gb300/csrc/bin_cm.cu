@@ -373,6 +373,7 @@ __global__ void __launch_bounds__(kCmChunk) k_place(const int4* __restrict__ rec
     if (g < B.total_gauss) pair_off[g] = pre + off;
     if (b == nchunks - 1 && threadIdx.x == blockDim.x - 1) pair_off[B.total_gauss] = pre + off + c;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, w0 = threadIdx.x & ~31;
+    const bool v8 = (reinterpret_cast<uintptr_t>(rec_binned) & 31) == 0;  // one 32-byte store per record
     const int woff = cs.off[threadIdx.x] - cs.off[w0];
     const int wtot = cs.off[w0 + 32] - cs.off[w0];
     for (int p = lane; p - lane < wtot; p += 32) {  // warp-uniform trip count
@@ -392,8 +393,12 @@ __global__ void __launch_bounds__(kCmChunk) k_place(const int4* __restrict__ rec
         ids[pos] = (uint32_t)(b * kCmChunk + w0 + l);
         if (emit) emit[pos] = (uint32_t)(pre + cs.off[w0 + l] + j);
         if (rec_binned) {
-            rec_binned[2 * (size_t)pos] = s_rec[w0 + l][0];
-            rec_binned[2 * (size_t)pos + 1] = s_rec[w0 + l][1];
+            if (v8) {
+                st_global_v8(rec_binned + 2 * (size_t)pos, s_rec[w0 + l][0], s_rec[w0 + l][1]);
+            } else {
+                rec_binned[2 * (size_t)pos] = s_rec[w0 + l][0];
+                rec_binned[2 * (size_t)pos + 1] = s_rec[w0 + l][1];
+            }
         }
     }
 }

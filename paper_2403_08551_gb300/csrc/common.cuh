@@ -363,6 +363,18 @@ __device__ Tv block_sum(Tv v, Tv* s_warp /*[32]*/) {
 
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// 32-byte global accesses (one 256-bit instruction); p 32-byte aligned.
+__device__ __forceinline__ void st_global_v8(void* p, float4 a, float4 b) {
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(a.x), "f"(a.y), "f"(a.z),
+                 "f"(a.w), "f"(b.x), "f"(b.y), "f"(b.z), "f"(b.w)
+                 : "memory");
+}
+__device__ __forceinline__ void ld_global_v8(const void* p, float4& a, float4& b) {
+    asm volatile("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+                 : "l"(p));
+}
+
 // Launch with the programmatic-stream-serialisation attribute (the launch
 // overlaps the previous kernel's tail; captured into graphs as a
 // programmatic dependency edge).

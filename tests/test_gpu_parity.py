@@ -157,6 +157,45 @@ def test_binning_paths_match_oracle(gi, W, H, n, T, seed, scale):
     np.testing.assert_array_equal(rb, rec.cpu().numpy()[ids_ref.astype(np.int64)])
 
 
+@pytest.mark.parametrize("W,H,n,T,seed,scale", BIN_CASES[:2])
+def test_binning_records_at_16_byte_offsets(gi, W, H, n, T, seed, scale):
+    """The ABI asks 16-byte alignment of rec and rec_binned; the binning
+    moves each 32-byte record in one access only when both are 32-byte
+    aligned. Records and binned records 16 bytes into their buffers (count
+    matrix and radix path) give the same binned records."""
+    import ctypes
+    from paper_2403_08551_gb300 import _lib as L
+    means, chol, color = synth.init_gaussians(n, W, H, seed)
+    chol = (chol * np.float32(scale)).astype(np.float32)
+    ids_ref, _, _ = oracle.bin_tiles(*oracle.rect_rule(means, chol, color, W, H, T), W, H, T)
+    rec, rect, cnt = gi.project(dev(means), dev(chol), dev(color), W, H, T)
+    K = ids_ref.shape[0]
+    cap = K + 64
+    img = L.GIImage(W, H, T)
+    lib = L.load()
+    sz = ctypes.c_size_t(0)
+    L.check(lib.gi_bin_workspace_size(n, img, cap, ctypes.byref(sz)), "gi_bin_workspace_size")
+    ws = torch.empty((sz.value + 256,), dtype=torch.uint8, device="cuda")
+    rec_off = torch.empty((n * 8 + 4,), dtype=torch.float32, device="cuda")
+    rec_off[4:] = rec.reshape(-1)
+    rb_off = torch.full((cap * 8 + 4,), float("nan"), dtype=torch.float32, device="cuda")
+    keys = torch.empty((cap,), dtype=torch.int32, device="cuda")
+    ids = torch.empty((cap,), dtype=torch.int32, device="cuda")
+    tw, th = oracle.tiles(W, H, T)
+    ranges = torch.empty((tw * th, 2), dtype=torch.int32, device="cuda")
+    pair_off = torch.empty((n + 1,), dtype=torch.int64, device="cuda")
+    k_dev = torch.empty((1,), dtype=torch.int64, device="cuda")
+    assert (rec_off[4:].data_ptr() % 32, rb_off[4:].data_ptr() % 32) == (16, 16)
+    L.check(lib.gi_bin_tiles(L.ptr(rect), L.ptr(cnt), rec_off[4:].data_ptr(), n, img, cap, L.ptr(ws), sz.value,
+                             L.ptr(keys), L.ptr(ids), L.ptr(ranges), rb_off[4:].data_ptr(), L.ptr(pair_off),
+                             L.ptr(k_dev), L.stream_handle()), "gi_bin_tiles")
+    torch.cuda.synchronize()
+    assert int(k_dev.item()) == K
+    rb = rb_off[4:].reshape(cap, 8)[:K].cpu().numpy()
+    np.testing.assert_array_equal(rb, rec.cpu().numpy()[ids_ref.astype(np.int64)])
+    assert gi.device_errors(clear=True) == 0
+
+
 @pytest.mark.parametrize("l3", [1e-2, 1e-3, 1e-4])
 def test_needle_gaussians(gi, l3):
     """Needle-shaped Gaussians (l1 = l2 = 8, l3 tiny: the short axis is about
