@@ -75,6 +75,56 @@ __global__ void __launch_bounds__(256) k_vq_decode(const uint16_t* __restrict__ 
     }
 }
 
+// One quad of the fast path below (at most two stages): the four
+// Gaussians' attributes from their index words w[attribute][stage] and the
+// padded codebook rows, then the 16-byte stores.
+__device__ __forceinline__ void vq_store_quad(int q, uint4 h, const uint32_t (&w)[2][2], const float4* srow,
+                                              int stages, int cbs, float4* __restrict__ means,
+                                              float4* __restrict__ chol, float4* __restrict__ color,
+                                              uint32_t* status) {
+    float o[2][4][3];
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) o[a][j][0] = o[a][j][1] = o[a][j][2] = 0.f;
+#pragma unroll
+        for (int st = 0; st < 2; ++st) {
+            if (st < stages) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    int i = (w[a][st] >> (8 * j)) & 0xff;
+                    if (i >= cbs) {  // index outside the codebook: skip the read
+                        flag_error(status, kErrBounds);
+                        i = 0;
+                    }
+                    const float4 r = srow[((size_t)a * stages + st) * cbs + i];
+                    o[a][j][0] = __fadd_rn(o[a][j][0], r.x);
+                    o[a][j][1] = __fadd_rn(o[a][j][1], r.y);
+                    o[a][j][2] = __fadd_rn(o[a][j][2], r.z);
+                }
+            }
+        }
+    }
+    const uint32_t hw[4] = {h.x, h.y, h.z, h.w};
+    float mf[8];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        mf[2 * j] = __half2float(__ushort_as_half((unsigned short)(hw[j] & 0xffffu)));
+        mf[2 * j + 1] = __half2float(__ushort_as_half((unsigned short)(hw[j] >> 16)));
+    }
+    means[2 * (size_t)q] = make_float4(mf[0], mf[1], mf[2], mf[3]);
+    means[2 * (size_t)q + 1] = make_float4(mf[4], mf[5], mf[6], mf[7]);
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        float4* dst = (a == 0 ? chol : color) + 3 * (size_t)q;
+        dst[0] = make_float4(o[a][0][0], o[a][0][1], o[a][0][2], o[a][1][0]);
+        dst[1] = make_float4(o[a][1][1], o[a][1][2], o[a][2][0], o[a][2][1]);
+        dst[2] = make_float4(o[a][2][2], o[a][3][0], o[a][3][1], o[a][3][2]);
+    }
+}
+
+constexpr int kVqQuads = 2;  // quads per thread and round of the fast path (4 measured slower)
+
 // Four consecutive Gaussians per thread when every array is 16-byte aligned
 // (the usual case): the FP16 positions of the four as one 16-byte load, each
 // index plane as one 4-byte load, codebook rows from shared memory as one
@@ -91,7 +141,35 @@ __global__ void __launch_bounds__(256) k_vq_decode4(const uint2* __restrict__ me
         srow[i] = make_float4(cb[3 * i], cb[3 * i + 1], cb[3 * i + 2], 0.f);
     __syncthreads();
     const int nq = n >> 2;  // whole quads; the tail is left to k_vq_decode
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+    const int stride = gridDim.x * blockDim.x;
+    if (stages <= 2) {
+        // kVqQuads quads per round, every load of the round issued before any
+        // quad is decoded (the loads' latency overlaps)
+        const uint4* M = reinterpret_cast<const uint4*>(means16);
+        for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += kVqQuads * stride) {
+            uint4 h[kVqQuads];
+            uint32_t w[kVqQuads][2][2];
+#pragma unroll
+            for (int u = 0; u < kVqQuads; ++u) {
+                const int qu = q + u * stride;
+                const bool in = qu < nq;
+                h[u] = in ? M[qu] : make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                for (int a = 0; a < 2; ++a)
+#pragma unroll
+                    for (int st = 0; st < 2; ++st) {
+                        const uint32_t* I = reinterpret_cast<const uint32_t*>(idx + ((size_t)a * stages + st) * n);
+                        w[u][a][st] = st < stages && in ? I[qu] : 0u;
+                    }
+            }
+#pragma unroll
+            for (int u = 0; u < kVqQuads; ++u)
+                if (q + u * stride < nq)
+                    vq_store_quad(q + u * stride, h[u], w[u], srow, stages, cbs, means, chol, color, status);
+        }
+        return;
+    }
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += stride) {
         const uint4 h = reinterpret_cast<const uint4*>(means16)[q];  // 4 Gaussians x (x, y) binary16
         float o[2][4][3];
 #pragma unroll
@@ -229,8 +307,8 @@ cudaError_t launch_vq_decode(const uint16_t* means16, const uint8_t* idx, const 
         return cudaGetLastError();
     }
     const size_t smem = (size_t)2 * stages * cb_size * 3 * sizeof(float);
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k_vq_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        cudaError_t e = smem_optin(reinterpret_cast<const void*>(k_vq_decode), (int)smem);
         if (e != cudaSuccess) return e;
     }
     int dev = 0, nsm = 0;
