@@ -15,9 +15,10 @@
 //             (P[b][t] = start[t] + sum_{b' < b} M[b'][t], written over M),
 //             chained scan of the column totals across tile groups (bounded
 //             look-back) -> start, ranges, K and the capacity check.
-//   k_place   one block per chunk: a per-warp lane mask of every tile in
-//             shared memory gives each pair's rank inside the chunk; the
-//             block scatters keys, ids and records and writes pair_off.
+//   k_place   one block per chunk (two warps per 32 Gaussians): a lane
+//             mask per 32 Gaussians of every tile in shared memory gives
+//             each pair's rank inside the chunk; the block scatters ids,
+//             records and emission indices and writes pair_off.
 #include <algorithm>
 
 #include "kernels.cuh"
@@ -79,12 +80,16 @@ __device__ __forceinline__ int pair_tile(const ChunkSmem& cs, int li, int j) {
 }
 
 // Loads this thread's Gaussian (count, rect, image) into the chunk layout
-// and returns its count (0 for a bad rect, with *bad set). Ends with the
-// block scan's barrier.
+// and returns its count (0 for a bad rect, with *bad set). Threads
+// kCmChunk and above of a larger block hold no Gaussian and only take part
+// in the scan. Ends with the block scan's barrier.
 __device__ __forceinline__ int load_chunk(const int4* __restrict__ rect, const int32_t* __restrict__ cnt,
                                           const Batch& B, int g, ChunkSmem& cs, int* s_warp, bool* bad) {
-    int c = g < B.total_gauss ? cnt[g] : 0;
-    int4 r = c > 0 ? rect[g] : make_int4(0, 0, 0, 0);
+    const bool holds = threadIdx.x < kCmChunk;
+    const bool in = holds && g < B.total_gauss;
+    int c = in ? cnt[g] : 0;
+    int4 r = in ? rect[g] : make_int4(0, 0, 0, 0);  // issued with the count: no dependent load
+    if (c <= 0) r = make_int4(0, 0, 0, 0);
     int2 im = make_int2(0, 0);
     *bad = false;
     if (c > 0) {
@@ -96,11 +101,13 @@ __device__ __forceinline__ int load_chunk(const int4* __restrict__ rect, const i
             c = 0;
         }
     }
-    cs.rect[threadIdx.x] = r;
-    cs.img[threadIdx.x] = im;
-    cs.inv_w[threadIdx.x] = c > 0 ? __frcp_rn((float)(r.z - r.x)) : 0.f;
+    if (holds) {
+        cs.rect[threadIdx.x] = r;
+        cs.img[threadIdx.x] = im;
+        cs.inv_w[threadIdx.x] = c > 0 ? __frcp_rn((float)(r.z - r.x)) : 0.f;
+    }
     const int incl = block_incl_scan<int>(c, s_warp);
-    cs.off[threadIdx.x + 1] = incl;
+    if (holds) cs.off[threadIdx.x + 1] = incl;
     if (threadIdx.x == 0) cs.off[0] = 0;
     __syncthreads();
     return c;
@@ -315,25 +322,29 @@ __global__ void __launch_bounds__(kCmScanThreads) k_colscan(uint32_t* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// Place: block = chunk b. Lane masks s_m[w][t] (bit l set when local
-// Gaussian 32 w + l covers tile t) are built with atomicOr, which is
-// order-independent; then pair (t, g), g = 128 b + 32 w + l, lands at
-//   P[b][t] + sum_{w' < w} popc(s_m[w'][t]) + popc(s_m[w][t] & bits below l),
+// Place: block = chunk b, two warps per lane group of 32 Gaussians (the
+// group's pairs alternate between them in rounds of 32). Lane masks
+// s_m[k][t] (bit l set when local Gaussian 32 k + l covers tile t) are built
+// with atomicOr, which is order-independent; then pair (t, g),
+// g = 128 b + 32 k + l, lands at
+//   P[b][t] + sum_{k' < k} popc(s_m[k'][t]) + popc(s_m[k][t] & bits below l),
 // i.e. ascending g inside the tile; the block writes ids and records there
 // (the keys come from the column scan). The chunk's row of P and its records
-// are staged in shared memory. pair_off = exclusive scan of cnt in emission order, the
-// chunk base from the chunk totals.
+// are staged in shared memory. pair_off = exclusive scan of cnt in emission
+// order, the chunk base from the chunk totals.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(kCmChunk) k_place(const int4* __restrict__ rect, const int32_t* __restrict__ cnt,
-                                                    const float4* __restrict__ rec, Batch B,
-                                                    const uint32_t* __restrict__ P,
-                                                    const uint32_t* __restrict__ chunk_sum, int nchunks,
-                                                    int64_t capacity, uint32_t* __restrict__ ids,
-                                                    float4* __restrict__ rec_binned, uint32_t* __restrict__ emit,
-                                                    int64_t* __restrict__ pair_off, uint32_t* __restrict__ status) {
-    constexpr int NW = kCmChunk / 32;
-    constexpr int kRowLoads = kCmMaxTiles / kCmChunk;
-    extern __shared__ uint32_t s_dyn[];  // [NW][total_tiles] lane masks, then [total_tiles] P row
+constexpr int kPlaceThreads = 2 * kCmChunk;
+
+__global__ void __launch_bounds__(kPlaceThreads) k_place(const int4* __restrict__ rect, const int32_t* __restrict__ cnt,
+                                                         const float4* __restrict__ rec, Batch B,
+                                                         const uint32_t* __restrict__ P,
+                                                         const uint32_t* __restrict__ chunk_sum, int nchunks,
+                                                         int64_t capacity, uint32_t* __restrict__ ids,
+                                                         float4* __restrict__ rec_binned, uint32_t* __restrict__ emit,
+                                                         int64_t* __restrict__ pair_off, uint32_t* __restrict__ status) {
+    constexpr int NG = kCmChunk / 32;  // lane groups
+    constexpr int kRowLoads = (kCmMaxTiles + kPlaceThreads - 1) / kPlaceThreads;
+    extern __shared__ uint32_t s_dyn[];  // [NG][total_tiles] lane masks, then [total_tiles] P row
     __shared__ ChunkSmem cs;
     __shared__ float4 s_rec[kCmChunk][2];
     __shared__ int s_warp[32];
@@ -341,54 +352,58 @@ __global__ void __launch_bounds__(kCmChunk) k_place(const int4* __restrict__ rec
     pdl_wait();
     const int Tn = B.total_tiles;
     uint32_t* s_m = s_dyn;
-    uint32_t* s_p = s_dyn + NW * Tn;
+    uint32_t* s_p = s_dyn + NG * Tn;
     const int b = blockIdx.x;
+    const bool holds = threadIdx.x < kCmChunk;  // threads holding a Gaussian of the chunk
     const int g = b * kCmChunk + threadIdx.x;
     // Independent loads first: the chunk's row of P, the chunk totals below
     // b and this Gaussian's record.
     const uint32_t* prow = P + (size_t)b * Tn;
 #pragma unroll
     for (int i = 0; i < kRowLoads; ++i) {
-        const int idx = threadIdx.x + i * kCmChunk;
+        const int idx = threadIdx.x + i * kPlaceThreads;
         if (idx < Tn) s_p[idx] = prow[idx];
     }
     int64_t pre = 0;
-    for (int i = threadIdx.x; i < b; i += 8 * kCmChunk) {  // eight predicated loads in flight per round
+    for (int i = threadIdx.x; i < b; i += 8 * kPlaceThreads) {  // eight predicated loads in flight per round
         uint32_t u[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) u[q] = i + q * kCmChunk < b ? chunk_sum[i + q * kCmChunk] : 0u;
+        for (int q = 0; q < 8; ++q) u[q] = i + q * kPlaceThreads < b ? chunk_sum[i + q * kPlaceThreads] : 0u;
 #pragma unroll
         for (int q = 0; q < 8; ++q) pre += u[q];
     }
-    if (rec_binned && g < B.total_gauss) {
+    if (rec_binned && holds && g < B.total_gauss) {
         s_rec[threadIdx.x][0] = rec[2 * (size_t)g];
         s_rec[threadIdx.x][1] = rec[2 * (size_t)g + 1];
     }
-    for (int i = threadIdx.x; i < NW * Tn; i += blockDim.x) s_m[i] = 0u;
+    for (int i = threadIdx.x; i < NG * Tn; i += kPlaceThreads) s_m[i] = 0u;
     bool bad;
     const int c = load_chunk(rect, cnt, B, g, cs, s_warp, &bad);
     if (bad) flag_error(status, kErrBounds);
     pre = block_sum<int64_t>(pre, s_warp64);
-    const int off = cs.off[threadIdx.x];
-    if (g < B.total_gauss) pair_off[g] = pre + off;
-    if (b == nchunks - 1 && threadIdx.x == blockDim.x - 1) pair_off[B.total_gauss] = pre + off + c;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, w0 = threadIdx.x & ~31;
+    if (holds) {
+        const int off = cs.off[threadIdx.x];
+        if (g < B.total_gauss) pair_off[g] = pre + off;
+        if (b == nchunks - 1 && threadIdx.x == kCmChunk - 1) pair_off[B.total_gauss] = pre + off + c;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = warp >> 1, p0 = 32 * (warp & 1), w0 = 32 * grp;
     const bool v8 = (reinterpret_cast<uintptr_t>(rec_binned) & 31) == 0;  // one 32-byte store per record
-    const int woff = cs.off[threadIdx.x] - cs.off[w0];
+    const int woff = cs.off[w0 + lane] - cs.off[w0];
     const int wtot = cs.off[w0 + 32] - cs.off[w0];
-    for (int p = lane; p - lane < wtot; p += 32) {  // warp-uniform trip count
+    for (int p = p0 + lane; p - lane < wtot; p += 64) {  // warp-uniform trip count
         const int l = warp_owner(woff, p);
         const int j = p - __shfl_sync(0xffffffffu, woff, l);
-        if (p < wtot) atomicOr(&s_m[warp * Tn + pair_tile(cs, w0 + l, j)], 1u << l);
+        if (p < wtot) atomicOr(&s_m[grp * Tn + pair_tile(cs, w0 + l, j)], 1u << l);
     }
     __syncthreads();
-    for (int p = lane; p - lane < wtot; p += 32) {
+    for (int p = p0 + lane; p - lane < wtot; p += 64) {
         const int l = warp_owner(woff, p);
         const int j = p - __shfl_sync(0xffffffffu, woff, l);
         if (p >= wtot) continue;
         const int t = pair_tile(cs, w0 + l, j);
-        uint32_t pos = s_p[t] + __popc(s_m[warp * Tn + t] & ((1u << l) - 1u));
-        for (int v = 0; v < warp; ++v) pos += __popc(s_m[v * Tn + t]);
+        uint32_t pos = s_p[t] + __popc(s_m[grp * Tn + t] & ((1u << l) - 1u));
+        for (int v = 0; v < grp; ++v) pos += __popc(s_m[v * Tn + t]);
         if ((int64_t)pos >= capacity) continue;  // dropped; the scan raised the capacity error
         ids[pos] = (uint32_t)(b * kCmChunk + w0 + l);
         if (emit) emit[pos] = (uint32_t)(pre + cs.off[w0 + l] + j);
@@ -430,7 +445,7 @@ cudaError_t launch_bin_cm(const int4* rect, const int32_t* cnt, const float4* re
     // up to 40 KB dynamic + the static layout: above the default 48 KB window
     e = smem_optin(reinterpret_cast<const void*>(k_place), (kCmChunk / 32 + 1) * kCmMaxTiles * 4);
     if (e != cudaSuccess) return e;
-    return launch_pdl(k_place, dim3(nchunks), dim3(kCmChunk), (size_t)(kCmChunk / 32 + 1) * Tn * 4, s, rect, cnt, rec,
+    return launch_pdl(k_place, dim3(nchunks), dim3(kPlaceThreads), (size_t)(kCmChunk / 32 + 1) * Tn * 4, s, rect, cnt, rec,
                       B, ws.cm, ws.chunk_sum, nchunks, capacity, ids, rec_binned, emit, pair_off, status);
 }
 
