@@ -654,7 +654,6 @@ BinWs bin_ws_layout(void* base, int64_t n, int64_t capacity, int total_tiles, bo
     const int64_t nblk = std::max<int64_t>(1, (n + kProjBlock - 1) / kProjBlock);
     const int64_t sblk = std::max<int64_t>(1, (capacity + kSortTile - 1) / kSortTile);
     const int64_t nchunks = std::max<int64_t>(1, (n + kCmChunk - 1) / kCmChunk);
-    const int64_t groups = std::max<int64_t>(1, (total_tiles + kCmGroupTiles - 1) / kCmGroupTiles);
     const int64_t cap = std::max<int64_t>(1, capacity);
     char* b = static_cast<char*>(base);
     size_t off = 0;
@@ -669,6 +668,7 @@ BinWs bin_ws_layout(void* base, int64_t n, int64_t capacity, int total_tiles, bo
     if (w.cm_path) {
         w.cm = static_cast<uint32_t*>(take((size_t)nchunks * total_tiles * 4));
         w.chunk_sum = static_cast<uint32_t*>(take((size_t)nchunks * 4));
+        w.tile_tot = static_cast<uint32_t*>(take((size_t)total_tiles * 4));
     } else {
         w.keys_tmp = static_cast<uint32_t*>(take(cap * 4));
         w.vals_tmp = static_cast<uint32_t*>(take(cap * 4));
@@ -679,8 +679,7 @@ BinWs bin_ws_layout(void* base, int64_t n, int64_t capacity, int total_tiles, bo
         w.hist = static_cast<uint32_t*>(take((size_t)rp.passes * kHistReplicas * kMaxRadix * 4));
         w.blk_lb = static_cast<uint64_t*>(take((size_t)nblk * 8));
     }
-    w.lookback =
-        static_cast<uint32_t*>(take(w.cm_path ? (size_t)groups * 4 : (size_t)rp.passes * sblk * kMaxRadix * 4));
+    if (!w.cm_path) w.lookback = static_cast<uint32_t*>(take((size_t)rp.passes * sblk * kMaxRadix * 4));
     w.tickets = static_cast<uint32_t*>(take(16));
     w.zero = b ? reinterpret_cast<uint32_t*>(b + zero_off) : nullptr;
     w.zero_words = (int64_t)((off - zero_off) / 4);

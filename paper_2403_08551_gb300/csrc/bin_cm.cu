@@ -8,17 +8,20 @@
 // with start = exclusive scan of the column sums over tiles. This is the
 // order the LSD radix path produces (tiles ascending, Gaussian index
 // ascending inside a tile), obtained without a sort:
-//   k_count   one block per two chunks: shared-memory tile histograms give
-//             the rows of M and the chunk pair totals; clears the binning
+//   k_count   one block per chunk: shared-memory tile histograms give the
+//             rows of M and the chunk pair totals; clears the binning
 //             scratch when asked.
 //   k_colscan one block per 16 tiles: column prefix sums over the chunks
-//             (P[b][t] = start[t] + sum_{b' < b} M[b'][t], written over M),
-//             chained scan of the column totals across tile groups (bounded
-//             look-back) -> start, ranges, K and the capacity check.
-//   k_place   one block per chunk (two warps per 32 Gaussians): a lane
-//             mask per 32 Gaussians of every tile in shared memory gives
-//             each pair's rank inside the chunk; the block scatters ids,
-//             records and emission indices and writes pair_off.
+//             (P[b][t] = sum_{b' < b} M[b'][t], written over M) and the
+//             column totals tot[t]; no block waits on another.
+//   k_place   one block per chunk (two warps per 32 Gaussians): every block
+//             scans the column totals itself (start = exclusive scan of tot
+//             over the at most kCmMaxTiles tiles); a lane mask per 32
+//             Gaussians of every tile in shared memory gives each pair's
+//             rank inside the chunk; the block scatters ids, records and
+//             emission indices and writes pair_off; the blocks share out
+//             the ranges, the keys (the tile id over each range), K and the
+//             capacity check.
 #include <algorithm>
 
 #include "kernels.cuh"
@@ -80,18 +83,22 @@ __device__ __forceinline__ int pair_tile(const ChunkSmem& cs, int li, int j) {
 }
 
 // Loads this thread's Gaussian (count, rect, image) into the chunk layout
-// and returns its count (0 for a bad rect, with *bad set). Threads
-// kCmChunk and above of a larger block hold no Gaussian and only take part
-// in the scan. Ends with the block scan's barrier.
+// and returns its count (0 for a bad rect or a negative count, with *bad
+// set). Threads kCmChunk and above of a larger block hold no Gaussian and
+// only take part in the scan. The block scan carries a second sum in its
+// upper 32 bits: `hi` in, its inclusive block prefix out in *hi_incl. Ends
+// with the block scan's barrier.
 __device__ __forceinline__ int load_chunk(const int4* __restrict__ rect, const int32_t* __restrict__ cnt,
-                                          const Batch& B, int g, ChunkSmem& cs, int* s_warp, bool* bad) {
+                                          const Batch& B, int g, ChunkSmem& cs, uint64_t* s_warp, bool* bad,
+                                          uint32_t hi = 0u, uint32_t* hi_incl = nullptr) {
     const bool holds = threadIdx.x < kCmChunk;
     const bool in = holds && g < B.total_gauss;
     int c = in ? cnt[g] : 0;
     int4 r = in ? rect[g] : make_int4(0, 0, 0, 0);  // issued with the count: no dependent load
     if (c <= 0) r = make_int4(0, 0, 0, 0);
     int2 im = make_int2(0, 0);
-    *bad = false;
+    *bad = c < 0;
+    if (c < 0) c = 0;
     if (c > 0) {
         const ImgDesc d = img_desc(B, image_of_gauss(B, g));
         if (rect_ok(r, d, c)) {
@@ -106,8 +113,9 @@ __device__ __forceinline__ int load_chunk(const int4* __restrict__ rect, const i
         cs.img[threadIdx.x] = im;
         cs.inv_w[threadIdx.x] = c > 0 ? __frcp_rn((float)(r.z - r.x)) : 0.f;
     }
-    const int incl = block_incl_scan<int>(c, s_warp);
-    if (holds) cs.off[threadIdx.x + 1] = incl;
+    const uint64_t incl = block_incl_scan<uint64_t>(((uint64_t)hi << 32) | (uint32_t)c, s_warp);
+    if (holds) cs.off[threadIdx.x + 1] = (int)(uint32_t)incl;
+    if (hi_incl) *hi_incl = (uint32_t)(incl >> 32);
     if (threadIdx.x == 0) cs.off[0] = 0;
     __syncthreads();
     return c;
@@ -124,7 +132,7 @@ __global__ void __launch_bounds__(kCmChunk) k_count(const int4* __restrict__ rec
                                                     int64_t zero_n) {
     extern __shared__ uint32_t s_h[];  // [total_tiles]
     __shared__ ChunkSmem cs;
-    __shared__ int s_warp[32];
+    __shared__ uint64_t s_warp[32];
     pdl_wait();
     if (zero) zero_words(zero, zero_n);
     const int Tn = B.total_tiles;
@@ -150,35 +158,21 @@ __global__ void __launch_bounds__(kCmChunk) k_count(const int4* __restrict__ rec
 }
 
 // ---------------------------------------------------------------------------
-// Column scan: block (in ticket order) -> tiles [16 blk, 16 blk + 16); thread
-// (tile ti, slab sl) -> chunk rows [sl rs, (sl + 1) rs) of tile ti, 32 slabs.
-// Pass 1 sums each slab's rows (kept in registers when they fit). Warp j
-// scans tile j's 32 slab partials, giving every slab's offset inside the
-// column and the column totals; warp 0 scans the totals over the block's
-// tiles and chains the block total through lower tickets (warp-wide
-// look-back over 32 predecessors per round, retried until the words up to
-// the nearest inclusive prefix are all published; bounded spin). Pass 2
-// writes P[r][t] = start[t] + prefix over M in place, and warp w writes the
-// sorted keys of the group's tile w (the tile id over its range). The block
-// holding the last tile stores K, updates k_max and raises the capacity
-// error.
+// Column scan: block blk -> tiles [16 blk, 16 blk + 16); thread (tile ti,
+// slab sl) -> chunk rows [sl rs, (sl + 1) rs) of tile ti, 32 slabs. Pass 1
+// sums each slab's rows (kept in registers when they fit). Warp j scans tile
+// j's 32 slab partials, giving every slab's offset inside the column and the
+// column total, which it stores in tot. Pass 2 writes
+// P[r][t] = sum_{r' < r} M[r'][t] in place. No block waits on another: the
+// start of each tile is added by the placement kernel.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kCmScanThreads) k_colscan(uint32_t* __restrict__ M, int nchunks, int total_tiles,
-                                                          int2* __restrict__ ranges, uint32_t* __restrict__ keys,
-                                                          int64_t capacity, int64_t* __restrict__ k_dev,
-                                                          int64_t* __restrict__ k_max, uint32_t* __restrict__ lookback,
-                                                          uint32_t* __restrict__ ticket,
-                                                          uint32_t* __restrict__ status) {
+                                                          uint32_t* __restrict__ tot) {
     constexpr int TG = kCmGroupTiles, NS = kCmSlabs, NW = kCmScanThreads / 32;
     static_assert(NS == 32 && TG <= NW && 32 % TG == 0, "a warp scans one tile's 32 slabs; one warp per tile");
     __shared__ uint32_t s_part[NS][TG];
-    __shared__ uint32_t s_start[TG];
-    __shared__ uint32_t s_col[TG];
-    __shared__ uint32_t s_ticket;
     pdl_wait();
-    if (threadIdx.x == 0) s_ticket = atomicAdd(ticket, 1u);
-    __syncthreads();
-    const int blk = (int)s_ticket;
+    const int blk = (int)blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // thread -> (tile ti of the group, row slab sl): TG consecutive tiles of one
     // slab row are one contiguous 4 TG-byte segment of M
@@ -220,88 +214,18 @@ __global__ void __launch_bounds__(kCmScanThreads) k_colscan(uint32_t* __restrict
             if (lane >= o) in += u;
         }
         s_part[lane][warp] = in - x;
-        if (lane == 31) {
-            s_start[warp] = in;  // column total, replaced by the start below
-            s_col[warp] = in;
-        }
+        if (lane == 31 && blk * TG + warp < total_tiles) tot[blk * TG + warp] = in;
     }
     __syncthreads();
-    if (warp == 0) {
-        const uint32_t col = lane < TG ? s_start[lane] : 0u;
-        uint32_t incl = col;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += u;
-        }
-        const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
-        uint32_t excl = 0;
-        if (blk == 0) {
-            if (lane == 0) st_relaxed_u32(lookback, kFlagPre | (tot & kValMask));
-        } else {
-            if (lane == 0) st_relaxed_u32(lookback + blk, kFlagAgg | (tot & kValMask));
-            int j = blk - 1;
-            uint32_t spins = 0;
-            while (j >= 0) {
-                const int idx = j - lane;  // lane 0 = nearest predecessor
-                const uint32_t w = idx >= 0 ? ld_relaxed_u32(lookback + idx) : kFlagPre;
-                const uint32_t f = w & (3u << 30);
-                const uint32_t pre = __ballot_sync(0xffffffffu, f == kFlagPre);
-                const int fp = pre ? __ffs(pre) - 1 : 31;
-                const uint32_t upto = fp == 31 ? 0xffffffffu : ((2u << fp) - 1u);  // lanes 0 .. fp
-                const uint32_t notready = __ballot_sync(0xffffffffu, f == 0u) & upto;
-                if (notready) {
-                    if (++spins > kSpinLimit) {
-                        if (lane == 0) flag_error(status, kErrTimeout);
-                        break;
-                    }
-                    if (spins > 16) __nanosleep(64);
-                    continue;
-                }
-                excl += warp_sum<uint32_t>(((upto >> lane) & 1u) ? (w & kValMask) : 0u);
-                if (pre) break;
-                j -= 32;
-            }
-            if (lane == 0) st_relaxed_u32(lookback + blk, kFlagPre | ((excl + tot) & kValMask));
-        }
-        const uint32_t start = excl + incl - col;
-        if (lane < TG) {
-            s_start[lane] = start;
-            const int tl = blk * TG + lane;
-            if (tl < total_tiles) {
-                int2 rg = make_int2(0, 0);
-                if (col) {
-                    rg.x = (int)min((int64_t)start, capacity);
-                    rg.y = (int)min((int64_t)start + col, capacity);
-                }
-                ranges[tl] = rg;
-            }
-        }
-        if ((blk + 1) * TG >= total_tiles && lane == 0) {
-            const int64_t K = (int64_t)excl + tot;
-            *k_dev = K;
-            if (k_max) atomicMax(reinterpret_cast<unsigned long long*>(k_max), (unsigned long long)K);
-            if (K > capacity) flag_error(status, kErrCapacity);
-        }
-    }
-    __syncthreads();
-    if (warp < TG) {
-        // keys: warp w writes tile (TG blk + w) over its sorted range
-        const int tk = blk * TG + warp;
-        if (tk < total_tiles) {
-            const int64_t s0 = s_start[warp], e0 = min(s0 + (int64_t)s_col[warp], capacity);
-            for (int64_t q = s0 + lane; q < e0; q += 32) keys[q] = (uint32_t)tk;
-        }
-    }
     if (tv && in_regs) {
-        uint32_t run = s_start[ti] + s_part[sl][ti];
+        uint32_t run = s_part[sl][ti];
 #pragma unroll
         for (int i = 0; i < kCmRowRegs; ++i) {
             if (r0 + i < r1) M[(size_t)(r0 + i) * total_tiles + t] = run;
             run += v[i];
         }
     } else if (tv) {
-        uint32_t run = s_start[ti] + s_part[sl][ti];
+        uint32_t run = s_part[sl][ti];
         int r = r0;
         for (; r + 8 <= r1; r += 8) {
             uint32_t u[8];
@@ -323,46 +247,73 @@ __global__ void __launch_bounds__(kCmScanThreads) k_colscan(uint32_t* __restrict
 
 // ---------------------------------------------------------------------------
 // Place: block = chunk b, two warps per lane group of 32 Gaussians (the
-// group's pairs alternate between them in rounds of 32). Lane masks
-// s_m[k][t] (bit l set when local Gaussian 32 k + l covers tile t) are built
-// with atomicOr, which is order-independent; then pair (t, g),
-// g = 128 b + 32 k + l, lands at
-//   P[b][t] + sum_{k' < k} popc(s_m[k'][t]) + popc(s_m[k][t] & bits below l),
-// i.e. ascending g inside the tile; the block writes ids and records there
-// (the keys come from the column scan). The chunk's row of P and its records
-// are staged in shared memory. pair_off = exclusive scan of cnt in emission
-// order, the chunk base from the chunk totals.
+// group's pairs alternate between them in rounds of 32). Every block first
+// forms start[t] = sum_{t' < t} tot[t'] (thread i holds tiles
+// [kTilesPerThread i, kTilesPerThread (i + 1)), one block scan) and adds it
+// to its chunk's row of P. Lane masks s_m[k][t] (bit l set when local
+// Gaussian 32 k + l covers tile t) are built with atomicOr, which is
+// order-independent; then pair (t, g), g = 128 b + 32 k + l, lands at
+//   start[t] + P[b][t] + sum_{k' < k} popc(s_m[k'][t]) + popc(s_m[k][t] & bits below l),
+// i.e. ascending g inside the tile; the block writes ids, records and
+// emission indices there. pair_off = exclusive scan of cnt in emission
+// order, the chunk base from the chunk totals. The blocks share out the
+// tile ranges (a thread per tile over the grid), the keys (a warp per tile
+// over the grid: the tile id over its range) and, in block 0, K, k_max and
+// the capacity check.
 // ---------------------------------------------------------------------------
 constexpr int kPlaceThreads = 2 * kCmChunk;
+constexpr int kTilesPerThread = kCmMaxTiles / kPlaceThreads;
+constexpr int kPlaceSmemWords = kCmChunk / 32 + 2;  // per tile: lane masks, P row, start
+static_assert(kCmMaxTiles % (4 * kPlaceThreads) == 0, "whole uint4 loads of the tile totals per thread");
 
 __global__ void __launch_bounds__(kPlaceThreads) k_place(const int4* __restrict__ rect, const int32_t* __restrict__ cnt,
                                                          const float4* __restrict__ rec, Batch B,
                                                          const uint32_t* __restrict__ P,
+                                                         const uint32_t* __restrict__ tot,
                                                          const uint32_t* __restrict__ chunk_sum, int nchunks,
-                                                         int64_t capacity, uint32_t* __restrict__ ids,
+                                                         int64_t capacity, uint32_t* __restrict__ keys,
+                                                         uint32_t* __restrict__ ids, int2* __restrict__ ranges,
                                                          float4* __restrict__ rec_binned, uint32_t* __restrict__ emit,
-                                                         int64_t* __restrict__ pair_off, uint32_t* __restrict__ status) {
+                                                         int64_t* __restrict__ pair_off, int64_t* __restrict__ k_dev,
+                                                         int64_t* __restrict__ k_max, uint32_t* __restrict__ status) {
     constexpr int NG = kCmChunk / 32;  // lane groups
     constexpr int kRowLoads = (kCmMaxTiles + kPlaceThreads - 1) / kPlaceThreads;
-    extern __shared__ uint32_t s_dyn[];  // [NG][total_tiles] lane masks, then [total_tiles] P row
+    // [NG][total_tiles] lane masks, [total_tiles] P row (+ start), [total_tiles + 1] start
+    extern __shared__ uint32_t s_dyn[];
     __shared__ ChunkSmem cs;
     __shared__ float4 s_rec[kCmChunk][2];
-    __shared__ int s_warp[32];
+    __shared__ uint64_t s_warp[32];
     __shared__ int64_t s_warp64[32];
     pdl_wait();
     const int Tn = B.total_tiles;
     uint32_t* s_m = s_dyn;
     uint32_t* s_p = s_dyn + NG * Tn;
+    uint32_t* s_start = s_p + Tn;
     const int b = blockIdx.x;
     const bool holds = threadIdx.x < kCmChunk;  // threads holding a Gaussian of the chunk
     const int g = b * kCmChunk + threadIdx.x;
-    // Independent loads first: the chunk's row of P, the chunk totals below
-    // b and this Gaussian's record.
+    // Independent loads first: the chunk's row of P, this thread's tile
+    // totals, the chunk totals below b and this Gaussian's record.
     const uint32_t* prow = P + (size_t)b * Tn;
 #pragma unroll
     for (int i = 0; i < kRowLoads; ++i) {
         const int idx = threadIdx.x + i * kPlaceThreads;
         if (idx < Tn) s_p[idx] = prow[idx];
+    }
+    const int t0 = threadIdx.x * kTilesPerThread;
+    uint32_t tt[kTilesPerThread];
+#pragma unroll
+    for (int i = 0; i < kTilesPerThread; i += 4) {
+        if (t0 + i + 3 < Tn) {
+            const uint4 q = *reinterpret_cast<const uint4*>(tot + t0 + i);
+            tt[i] = q.x;
+            tt[i + 1] = q.y;
+            tt[i + 2] = q.z;
+            tt[i + 3] = q.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) tt[i + e] = t0 + i + e < Tn ? tot[t0 + i + e] : 0u;
+        }
     }
     int64_t pre = 0;
     for (int i = threadIdx.x; i < b; i += 8 * kPlaceThreads) {  // eight predicated loads in flight per round
@@ -377,10 +328,27 @@ __global__ void __launch_bounds__(kPlaceThreads) k_place(const int4* __restrict_
         s_rec[threadIdx.x][1] = rec[2 * (size_t)g + 1];
     }
     for (int i = threadIdx.x; i < NG * Tn; i += kPlaceThreads) s_m[i] = 0u;
+    uint32_t tsum = 0;
+#pragma unroll
+    for (int i = 0; i < kTilesPerThread; ++i) tsum += tt[i];
     bool bad;
-    const int c = load_chunk(rect, cnt, B, g, cs, s_warp, &bad);
+    uint32_t tincl = 0;
+    const int c = load_chunk(rect, cnt, B, g, cs, s_warp, &bad, tsum, &tincl);  // also scans the tile totals
     if (bad) flag_error(status, kErrBounds);
-    pre = block_sum<int64_t>(pre, s_warp64);
+    {
+        // start of this thread's tiles, added to the chunk's row of P
+        uint32_t run = tincl - tsum;
+#pragma unroll
+        for (int i = 0; i < kTilesPerThread; ++i) {
+            if (t0 + i < Tn) {
+                s_start[t0 + i] = run;
+                s_p[t0 + i] += run;
+            }
+            run += tt[i];
+        }
+        if (threadIdx.x == kPlaceThreads - 1) s_start[Tn] = tincl;  // K
+    }
+    pre = block_sum<int64_t>(pre, s_warp64);  // its barriers also publish the starts
     if (holds) {
         const int off = cs.off[threadIdx.x];
         if (g < B.total_gauss) pair_off[g] = pre + off;
@@ -404,7 +372,7 @@ __global__ void __launch_bounds__(kPlaceThreads) k_place(const int4* __restrict_
         const int t = pair_tile(cs, w0 + l, j);
         uint32_t pos = s_p[t] + __popc(s_m[grp * Tn + t] & ((1u << l) - 1u));
         for (int v = 0; v < grp; ++v) pos += __popc(s_m[v * Tn + t]);
-        if ((int64_t)pos >= capacity) continue;  // dropped; the scan raised the capacity error
+        if ((int64_t)pos >= capacity) continue;  // dropped; block 0 raises the capacity error
         ids[pos] = (uint32_t)(b * kCmChunk + w0 + l);
         if (emit) emit[pos] = (uint32_t)(pre + cs.off[w0 + l] + j);
         if (rec_binned) {
@@ -415,6 +383,26 @@ __global__ void __launch_bounds__(kPlaceThreads) k_place(const int4* __restrict_
                 rec_binned[2 * (size_t)pos + 1] = s_rec[w0 + l][1];
             }
         }
+    }
+    // ranges, keys and K, shared out over the grid
+    for (int t = b * kPlaceThreads + threadIdx.x; t < Tn; t += gridDim.x * kPlaceThreads) {
+        const uint32_t s0 = s_start[t], s1 = s_start[t + 1];
+        int2 rg = make_int2(0, 0);
+        if (s1 > s0) {
+            rg.x = (int)min((int64_t)s0, capacity);
+            rg.y = (int)min((int64_t)s1, capacity);
+        }
+        ranges[t] = rg;
+    }
+    for (int t = b * (kPlaceThreads / 32) + warp; t < Tn; t += gridDim.x * (kPlaceThreads / 32)) {
+        const int64_t s0 = s_start[t], e0 = min((int64_t)s_start[t + 1], capacity);
+        for (int64_t q = s0 + lane; q < e0; q += 32) keys[q] = (uint32_t)t;
+    }
+    if (b == 0 && threadIdx.x == 0) {
+        const int64_t K = s_start[Tn];
+        *k_dev = K;
+        if (k_max) atomicMax(reinterpret_cast<unsigned long long*>(k_max), (unsigned long long)K);
+        if (K > capacity) flag_error(status, kErrCapacity);
     }
 }
 
@@ -439,14 +427,15 @@ cudaError_t launch_bin_cm(const int4* rect, const int32_t* cnt, const float4* re
                        ws.zero, ws.zero_words);
         if (e != cudaSuccess) return e;
     }
-    e = launch_pdl(k_colscan, dim3(groups), dim3(kCmScanThreads), 0, s, ws.cm, nchunks, Tn, ranges, keys, capacity,
-                   k_dev, k_max, ws.lookback, ws.tickets, status);
+    e = launch_pdl(k_colscan, dim3(groups), dim3(kCmScanThreads), 0, s, ws.cm, nchunks, Tn, ws.tile_tot);
     if (e != cudaSuccess) return e;
-    // up to 40 KB dynamic + the static layout: above the default 48 KB window
-    e = smem_optin(reinterpret_cast<const void*>(k_place), (kCmChunk / 32 + 1) * kCmMaxTiles * 4);
+    // lane masks, P row and starts: up to 48 KB dynamic + the static layout,
+    // above the default 48 KB window
+    e = smem_optin(reinterpret_cast<const void*>(k_place), kPlaceSmemWords * kCmMaxTiles * 4 + 4);
     if (e != cudaSuccess) return e;
-    return launch_pdl(k_place, dim3(nchunks), dim3(kPlaceThreads), (size_t)(kCmChunk / 32 + 1) * Tn * 4, s, rect, cnt, rec,
-                      B, ws.cm, ws.chunk_sum, nchunks, capacity, ids, rec_binned, emit, pair_off, status);
+    return launch_pdl(k_place, dim3(nchunks), dim3(kPlaceThreads), (size_t)(kPlaceSmemWords * Tn + 1) * 4, s, rect,
+                      cnt, rec, B, ws.cm, ws.tile_tot, ws.chunk_sum, nchunks, capacity, keys, ids, ranges, rec_binned,
+                      emit, pair_off, k_dev, k_max, status);
 }
 
 }  // namespace gi

@@ -52,7 +52,7 @@ bool cm_applies(int64_t n, int total_tiles);
 // Binning workspace carve-up. [zero, zero + zero_words) holds every buffer
 // that must be zero before a binning pass. Radix path: keys_tmp, vals_tmp,
 // hist [passes][kHistReplicas][kMaxRadix], lookback [passes][sort_blocks][kMaxRadix]. Count-matrix path: cm
-// [chunks][tiles], chunk_sum [chunks], lookback [tile groups].
+// [chunks][tiles], chunk_sum [chunks], tile_tot [tiles] (column totals).
 struct BinWs {
     bool cm_path;
     int64_t* blk_sum;     // [ceil(n / kProjBlock)]
@@ -62,6 +62,7 @@ struct BinWs {
                           //            sort carries the emission index instead of the Gaussian)
     uint32_t* cm;         // [chunks][tiles]     (count matrix)
     uint32_t* chunk_sum;  // [chunks]            (count matrix)
+    uint32_t* tile_tot;   // [tiles]             (count matrix: column totals, 16-byte aligned)
     uint32_t* zero;
     int64_t zero_words;
     uint32_t* hist;       // [passes][kHistReplicas][kMaxRadix] (radix)
