@@ -359,20 +359,41 @@ __global__ void __launch_bounds__(kPlaceThreads) k_place(const int4* __restrict_
     const bool v8 = (reinterpret_cast<uintptr_t>(rec_binned) & 31) == 0;  // one 32-byte store per record
     const int woff = cs.off[w0 + lane] - cs.off[w0];
     const int wtot = cs.off[w0 + 32] - cs.off[w0];
-    for (int p = p0 + lane; p - lane < wtot; p += 64) {  // warp-uniform trip count
-        const int l = warp_owner(woff, p);
-        const int j = p - __shfl_sync(0xffffffffu, woff, l);
+    // Pair p of the lane group (emission order) -> owning lane l, index j in
+    // its rect, tile t. The first kCache rounds keep (t, l, j) in registers
+    // for the scatter after the barrier; later rounds recompute them.
+    constexpr int kCache = 4;
+    int ct[kCache], clj[kCache];
+    auto locate = [&](int p, int& l, int& j) {
+        l = warp_owner(woff, p);
+        j = p - __shfl_sync(0xffffffffu, woff, l);
+    };
+#pragma unroll
+    for (int r = 0; r < kCache; ++r) {
+        const int p = p0 + lane + 64 * r;
+        ct[r] = 0;
+        clj[r] = 0;
+        if (p - lane < wtot) {  // warp-uniform
+            int l, j;
+            locate(p, l, j);
+            if (p < wtot) {
+                const int t = pair_tile(cs, w0 + l, j);
+                atomicOr(&s_m[grp * Tn + t], 1u << l);
+                ct[r] = t;
+                clj[r] = (j << 5) | l;  // j < 2048 tiles
+            }
+        }
+    }
+    for (int p = p0 + lane + 64 * kCache; p - lane < wtot; p += 64) {  // warp-uniform trip count
+        int l, j;
+        locate(p, l, j);
         if (p < wtot) atomicOr(&s_m[grp * Tn + pair_tile(cs, w0 + l, j)], 1u << l);
     }
     __syncthreads();
-    for (int p = p0 + lane; p - lane < wtot; p += 64) {
-        const int l = warp_owner(woff, p);
-        const int j = p - __shfl_sync(0xffffffffu, woff, l);
-        if (p >= wtot) continue;
-        const int t = pair_tile(cs, w0 + l, j);
+    auto scatter = [&](int t, int l, int j) {
         uint32_t pos = s_p[t] + __popc(s_m[grp * Tn + t] & ((1u << l) - 1u));
         for (int v = 0; v < grp; ++v) pos += __popc(s_m[v * Tn + t]);
-        if ((int64_t)pos >= capacity) continue;  // dropped; block 0 raises the capacity error
+        if ((int64_t)pos >= capacity) return;  // dropped; block 0 raises the capacity error
         ids[pos] = (uint32_t)(b * kCmChunk + w0 + l);
         if (emit) emit[pos] = (uint32_t)(pre + cs.off[w0 + l] + j);
         if (rec_binned) {
@@ -383,6 +404,14 @@ __global__ void __launch_bounds__(kPlaceThreads) k_place(const int4* __restrict_
                 rec_binned[2 * (size_t)pos + 1] = s_rec[w0 + l][1];
             }
         }
+    };
+#pragma unroll
+    for (int r = 0; r < kCache; ++r)
+        if (p0 + lane + 64 * r < wtot) scatter(ct[r], clj[r] & 31, clj[r] >> 5);
+    for (int p = p0 + lane + 64 * kCache; p - lane < wtot; p += 64) {
+        int l, j;
+        locate(p, l, j);
+        if (p < wtot) scatter(pair_tile(cs, w0 + l, j), l, j);
     }
     // ranges, keys and K, shared out over the grid
     for (int t = b * kPlaceThreads + threadIdx.x; t < Tn; t += gridDim.x * kPlaceThreads) {
