@@ -425,8 +425,10 @@ cudaError_t launch_render(const float4* rec_binned, const int2* ranges, const Ba
                           uint32_t* status, cudaStream_t s, const TileQueue* queue) {
     // split: lane groups that share one tile's list (each group covers all
     // of the tile's pixels); 0 picks the default for the tile edge. Tile 16
-    // gives a lane a 4 x 4 block (four rows share each column's terms; 16
-    // lanes per group), tiles 8 and 32 a strip of one row.
+    // gives a lane a block 4 pixels wide (the rows share each column's
+    // terms): 4 rows (16 lanes per group) with split 4, 8 rows (8 lanes per
+    // group, 64 threads per block) with split 8; tiles 8 and 32 a strip of
+    // one row.
     const int sp = B.split;
     switch (B.tile) {
         case 8:
@@ -442,7 +444,7 @@ cudaError_t launch_render(const float4* rec_binned, const int2* ranges, const Ba
                 return launch_cfg<RCfg<16, 4, 4, 4>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
                                                      loss_tile, queue, status, s);
             if (sp == 0 || sp == 8)
-                return launch_cfg<RCfg<16, 4, 8, 4>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
+                return launch_cfg<RCfg<16, 4, 8, 8>>(rec_binned, ranges, B, target, out, dl_hwc, dl_tiled, loss_sum,
                                                      loss_tile, queue, status, s);
             return cudaErrorInvalidValue;
         case 32:
