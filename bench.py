@@ -45,7 +45,7 @@ BWD_FLOP_PER_EVAL = 24   # sigma 7 + 3 FFMA (dL/dc') + FMUL + 2 FFMA (<G, c'>) +
 # DRAM bytes (read + write) per launch of the ALU-bound kernels at this
 # workload, from one ncu --set full capture of the current kernels
 # (profiles/k_backward_c1_768x512_70k.md, profiles/k_render_c1_768x512_70k.md).
-NCU_TRAFFIC_BYTES = {"k_backward": 20.628e6, "k_render": 16.119e6}
+NCU_TRAFFIC_BYTES = {"k_backward": 20.628e6, "k_render": 16.187e6}
 # SFU_LANES: ex2 results per clock per SM as measured by gi_alu_peaks on GB300
 # (9.99e12 ex2/s at 2064 MHz over 152 SMs = 32).
 SMS, FP32_LANES, SFU_LANES, SM_MAX_MHZ = 152, 128, 32, 2070.0
