@@ -138,9 +138,10 @@ __device__ __forceinline__ void render_tile(int t, uint32_t& phase, const RSmem<
                 const float dx0 = px0 - r0.x;
                 const float2 M11 = make_float2(r0.z, r0.z), M21 = make_float2(r0.w, r0.w);
                 float2 Z2Y[ROWS];
+                const float z2y0 = r1.x * dy;
 #pragma unroll
                 for (int r = 0; r < ROWS; ++r) {
-                    const float z2y = r1.x * (dy + (float)r);
+                    const float z2y = r ? fmaf(r1.x, (float)r, z2y0) : z2y0;  // m22 (dy + r)
                     Z2Y[r] = make_float2(z2y, z2y);
                 }
                 const float2 cr = make_float2(r1.y, r1.y), cg = make_float2(r1.z, r1.z), cb = make_float2(r1.w, r1.w);
