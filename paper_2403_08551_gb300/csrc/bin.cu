@@ -58,15 +58,16 @@ __global__ void __launch_bounds__(kProjBlock) k_project(ParamsIn P, Batch B, flo
                                                         int4* __restrict__ rect, int32_t* __restrict__ cnt,
                                                         int64_t* __restrict__ blk_sum, ZeroJob zj,
                                                         uint32_t* __restrict__ M, uint32_t* __restrict__ chunk_sum) {
-    static_assert(kProjBlock == 2 * kCmChunk, "a projection block holds two count-matrix chunks");
-    extern __shared__ uint32_t s_h[];  // with M: [2][total_tiles] tile histograms of the block's two chunks
+    constexpr int CPB = kProjBlock / kCmChunk;  // count-matrix chunks per projection block
+    static_assert(kProjBlock % kCmChunk == 0, "a projection block holds whole count-matrix chunks");
+    extern __shared__ uint32_t s_h[];  // with M: [CPB][total_tiles] tile histograms of the block's chunks
     __shared__ int64_t s_warp[32];
-    __shared__ uint32_t s_tot[2];
+    __shared__ uint32_t s_tot[CPB];
     pdl_wait();
     zero_job(zj);
     if (M) {
-        for (int i = threadIdx.x; i < 2 * B.total_tiles; i += blockDim.x) s_h[i] = 0u;
-        if (threadIdx.x < 2) s_tot[threadIdx.x] = 0u;
+        for (int i = threadIdx.x; i < CPB * B.total_tiles; i += blockDim.x) s_h[i] = 0u;
+        if (threadIdx.x < CPB) s_tot[threadIdx.x] = 0u;
         __syncthreads();
     }
     const int g = blockIdx.x * kProjBlock + threadIdx.x;
@@ -223,8 +224,8 @@ __global__ void __launch_bounds__(kProjBlock) k_project(ParamsIn P, Batch B, flo
     if (threadIdx.x == 0 && blk_sum) blk_sum[blockIdx.x] = tot;
     if (M) {
         const int nchunks = (B.total_gauss + kCmChunk - 1) / kCmChunk;
-        for (int q = 0; q < 2; ++q) {
-            const int chunk = 2 * blockIdx.x + q;
+        for (int q = 0; q < CPB; ++q) {
+            const int chunk = CPB * blockIdx.x + q;
             if (chunk >= nchunks) break;
             uint32_t* row = M + (size_t)chunk * B.total_tiles;
             for (int i = threadIdx.x; i < B.total_tiles; i += blockDim.x) row[i] = s_h[q * B.total_tiles + i];
@@ -690,7 +691,7 @@ BinWs bin_ws_layout(void* base, int64_t n, int64_t capacity, int total_tiles, bo
 cudaError_t launch_project(const ParamsIn& P, const Batch& B, float4* rec, int4* rect, int32_t* cnt,
                            int64_t* blk_sum, const ZeroJob& zj, cudaStream_t s, uint32_t* cm, uint32_t* chunk_sum) {
     const int nblk = std::max(1, (B.total_gauss + kProjBlock - 1) / kProjBlock);
-    const size_t smem = cm ? (size_t)2 * B.total_tiles * 4 : 0;
+    const size_t smem = cm ? (size_t)(kProjBlock / kCmChunk) * B.total_tiles * 4 : 0;
     return launch_pdl(k_project, dim3(nblk), dim3(kProjBlock), smem, s, P, B, rec, rect, cnt, blk_sum, zj, cm,
                       chunk_sum);
 }
