@@ -432,18 +432,9 @@ __global__ void __launch_bounds__(kSortThreads) k_onesweep(
 #pragma unroll
     for (int r = 0; r < kSortItems; ++r) {
         const uint32_t dg = dig[r];
-        // lanes with the same digit: one ballot per digit bit (and one for
-        // "has a digit"), each lane keeping the lanes that agree with it
-        uint32_t peers = __ballot_sync(0xffffffffu, dg < kMaxRadix);
-        if (dg >= kMaxRadix) peers = ~peers;
-#pragma unroll
-        for (int b = 0; b < kMaxDigitBits; ++b) {
-            if (b < dbits) {
-                const bool bit = (dg >> b) & 1u;
-                const uint32_t bal = __ballot_sync(0xffffffffu, bit);
-                peers &= bit ? bal : ~bal;
-            }
-        }
+        // lanes with the same digit (keys past K carry kMaxRadix, a value no
+        // digit has, and are grouped apart): one warp match
+        const uint32_t peers = __match_any_sync(0xffffffffu, dg);
         const int leader = __ffs(peers) - 1;
         uint32_t base = 0;
         if (lane == leader && dg < kMaxRadix) {
