@@ -324,11 +324,13 @@ __global__ void __launch_bounds__(kProjBlock) k_emit(const int4* __restrict__ re
         const int lane = threadIdx.x & 31;
         int4 r = make_int4(0, 0, 0, 0);
         int tb = 0, tw = 0;
+        float inv_w = 0.f;
         if (c > 0) {
             r = rect[g];
             const ImgDesc d = img_desc(B, image_of_gauss(B, g));
             tb = d.tile_base;
             tw = d.tw;
+            inv_w = __frcp_rn((float)max(1, r.z - r.x));
         }
         int incl = c;  // warp inclusive prefix of the counts
 #pragma unroll
@@ -350,10 +352,14 @@ __global__ void __launch_bounds__(kProjBlock) k_emit(const int4* __restrict__ re
             const int rx = __shfl_sync(0xffffffffu, r.x, lo), ry = __shfl_sync(0xffffffffu, r.y, lo);
             const int rz = __shfl_sync(0xffffffffu, r.z, lo);
             const int otb = __shfl_sync(0xffffffffu, tb, lo), otw = __shfl_sync(0xffffffffu, tw, lo);
+            const float oinv = __shfl_sync(0xffffffffu, inv_w, lo);
             const int64_t pp = wbase + q;
             if (q < wtot && pp < capacity) {
                 const int w = max(1, rz - rx);
-                const int row = j / w;
+                // row = j / w: for j < 2^11, (j + 0.5) (1/w) truncated is exact
+                // (the product's error stays below 2^-12 / w, less than the
+                // 0.5 / w distance of (j + 0.5) / w from an integer)
+                const int row = j < 2048 ? __float2int_rz(((float)j + 0.5f) * oinv) : j / w;
                 const uint32_t key = (uint32_t)(otb + (ry + row) * otw + rx + (j - row * w));
                 keys[pp] = key;
                 const uint32_t og = (uint32_t)(blockIdx.x * kProjBlock + (threadIdx.x & ~31) + lo);
